@@ -1,0 +1,194 @@
+/*
+ * ncs.h - C ABI of the GB300 narrow capture / narrow escape solver.
+ *
+ * The library solves the block-preconditioned second-kind multiple-scattering
+ * system of Kaye & Greengard, "A fast solver for the narrow capture and narrow
+ * escape problems in the sphere" (arXiv 1906.04209), Section 6, eq. (opinteqnsdisc):
+ *
+ *     f_i + P sum_{j != i} S_ij B f_j = P 1,     i = 1..N,
+ *
+ * for N disk patches of geodesic radius eps on the unit sphere, with K Zernike
+ * coefficients per patch. The matrix-vector product runs on the GPU
+ * (Section 7, Step 3): the outgoing map rho_j = T f_j, the far-field sums of the
+ * Neumann Green's function over skeleton points, and the Zernike transform P.
+ *
+ * Conventions (all entry points):
+ *   - Return 0 (NCS_OK) on success or a negative NCS_E_* code; no exceptions
+ *     cross the ABI. ncs_last_error() describes the most recent failure on a
+ *     context. Inputs are validated before any device work is issued.
+ *   - Host arrays are owned by the caller, read (or written) only during the
+ *     call, and copied where the library keeps the data.
+ *   - Device pointers are owned by the caller, must be resident on the device
+ *     that was current when the context was created, are used only on the given
+ *     CUDA stream and only until the call's work on that stream completes.
+ *   - Vectors over all patches are patch-major: x[i*K + k] is coefficient k of
+ *     patch i; k follows the Zernike ordering (n ascending, then m ascending,
+ *     cos before sin) of Section 4.
+ *   - Patch frames: for a centre c, e3 = c, e1 = (z x c)/|z x c| (e1 = x when c
+ *     is a pole), e2 = e3 x e1; the local point (t, theta) is
+ *     cos t c + sin t (cos theta e1 + sin theta e2), t the arclength from c.
+ *   - A context is not thread-safe; use one per host thread.
+ */
+#ifndef NCS_H
+#define NCS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NCS_OK 0
+#define NCS_E_INPUT (-1)   /* invalid argument or infeasible patch layout */
+#define NCS_E_NOCONV (-2)  /* iteration cap reached before the tolerance */
+#define NCS_E_NUMERIC (-3) /* breakdown, NaN or Inf in the iteration */
+#define NCS_E_CUDA (-4)    /* CUDA runtime error (message in ncs_last_error) */
+#define NCS_E_TIMEOUT (-5) /* a bounded device wait gave up */
+#define NCS_E_OOM (-6)     /* device or host allocation failed */
+#define NCS_E_STATE (-7)   /* call out of order (e.g. matvec before set_patches) */
+
+#define NCS_EXTERIOR 0 /* narrow capture: G_E, Section 2.2 */
+#define NCS_INTERIOR 1 /* narrow escape:  G_I, Section 2.3 */
+
+#define NCS_FP64 0  /* all pair sums and transforms in FP64 */
+#define NCS_FP32 1  /* FP32 pair sums / transforms in patch- or group-local frames */
+#define NCS_MIXED 2 /* solve only: FP32 inner GMRES + FP64 iterative refinement */
+
+#define NCS_METHOD_AUTO 0   /* tree when N >= tree_min_patches, else direct */
+#define NCS_METHOD_DIRECT 1 /* compressed sums over all other patches, O(N^2) (Section 7.1) */
+#define NCS_METHOD_TREE 2   /* cube-sphere quadtree, O(N log N) (Sections 7.2-7.3, Step 3) */
+
+typedef struct ncs_ctx ncs_ctx;
+
+typedef struct ncs_params {
+  int npan;            /* radial panels of the one-patch solver (Section 8.2), default 13 */
+  int nord;            /* nodes per panel, default 20 */
+  int ntheta_fine;     /* fine-grid azimuths; 0 = M + 40 rounded up to even */
+  double id_tol;       /* interpolative-decomposition tolerance (Section 7.1), default 1e-11 */
+  int threads;         /* host threads for the precompute; 0 = all */
+  double grid_tol;     /* incoming-grid tolerance (Section 7.3), default 1e-8 */
+  int method;          /* NCS_METHOD_*, default AUTO */
+  int tree_min_patches;/* AUTO switches to the tree at this N, default 2000 */
+  int gmres_maxit;     /* GMRES iteration cap, default 200 */
+  int verbose;         /* 0 silent .. 3 chatty (stderr) */
+} ncs_params;
+
+/* Fills *p with the defaults listed above. */
+void ncs_default_params(ncs_params* p);
+
+/*
+ * Creates a context for patch radius eps (0 < eps < 1), problem mode
+ * (NCS_EXTERIOR / NCS_INTERIOR) and K Zernike functions per patch (1 <= K <= 2000),
+ * and runs the one-patch precompute on the host (Section 7, Step 1): modal solves
+ * giving B (Sections 5 and 8), I = w^T B (eq. getI), the interpolative decomposition
+ * and T = Pi W B (Section 7.1, eq. Tmap), and the Zernike transform P (Section 4).
+ * params may be NULL (defaults). This call and ncs_set_patches are host-only; the
+ * CUDA device current at the first call that needs the GPU (a product, solve or
+ * evaluation) is bound to the context for its lifetime and receives the uploads.
+ * On success *out owns host and device memory that ncs_destroy releases.
+ * Errors: NCS_E_INPUT, NCS_E_NUMERIC (precompute failure), NCS_E_OOM; *out is NULL.
+ */
+int ncs_create(double eps, int mode, int K, const ncs_params* params, ncs_ctx** out);
+
+/*
+ * Like ncs_create, but takes the outgoing operator from the caller instead of
+ * computing it: T (p x K row-major), the skeleton points' local polar coordinates
+ * skel_t, skel_theta (p each, t in [0, eps]) and I (K). P and the Zernike
+ * sampling nodes are still formed by the library (Section 4). The arrays are
+ * copied. Used to reuse a stored precompute.
+ */
+int ncs_create_from_operator(double eps, int mode, int K, int p, const double* T,
+                             const double* skel_t, const double* skel_theta, const double* I,
+                             const ncs_params* params, ncs_ctx** out);
+
+/*
+ * Writes context sizes into out[0..n): K, Kstar, p, M, nf (fine-grid points),
+ * N (patches set, 0 if none), nrad (radial nodes), tree levels (0 if no tree),
+ * grid points over all tree groups, pair evaluations per tree matvec (FP counts
+ * of far-field kernel evaluations), direct pairs per matvec.
+ */
+int ncs_info(const ncs_ctx* ctx, int64_t* out, int n);
+
+/* Precompute timings in seconds: out[0] one-patch solve, out[1] ID. */
+int ncs_timings(const ncs_ctx* ctx, double* out, int n);
+
+/*
+ * Copies the precompute out (any pointer may be NULL to skip it): T (p x K),
+ * skeleton (t, theta) (p each), I (K), P (K x Kstar), Zernike nodes on the unit
+ * disk (r, theta) (Kstar each).
+ */
+int ncs_get_operator(const ncs_ctx* ctx, double* T, double* skel_t, double* skel_theta,
+                     double* I, double* P, double* znode_r, double* znode_theta);
+
+/*
+ * Copies the one-patch solution (Section 8): radial collocation nodes trad (nrad)
+ * and radial profiles beta (nrad x K, row-major), so that b_j(t, theta) =
+ * beta_j(t) trig(m_j theta). NCS_E_STATE for contexts made from an operator.
+ */
+int ncs_get_onepatch(const ncs_ctx* ctx, double* trad, double* beta);
+
+/*
+ * Sets the patch layout: N >= 1 unit centres (N x 3 row-major, host, copied).
+ * Validates |c| = 1 (to 1e-10) and the geodesic separation >= 3 eps (Section 3)
+ * and, for the tree method, builds the cube-sphere quadtree, interaction lists and
+ * incoming grids on the host (Section 7, Step 2). Device copies are made at the
+ * next call that uses the GPU. Errors: NCS_E_INPUT (bad centre, separation), NCS_E_OOM.
+ */
+int ncs_set_patches(ncs_ctx* ctx, int64_t N, const double* centres);
+
+/* Selects NCS_METHOD_AUTO / DIRECT / TREE for later products and solves. */
+int ncs_set_method(ncs_ctx* ctx, int method);
+
+/*
+ * y = A x for the system of eq. (opinteqnsdisc): y_i = x_i + P sum_{j != i} S_ij B x_j,
+ * evaluated by the compressed representation (Section 7, Step 3). x, y: host,
+ * N*K doubles. precision: NCS_FP64 or NCS_FP32 (FP32 kernels, FP64 in/out).
+ */
+int ncs_matvec(ncs_ctx* ctx, const double* x, double* y, int precision);
+
+/* As ncs_matvec with device pointers x, y (N*K doubles) on the given stream
+ * (cudaStream_t, NULL = legacy default stream). Asynchronous. */
+int ncs_matvec_dev(ncs_ctx* ctx, const double* x, double* y, int precision, void* stream);
+
+/*
+ * The multiple-scattering field before the transform P (Section 7, end of Step 4):
+ * z_i(k) = sum_{j != i} [S_ij B x_j](k) at the Zernike sampling nodes, z: device,
+ * N*Kstar doubles, patch-major. Asynchronous on `stream`.
+ */
+int ncs_field_dev(ncs_ctx* ctx, const double* x, double* z, int precision, void* stream);
+
+/*
+ * Solves the system by GMRES (Section 7, Step 3; x0 = 0, relative residual tol).
+ * precision: NCS_FP64 (all FP64), NCS_FP32 (FP32 products, FP64 Arnoldi) or
+ * NCS_MIXED (FP32 inner GMRES wrapped in FP64 iterative refinement).
+ * Outputs (each may be NULL): fhat (N*K host doubles, the densities in the b_n
+ * basis, Remark sigrep), scalar = mean first passage time mu = 1/(3 I_sigma) - 3/5
+ * (interior, eq. mufromsigma2) or capacitance C = 4 pi I_sigma (exterior, |J|
+ * of Section 2.2), I_sigma (eq. getI), iterations (total products by A), and the
+ * final true relative residual. Errors: NCS_E_NOCONV (cap reached; outputs hold
+ * the last iterate), NCS_E_NUMERIC, NCS_E_STATE, NCS_E_CUDA.
+ */
+int ncs_solve(ncs_ctx* ctx, double tol, int precision, double* fhat, double* scalar,
+              double* Isigma, int* iterations, double* relres);
+
+/*
+ * Single-layer potential at M off-patch targets (Section 2, eqs. urep and
+ * intBVPansatz, off-surface Green's functions eqs. Gextoffsurface /
+ * Gintoffsurface): u(x) = sum_j sum_m G(x, s_jm) rho_jm with rho_j = T fhat_j.
+ * targets: M x 3 host (|x| >= 1 exterior, |x| <= 1 interior; each at least 2 eps
+ * in arclength of its radial projection from every patch centre); fhat: N*K host.
+ * out (M): exterior ubar = 1 - u; interior vbar = (v - 1)/(3D) + (1 - |x|^2)/6 with
+ * D = -I_sigma (eq. vtilde). Errors: NCS_E_INPUT for targets too close.
+ */
+int ncs_eval(ncs_ctx* ctx, int64_t M, const double* targets, const double* fhat, double* out);
+
+/* Message of the last failure on ctx (static string if ctx is NULL). */
+const char* ncs_last_error(const ncs_ctx* ctx);
+
+/* Releases all host and device memory of ctx (NULL is ignored). */
+void ncs_destroy(ncs_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NCS_H */

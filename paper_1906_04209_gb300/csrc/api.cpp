@@ -1,0 +1,741 @@
+// C ABI of the narrow capture / narrow escape solver (see include/ncs.h).
+// Host orchestration only: every step of the matrix-vector product and of the
+// Krylov iteration runs in the CUDA kernels of kernels.cu, tree.cu and blas.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <exception>
+#include <new>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "internal.hpp"
+
+using ncs::DeviceData;
+
+namespace {
+
+const char* g_static_err = "ncs: no context";
+
+struct Fail {
+  int code;
+  std::string msg;
+};
+
+#define CU(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess) throw Fail{e_ == cudaErrorMemoryAllocation ? NCS_E_OOM : NCS_E_CUDA, \
+                                      std::string(#call) + ": " + cudaGetErrorString(e_)};    \
+  } while (0)
+
+int log_level() {
+  static int lv = -1;
+  if (lv < 0) {
+    const char* e = std::getenv("NCS_LOG");
+    lv = e ? std::atoi(e) : 0;
+  }
+  return lv;
+}
+
+template <typename T>
+void dev_free(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+template <typename T>
+T* dev_upload(const std::vector<T>& h) {
+  T* p = nullptr;
+  CU(cudaMalloc(&p, std::max<size_t>(1, h.size()) * sizeof(T)));
+  if (!h.empty()) CU(cudaMemcpy(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return p;
+}
+
+template <typename T>
+T* dev_alloc(size_t n) {
+  T* p = nullptr;
+  CU(cudaMalloc(&p, std::max<size_t>(1, n) * sizeof(T)));
+  return p;
+}
+
+void free_layout(ncs_ctx* c) {
+  DeviceData& d = c->d;
+  dev_free(d.centres);
+  dev_free(d.soff64);
+  dev_free(d.soff32);
+  dev_free(d.rho64);
+  dev_free(d.rho32);
+  dev_free(d.z);
+  dev_free(c->V);
+  dev_free(c->work);
+  dev_free(c->partial);
+  dev_free(c->hdev);
+  c->Vcap = 0;
+  ncs::tree_free(c->tdev);
+  c->tree_built = false;
+  c->tree_uploaded = false;
+  c->tree = ncs::TreeHost();
+  d.N = 0;
+}
+
+void free_all(ncs_ctx* c) {
+  free_layout(c);
+  DeviceData& d = c->d;
+  dev_free(d.zloc);
+  dev_free(d.sloc);
+  dev_free(d.TT64);
+  dev_free(d.TT32);
+  dev_free(d.PT64);
+  dev_free(d.PT32);
+  dev_free(d.I);
+  if (c->stream) cudaStreamDestroy(c->stream);
+  c->stream = nullptr;
+}
+
+// Uploads the precompute (T, P transposed, node and skeleton offsets, I).
+void upload_operator(ncs_ctx* c) {
+  const ncs::Precomputed& pc = c->pc;
+  DeviceData& d = c->d;
+  d.K = pc.K;
+  d.Kstar = pc.Kstar;
+  d.p = pc.p;
+  std::vector<double> TT((size_t)pc.K * pc.p), PT((size_t)pc.Kstar * pc.K);
+  for (int m = 0; m < pc.p; ++m)
+    for (int k = 0; k < pc.K; ++k) TT[(size_t)k * pc.p + m] = pc.T[(size_t)m * pc.K + k];
+  for (int j = 0; j < pc.K; ++j)
+    for (int q = 0; q < pc.Kstar; ++q) PT[(size_t)q * pc.K + j] = pc.P[(size_t)j * pc.Kstar + q];
+  std::vector<float> TT32(TT.begin(), TT.end()), PT32(PT.begin(), PT.end());
+  d.TT64 = dev_upload(TT);
+  d.TT32 = dev_upload(TT32);
+  d.PT64 = dev_upload(PT);
+  d.PT32 = dev_upload(PT32);
+  d.zloc = dev_upload(pc.zloc);
+  d.sloc = dev_upload(pc.sloc);
+  d.I = dev_upload(pc.I);
+}
+
+int finish(ncs_ctx* c, const Fail& f) {
+  if (c) c->err = f.msg;
+  if (c && log_level() > 0) std::fprintf(stderr, "ncs: %s\n", f.msg.c_str());
+  return f.code;
+}
+
+// The device is bound at the first call that needs it; set-up (precompute, layout
+// validation, tree construction) is host-only.
+void ensure_device(ncs_ctx* c) {
+  if (c->device_ready) {
+    CU(cudaSetDevice(c->device));
+    return;
+  }
+  CU(cudaGetDevice(&c->device));
+  CU(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+  upload_operator(c);
+  c->device_ready = true;
+}
+
+void ensure_layout(ncs_ctx* c) {
+  if (!c->layout_dirty) return;
+  DeviceData& d = c->d;
+  const int64_t N = (int64_t)(c->centres.size() / 3);
+  d.centres = dev_upload(c->centres);
+  d.soff64 = dev_alloc<double>((size_t)N * d.p * 3);
+  d.soff32 = dev_alloc<float>((size_t)N * d.p * 3);
+  d.rho64 = dev_alloc<double>((size_t)N * d.p);
+  d.rho32 = dev_alloc<float>((size_t)N * d.p);
+  d.z = dev_alloc<double>((size_t)N * d.Kstar);
+  d.N = N;
+  CU(ncs::launch_skeleton_offsets(d, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  c->layout_dirty = false;
+}
+
+void check_ready(ncs_ctx* c) {
+  if (!c) throw Fail{NCS_E_INPUT, "null context"};
+  if (c->centres.empty()) throw Fail{NCS_E_STATE, "no patches: call ncs_set_patches first"};
+  ensure_device(c);
+  ensure_layout(c);
+}
+
+bool use_tree(const ncs_ctx* c) {
+  if (c->method == NCS_METHOD_TREE) return true;
+  if (c->method == NCS_METHOD_DIRECT) return false;
+  return (int64_t)(c->centres.size() / 3) >= c->prm.tree_min_patches;
+}
+
+// host part of the tree (Step 2 of Section 7)
+void ensure_tree_host(ncs_ctx* c) {
+  if (c->tree_built) return;
+  ncs::TreeOptions to;
+  to.grid_tol = c->prm.grid_tol;
+  to.eps = c->pc.eps;
+  ncs::tree_build(c->centres, c->pc, to, c->tree);
+  c->tree_built = true;
+}
+
+void ensure_tree(ncs_ctx* c) {
+  ensure_tree_host(c);
+  if (!c->tree_uploaded) {
+    ncs::tree_upload(c->tree, c->pc, c->tdev);
+    c->tree_uploaded = true;
+  }
+}
+
+// z = field of x at the Zernike nodes (before P), on stream s.
+void field(ncs_ctx* c, const double* x, int prec, cudaStream_t s) {
+  CU(ncs::launch_outgoing(c->d, x, prec, s));
+  if (use_tree(c)) {
+    ensure_tree(c);
+    CU(ncs::launch_tree_field(c->d, c->tdev, c->pc.mode, prec, s));
+  } else {
+    CU(ncs::launch_direct_field(c->d, c->pc.mode, prec, s));
+  }
+}
+
+void matvec(ncs_ctx* c, const double* x, double* y, int prec, cudaStream_t s) {
+  field(c, x, prec, s);
+  CU(ncs::launch_apply_P(c->d, x, y, s));
+}
+
+double dev_dot(ncs_ctx* c, const double* a, const double* b, cudaStream_t s) {
+  const int64_t n = c->d.N * c->d.K;
+  CU(ncs::launch_dots(n, 1, a, n, b, c->partial, c->hdev, s));
+  double h = 0.0;
+  CU(cudaMemcpyAsync(&h, c->hdev, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  return h;
+}
+
+void ensure_krylov(ncs_ctx* c, int maxit) {
+  const int64_t n = c->d.N * c->d.K;
+  if (c->Vcap < maxit + 1) {
+    dev_free(c->V);
+    c->V = dev_alloc<double>((size_t)(maxit + 1) * n);
+    c->Vcap = maxit + 1;
+    dev_free(c->partial);
+    dev_free(c->hdev);
+    c->partial = dev_alloc<double>((size_t)ncs::kDotChunks * (maxit + 2));
+    c->hdev = dev_alloc<double>(maxit + 2);
+  }
+  if (!c->work) c->work = dev_alloc<double>(5 * (size_t)n);
+}
+
+// GMRES (x0 = 0, no restart, CGS2 orthogonalisation on the device, Givens on the host)
+// for A e = r with products at precision `prec`. Returns the number of products and
+// the estimated relative residual; e receives the iterate.
+int gmres(ncs_ctx* c, const double* r, double* e, double tol, int prec, int maxit, double* est,
+          cudaStream_t s) {
+  const int64_t n = c->d.N * c->d.K;
+  double* w = c->work + 3 * n;
+  const double beta = std::sqrt(dev_dot(c, r, r, s));
+  CU(cudaMemsetAsync(e, 0, n * sizeof(double), s));
+  if (!(beta > 0.0)) {
+    if (!std::isfinite(beta)) throw Fail{NCS_E_NUMERIC, "GMRES: non-finite right-hand side"};
+    *est = 0.0;
+    return 0;
+  }
+  double* V = c->V;
+  CU(ncs::launch_scale_copy(n, r, 1.0 / beta, V, s));
+  std::vector<double> H((size_t)(maxit + 1) * maxit, 0.0), cs(maxit), sn(maxit), g(maxit + 1, 0.0);
+  std::vector<double> h(maxit + 2), h2(maxit + 2);
+  g[0] = beta;
+  int k = 0, m = 0;
+  double res = 1.0;
+  for (k = 0; k < maxit; ++k) {
+    matvec(c, V + (size_t)k * n, w, prec, s);
+    // classical Gram-Schmidt, twice
+    CU(ncs::launch_dots(n, k + 1, V, n, w, c->partial, c->hdev, s));
+    CU(cudaMemcpyAsync(h.data(), c->hdev, (k + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CU(ncs::launch_sub_combination(n, k + 1, V, n, c->hdev, w, -1.0, s));
+    CU(ncs::launch_dots(n, k + 1, V, n, w, c->partial, c->hdev, s));
+    CU(cudaMemcpyAsync(h2.data(), c->hdev, (k + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CU(ncs::launch_sub_combination(n, k + 1, V, n, c->hdev, w, -1.0, s));
+    const double hn = std::sqrt(dev_dot(c, w, w, s));  // synchronises the stream
+    for (int j = 0; j <= k; ++j) H[(size_t)j * maxit + k] = h[j] + h2[j];
+    H[(size_t)(k + 1) * maxit + k] = hn;
+    if (!std::isfinite(hn)) throw Fail{NCS_E_NUMERIC, "GMRES: non-finite Arnoldi vector"};
+    for (int j = 0; j < k; ++j) {
+      const double a = H[(size_t)j * maxit + k], b = H[(size_t)(j + 1) * maxit + k];
+      H[(size_t)j * maxit + k] = cs[j] * a + sn[j] * b;
+      H[(size_t)(j + 1) * maxit + k] = -sn[j] * a + cs[j] * b;
+    }
+    const double a = H[(size_t)k * maxit + k], b = H[(size_t)(k + 1) * maxit + k];
+    const double rr = std::hypot(a, b);
+    if (!(rr > 0.0)) throw Fail{NCS_E_NUMERIC, "GMRES: breakdown (zero Hessenberg column)"};
+    cs[k] = a / rr;
+    sn[k] = b / rr;
+    H[(size_t)k * maxit + k] = rr;
+    H[(size_t)(k + 1) * maxit + k] = 0.0;
+    g[k + 1] = -sn[k] * g[k];
+    g[k] = cs[k] * g[k];
+    res = std::fabs(g[k + 1]) / beta;
+    m = k + 1;
+    if (log_level() > 1) std::fprintf(stderr, "ncs: gmres it %d est %.3e\n", m, res);
+    if (res <= tol || hn == 0.0) break;
+    CU(ncs::launch_scale_copy(n, w, 1.0 / hn, V + (size_t)(k + 1) * n, s));
+  }
+  // y = H^-1 g, e = V y
+  std::vector<double> y(m);
+  for (int i = m - 1; i >= 0; --i) {
+    double t = g[i];
+    for (int j = i + 1; j < m; ++j) t -= H[(size_t)i * maxit + j] * y[j];
+    y[i] = t / H[(size_t)i * maxit + i];
+  }
+  CU(cudaMemcpyAsync(c->hdev, y.data(), m * sizeof(double), cudaMemcpyHostToDevice, s));
+  CU(ncs::launch_sub_combination(n, m, V, n, c->hdev, e, 1.0, s));
+  CU(cudaStreamSynchronize(s));
+  *est = res;
+  return m;
+}
+
+void validate_centres(int64_t N, const double* cen, double eps) {
+  if (N < 1) throw Fail{NCS_E_INPUT, "N must be >= 1"};
+  if (!cen) throw Fail{NCS_E_INPUT, "centres is NULL"};
+  for (int64_t i = 0; i < N; ++i) {
+    const double* c = cen + 3 * i;
+    const double r2 = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
+    if (!std::isfinite(r2) || std::fabs(r2 - 1.0) > 2e-10)
+      throw Fail{NCS_E_INPUT, "centre " + std::to_string(i) + " is not a unit vector"};
+  }
+  // geodesic separation >= 3 eps (Section 3), by a cell hash on chord distance
+  const double chord_min = 2.0 * std::sin(1.5 * eps) * (1.0 - 1e-9);
+  const double h = chord_min;
+  std::unordered_map<uint64_t, std::vector<int64_t>> cells;
+  cells.reserve((size_t)N * 2);
+  auto key = [h](double x, double y, double z) {
+    const int64_t a = (int64_t)std::floor(x / h) + (1 << 20), b = (int64_t)std::floor(y / h) + (1 << 20),
+                  cc = (int64_t)std::floor(z / h) + (1 << 20);
+    return ((uint64_t)a << 42) ^ ((uint64_t)b << 21) ^ (uint64_t)cc;
+  };
+  for (int64_t i = 0; i < N; ++i) cells[key(cen[3 * i], cen[3 * i + 1], cen[3 * i + 2])].push_back(i);
+  for (int64_t i = 0; i < N; ++i) {
+    const double* c = cen + 3 * i;
+    for (int dx = -1; dx <= 1; ++dx)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dz = -1; dz <= 1; ++dz) {
+          auto it = cells.find(key(c[0] + dx * h, c[1] + dy * h, c[2] + dz * h));
+          if (it == cells.end()) continue;
+          for (int64_t j : it->second) {
+            if (j <= i) continue;
+            const double* e = cen + 3 * j;
+            const double d2 = (c[0] - e[0]) * (c[0] - e[0]) + (c[1] - e[1]) * (c[1] - e[1]) +
+                              (c[2] - e[2]) * (c[2] - e[2]);
+            if (d2 < chord_min * chord_min)
+              throw Fail{NCS_E_INPUT, "patches " + std::to_string(i) + " and " + std::to_string(j) +
+                                          " are closer than 3 eps"};
+          }
+        }
+  }
+}
+
+ncs_ctx* new_ctx(const ncs_params* params) {
+  ncs_ctx* c = new (std::nothrow) ncs_ctx();
+  if (!c) throw Fail{NCS_E_OOM, "out of host memory"};
+  if (params)
+    c->prm = *params;
+  else
+    ncs_default_params(&c->prm);
+  c->method = c->prm.method;
+  return c;
+}
+
+void validate_params(const ncs_params& p) {
+  if (p.npan < 2 || p.npan > 40 || p.nord < 2 || p.nord > 64) throw Fail{NCS_E_INPUT, "bad panel parameters"};
+  if (!(p.id_tol > 0.0 && p.id_tol < 1e-2)) throw Fail{NCS_E_INPUT, "id_tol out of range"};
+  if (!(p.grid_tol > 0.0 && p.grid_tol < 1e-1)) throw Fail{NCS_E_INPUT, "grid_tol out of range"};
+  if (p.gmres_maxit < 1 || p.gmres_maxit > 2000) throw Fail{NCS_E_INPUT, "gmres_maxit out of range"};
+  if (p.method < 0 || p.method > 2) throw Fail{NCS_E_INPUT, "bad method"};
+}
+
+}  // namespace
+
+extern "C" {
+
+void ncs_default_params(ncs_params* p) {
+  if (!p) return;
+  p->npan = 13;
+  p->nord = 20;
+  p->ntheta_fine = 0;
+  p->id_tol = 1e-11;
+  p->threads = 0;
+  p->grid_tol = 1e-8;
+  p->method = NCS_METHOD_AUTO;
+  p->tree_min_patches = 2000;
+  p->gmres_maxit = 200;
+  p->verbose = 0;
+}
+
+int ncs_create(double eps, int mode, int K, const ncs_params* params, ncs_ctx** out) {
+  if (!out) return NCS_E_INPUT;
+  *out = nullptr;
+  ncs_ctx* c = nullptr;
+  try {
+    if (!(eps > 0.0 && eps < 1.0)) throw Fail{NCS_E_INPUT, "eps must be in (0, 1)"};
+    if (mode != NCS_EXTERIOR && mode != NCS_INTERIOR) throw Fail{NCS_E_INPUT, "mode must be 0 or 1"};
+    if (K < 1 || K > 2000) throw Fail{NCS_E_INPUT, "K must be in [1, 2000]"};
+    c = new_ctx(params);
+    validate_params(c->prm);
+    ncs::PrecomputeOptions o;
+    o.npan = c->prm.npan;
+    o.nord = c->prm.nord;
+    o.ntheta_fine = c->prm.ntheta_fine;
+    o.id_tol = c->prm.id_tol;
+    o.threads = c->prm.threads;
+    try {
+      ncs::precompute(eps, mode, K, o, c->pc);
+    } catch (const std::exception& e) {
+      throw Fail{NCS_E_NUMERIC, std::string("precompute: ") + e.what()};
+    }
+    if (log_level() > 0)
+      std::fprintf(stderr, "ncs: precompute eps=%g K=%d p=%d nf=%d (%.2fs + %.2fs)\n", eps, K, c->pc.p, c->pc.nf,
+                   c->pc.seconds_onepatch, c->pc.seconds_id);
+    *out = c;
+    return NCS_OK;
+  } catch (const Fail& f) {
+    if (c) {
+      free_all(c);
+      delete c;
+    }
+    if (log_level() > 0) std::fprintf(stderr, "ncs_create: %s\n", f.msg.c_str());
+    return f.code;
+  } catch (const std::bad_alloc&) {
+    if (c) {
+      free_all(c);
+      delete c;
+    }
+    return NCS_E_OOM;
+  }
+}
+
+int ncs_create_from_operator(double eps, int mode, int K, int p, const double* T, const double* skel_t,
+                             const double* skel_theta, const double* I, const ncs_params* params,
+                             ncs_ctx** out) {
+  if (!out) return NCS_E_INPUT;
+  *out = nullptr;
+  ncs_ctx* c = nullptr;
+  try {
+    if (!(eps > 0.0 && eps < 1.0)) throw Fail{NCS_E_INPUT, "eps must be in (0, 1)"};
+    if (mode != NCS_EXTERIOR && mode != NCS_INTERIOR) throw Fail{NCS_E_INPUT, "mode must be 0 or 1"};
+    if (K < 1 || K > 2000 || p < 1 || p > 100000) throw Fail{NCS_E_INPUT, "K or p out of range"};
+    if (!T || !skel_t || !skel_theta || !I) throw Fail{NCS_E_INPUT, "NULL operator array"};
+    c = new_ctx(params);
+    validate_params(c->prm);
+    c->from_operator = true;
+    ncs::precompute_zernike(eps, K, c->pc);
+    c->pc.mode = mode;
+    c->pc.p = p;
+    c->pc.T.assign(T, T + (size_t)p * K);
+    c->pc.st.assign(skel_t, skel_t + p);
+    c->pc.sth.assign(skel_theta, skel_theta + p);
+    c->pc.I.assign(I, I + K);
+    c->pc.sloc.resize(3 * (size_t)p);
+    for (int m = 0; m < p; ++m) {
+      if (!(skel_t[m] >= 0.0 && skel_t[m] <= eps)) throw Fail{NCS_E_INPUT, "skeleton t outside [0, eps]"};
+      ncs::local_offset(skel_t[m], skel_theta[m], &c->pc.sloc[3 * (size_t)m]);
+    }
+    for (size_t q = 0; q < c->pc.T.size(); ++q)
+      if (!std::isfinite(c->pc.T[q])) throw Fail{NCS_E_INPUT, "non-finite T"};
+    *out = c;
+    return NCS_OK;
+  } catch (const Fail& f) {
+    if (c) {
+      free_all(c);
+      delete c;
+    }
+    return f.code;
+  } catch (const std::bad_alloc&) {
+    if (c) {
+      free_all(c);
+      delete c;
+    }
+    return NCS_E_OOM;
+  }
+}
+
+int ncs_info(const ncs_ctx* c, int64_t* out, int n) {
+  if (!c || !out) return NCS_E_INPUT;
+  const int64_t v[11] = {c->pc.K,
+                         c->pc.Kstar,
+                         c->pc.p,
+                         c->pc.M,
+                         c->pc.nf,
+                         (int64_t)(c->centres.size() / 3),
+                         c->pc.nrad,
+                         c->tree_built ? (int64_t)c->tree.levels : 0,
+                         c->tree_built ? c->tree.total_grid_points : 0,
+                         c->tree_built ? c->tree.pairs_per_matvec : 0,
+                         (int64_t)(c->centres.size() / 3) * ((int64_t)(c->centres.size() / 3) - 1) *
+                             (int64_t)c->pc.p * c->pc.Kstar};
+  for (int i = 0; i < n && i < 11; ++i) out[i] = v[i];
+  return NCS_OK;
+}
+
+int ncs_timings(const ncs_ctx* c, double* out, int n) {
+  if (!c || !out) return NCS_E_INPUT;
+  if (n > 0) out[0] = c->pc.seconds_onepatch;
+  if (n > 1) out[1] = c->pc.seconds_id;
+  return NCS_OK;
+}
+
+int ncs_get_operator(const ncs_ctx* c, double* T, double* skel_t, double* skel_theta, double* I, double* P,
+                     double* zr, double* zth) {
+  if (!c) return NCS_E_INPUT;
+  const ncs::Precomputed& pc = c->pc;
+  if (T) std::memcpy(T, pc.T.data(), pc.T.size() * sizeof(double));
+  if (skel_t) std::memcpy(skel_t, pc.st.data(), pc.st.size() * sizeof(double));
+  if (skel_theta) std::memcpy(skel_theta, pc.sth.data(), pc.sth.size() * sizeof(double));
+  if (I) std::memcpy(I, pc.I.data(), pc.I.size() * sizeof(double));
+  if (P) std::memcpy(P, pc.P.data(), pc.P.size() * sizeof(double));
+  if (zr) std::memcpy(zr, pc.zr.data(), pc.zr.size() * sizeof(double));
+  if (zth) std::memcpy(zth, pc.zth.data(), pc.zth.size() * sizeof(double));
+  return NCS_OK;
+}
+
+int ncs_get_onepatch(const ncs_ctx* c, double* trad, double* beta) {
+  if (!c) return NCS_E_INPUT;
+  if (c->from_operator) return NCS_E_STATE;
+  if (trad) std::memcpy(trad, c->pc.trad.data(), c->pc.trad.size() * sizeof(double));
+  if (beta) std::memcpy(beta, c->pc.beta.data(), c->pc.beta.size() * sizeof(double));
+  return NCS_OK;
+}
+
+int ncs_set_patches(ncs_ctx* c, int64_t N, const double* centres) {
+  if (!c) return NCS_E_INPUT;
+  try {
+    validate_centres(N, centres, c->pc.eps);
+    if (c->device_ready) CU(cudaSetDevice(c->device));
+    free_layout(c);
+    c->centres.assign(centres, centres + 3 * N);
+    c->layout_dirty = true;
+    if (use_tree(c)) ensure_tree_host(c);
+    return NCS_OK;
+  } catch (const Fail& f) {
+    return finish(c, f);
+  } catch (const std::bad_alloc&) {
+    return finish(c, Fail{NCS_E_OOM, "out of host memory"});
+  } catch (const std::exception& e) {
+    return finish(c, Fail{NCS_E_INPUT, std::string("set_patches: ") + e.what()});
+  }
+}
+
+int ncs_set_method(ncs_ctx* c, int method) {
+  if (!c) return NCS_E_INPUT;
+  if (method < 0 || method > 2) return finish(c, Fail{NCS_E_INPUT, "bad method"});
+  c->method = method;
+  if (!c->centres.empty() && use_tree(c)) {
+    try {
+      ensure_tree_host(c);
+    } catch (const Fail& f) {
+      return finish(c, f);
+    } catch (const std::exception& e) {
+      return finish(c, Fail{NCS_E_INPUT, std::string("tree: ") + e.what()});
+    }
+  }
+  return NCS_OK;
+}
+
+int ncs_matvec_dev(ncs_ctx* c, const double* x, double* y, int precision, void* stream) {
+  try {
+    if (!c) throw Fail{NCS_E_INPUT, "null context"};
+    if (!x || !y) throw Fail{NCS_E_INPUT, "NULL vector"};
+    if (precision != NCS_FP64 && precision != NCS_FP32) throw Fail{NCS_E_INPUT, "precision must be FP64 or FP32"};
+    check_ready(c);
+    matvec(c, x, y, precision, (cudaStream_t)stream);
+    return NCS_OK;
+  } catch (const Fail& f) {
+    return finish(c, f);
+  } catch (const std::exception& e) {
+    return finish(c, Fail{NCS_E_INPUT, e.what()});
+  }
+}
+
+int ncs_field_dev(ncs_ctx* c, const double* x, double* z, int precision, void* stream) {
+  try {
+    if (!c) throw Fail{NCS_E_INPUT, "null context"};
+    if (!x || !z) throw Fail{NCS_E_INPUT, "NULL vector"};
+    if (precision != NCS_FP64 && precision != NCS_FP32) throw Fail{NCS_E_INPUT, "precision must be FP64 or FP32"};
+    check_ready(c);
+    cudaStream_t s = (cudaStream_t)stream;
+    field(c, x, precision, s);
+    CU(cudaMemcpyAsync(z, c->d.z, (size_t)c->d.N * c->d.Kstar * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    return NCS_OK;
+  } catch (const Fail& f) {
+    return finish(c, f);
+  } catch (const std::exception& e) {
+    return finish(c, Fail{NCS_E_INPUT, e.what()});
+  }
+}
+
+int ncs_matvec(ncs_ctx* c, const double* x, double* y, int precision) {
+  try {
+    if (!c) throw Fail{NCS_E_INPUT, "null context"};
+    if (!x || !y) throw Fail{NCS_E_INPUT, "NULL vector"};
+    if (precision != NCS_FP64 && precision != NCS_FP32) throw Fail{NCS_E_INPUT, "precision must be FP64 or FP32"};
+    check_ready(c);
+    ensure_krylov(c, 1);
+    const int64_t n = c->d.N * c->d.K;
+    CU(cudaMemcpyAsync(c->work, x, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    matvec(c, c->work, c->work + n, precision, c->stream);
+    CU(cudaMemcpyAsync(y, c->work + n, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    return NCS_OK;
+  } catch (const Fail& f) {
+    return finish(c, f);
+  } catch (const std::exception& e) {
+    return finish(c, Fail{NCS_E_INPUT, e.what()});
+  }
+}
+
+int ncs_solve(ncs_ctx* c, double tol, int precision, double* fhat, double* scalar, double* Isigma, int* iterations,
+              double* relres) {
+  try {
+    if (!c) throw Fail{NCS_E_INPUT, "null context"};
+    if (!(tol > 0.0 && tol < 1.0)) throw Fail{NCS_E_INPUT, "tol must be in (0, 1)"};
+    if (precision != NCS_FP64 && precision != NCS_FP32 && precision != NCS_MIXED)
+      throw Fail{NCS_E_INPUT, "bad precision"};
+    check_ready(c);
+    const int maxit = c->prm.gmres_maxit;
+    ensure_krylov(c, maxit);
+    const int64_t n = c->d.N * c->d.K;
+    cudaStream_t s = c->stream;
+    double* b = c->work;           // right-hand side P 1
+    double* x = c->work + n;       // solution
+    double* r = c->work + 2 * n;   // residual / correction
+    // b_i = P 1 for every patch (eq. opinteqnsdisc)
+    {
+      std::vector<double> P1(c->d.K, 0.0);
+      for (int j = 0; j < c->d.K; ++j)
+        for (int q = 0; q < c->d.Kstar; ++q) P1[j] += c->pc.P[(size_t)j * c->d.Kstar + q];
+      std::vector<double> bh((size_t)n);
+      for (int64_t i = 0; i < c->d.N; ++i) std::memcpy(&bh[(size_t)i * c->d.K], P1.data(), c->d.K * sizeof(double));
+      CU(cudaMemcpyAsync(b, bh.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
+      CU(cudaStreamSynchronize(s));
+    }
+    const double bnorm = std::sqrt(dev_dot(c, b, b, s));
+    int total = 0;
+    double est = 1.0, rel = 1.0;
+    bool converged = false;
+    if (precision != NCS_MIXED) {
+      total = gmres(c, b, x, tol, precision, maxit, &est, s);
+      // true residual r = b - A x
+      matvec(c, x, r, precision, s);
+      CU(ncs::launch_axpby(n, 1.0, b, -1.0, r, s));
+      rel = std::sqrt(dev_dot(c, r, r, s)) / bnorm;
+      ++total;
+      converged = est <= tol;
+    } else {
+      // iterative refinement: FP32 inner GMRES, FP64 residuals
+      double* corr = c->work + 4 * n;
+      CU(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+      CU(cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      rel = 1.0;
+      for (int outer = 0; outer < 20; ++outer) {
+        if (rel <= tol) break;
+        const double inner_tol = std::max(0.3 * tol / rel, 3e-6);
+        double inner_est = 1.0;
+        total += gmres(c, r, corr, std::min(inner_tol, 0.5), NCS_FP32, maxit, &inner_est, s);
+        CU(ncs::launch_axpby(n, 1.0, corr, 1.0, x, s));
+        matvec(c, x, r, NCS_FP64, s);
+        CU(ncs::launch_axpby(n, 1.0, b, -1.0, r, s));
+        ++total;
+        const double newrel = std::sqrt(dev_dot(c, r, r, s)) / bnorm;
+        if (log_level() > 0) std::fprintf(stderr, "ncs: refinement %d relres %.3e\n", outer, newrel);
+        if (!std::isfinite(newrel)) throw Fail{NCS_E_NUMERIC, "refinement: non-finite residual"};
+        const bool stalled = newrel > 0.9 * rel && outer > 0;
+        rel = newrel;
+        if (stalled) break;
+      }
+      converged = rel <= tol;
+    }
+    // I_sigma = I . sum_i f_i (eq. getI), then mu or C
+    CU(ncs::launch_periodic_dot(n, c->d.K, x, c->d.I, c->partial, c->hdev, s));
+    double Is = 0.0;
+    CU(cudaMemcpyAsync(&Is, c->hdev, sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (fhat) CU(cudaMemcpyAsync(fhat, x, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (Isigma) *Isigma = Is;
+    if (scalar) *scalar = (c->pc.mode == NCS_INTERIOR) ? 1.0 / (3.0 * Is) - 0.6 : 4.0 * M_PI * Is;
+    if (iterations) *iterations = total;
+    if (relres) *relres = rel;
+    if (!converged) throw Fail{NCS_E_NOCONV, "GMRES: tolerance not reached within the iteration cap"};
+    return NCS_OK;
+  } catch (const Fail& f) {
+    return finish(c, f);
+  } catch (const std::exception& e) {
+    return finish(c, Fail{NCS_E_INPUT, e.what()});
+  }
+}
+
+int ncs_eval(ncs_ctx* c, int64_t M, const double* targets, const double* fhat, double* out) {
+  try {
+    check_ready(c);
+    if (M < 0 || (M > 0 && (!targets || !out)) || !fhat) throw Fail{NCS_E_INPUT, "bad eval arguments"};
+    const double eps = c->pc.eps;
+    // every target's radial projection must be >= 2 eps from each centre (far region of Section 7.1)
+    for (int64_t t = 0; t < M; ++t) {
+      const double* x = targets + 3 * t;
+      const double r = std::sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+      if (!(r > 0.0) || !std::isfinite(r)) throw Fail{NCS_E_INPUT, "bad target"};
+      if (c->pc.mode == NCS_EXTERIOR && r < 1.0 - 1e-12) throw Fail{NCS_E_INPUT, "exterior target inside the sphere"};
+      if (c->pc.mode == NCS_INTERIOR && r > 1.0 + 1e-12) throw Fail{NCS_E_INPUT, "interior target outside the sphere"};
+      for (int64_t j = 0; j < c->d.N; ++j) {
+        const double* cc = &c->centres[3 * j];
+        const double dot = (x[0] * cc[0] + x[1] * cc[1] + x[2] * cc[2]) / r;
+        if (std::acos(std::max(-1.0, std::min(1.0, dot))) < 2.0 * eps)
+          throw Fail{NCS_E_INPUT, "target " + std::to_string(t) + " within 2 eps of patch " + std::to_string(j)};
+      }
+    }
+    const int64_t n = c->d.N * c->d.K;
+    ensure_krylov(c, 1);
+    cudaStream_t s = c->stream;
+    double *dt = nullptr, *dout = nullptr;
+    CU(cudaMalloc(&dt, std::max<int64_t>(1, 3 * M) * sizeof(double)));
+    CU(cudaMalloc(&dout, std::max<int64_t>(1, M) * sizeof(double)));
+    try {
+      CU(cudaMemcpyAsync(c->work, fhat, n * sizeof(double), cudaMemcpyHostToDevice, s));
+      if (M) CU(cudaMemcpyAsync(dt, targets, 3 * M * sizeof(double), cudaMemcpyHostToDevice, s));
+      CU(ncs::launch_outgoing(c->d, c->work, NCS_FP64, s));
+      CU(ncs::launch_eval(c->d, c->pc.mode, M, dt, dout, s));
+      CU(ncs::launch_periodic_dot(n, c->d.K, c->work, c->d.I, c->partial, c->hdev, s));
+      double Is = 0.0;
+      CU(cudaMemcpyAsync(&Is, c->hdev, sizeof(double), cudaMemcpyDeviceToHost, s));
+      if (M) CU(cudaMemcpyAsync(out, dout, M * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CU(cudaStreamSynchronize(s));
+      for (int64_t t = 0; t < M; ++t) {
+        const double* x = targets + 3 * t;
+        const double r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+        if (c->pc.mode == NCS_EXTERIOR)
+          out[t] = 1.0 - out[t];  // ubar = 1 - u (Section 2.2)
+        else
+          out[t] = (out[t] - 1.0) / (3.0 * (-Is)) + (1.0 - r2) / 6.0;  // eq. (vtilde), D = -I_sigma
+      }
+    } catch (...) {
+      cudaFree(dt);
+      cudaFree(dout);
+      throw;
+    }
+    cudaFree(dt);
+    cudaFree(dout);
+    return NCS_OK;
+  } catch (const Fail& f) {
+    return finish(c, f);
+  } catch (const std::exception& e) {
+    return finish(c, Fail{NCS_E_INPUT, e.what()});
+  }
+}
+
+const char* ncs_last_error(const ncs_ctx* c) { return c ? c->err.c_str() : g_static_err; }
+
+void ncs_destroy(ncs_ctx* c) {
+  if (!c) return;
+  if (c->device_ready) cudaSetDevice(c->device);
+  free_all(c);
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,59 @@
+// Device helpers shared by the kernels: patch frames and the on-surface Neumann
+// Green's functions of the unit sphere (Kaye & Greengard, Section 2.1).
+#pragma once
+#include <cuda_runtime.h>
+
+namespace ncs {
+
+constexpr double kLn4 = 1.3862943611198906188;
+constexpr float kLn2f = 0.69314718055994530942f;
+constexpr float kLn4f = 1.3862943611198906188f;
+
+// Patch frame for unit centre c: e1 = (z x c)/|z x c| (x-axis at the poles), e2 = c x e1.
+__device__ __forceinline__ void patch_frame(double cx, double cy, double cz, double* e1, double* e2) {
+  const double ax = -cy, ay = cx, na2 = ax * ax + ay * ay;
+  if (na2 >= 1e-24) {
+    const double inv = 1.0 / sqrt(na2);
+    e1[0] = ax * inv;
+    e1[1] = ay * inv;
+    e1[2] = 0.0;
+  } else {
+    e1[0] = 1.0;
+    e1[1] = 0.0;
+    e1[2] = 0.0;
+  }
+  e2[0] = cy * e1[2] - cz * e1[1];
+  e2[1] = cz * e1[0] - cx * e1[2];
+  e2[2] = cx * e1[1] - cy * e1[0];
+}
+
+// Global offset of a local offset (o0, o1, o2) in the frame (e1, e2, c).
+__device__ __forceinline__ void frame_apply(const double* e1, const double* e2, double cx, double cy,
+                                            double cz, double o0, double o1, double o2, double* g) {
+  g[0] = o0 * e1[0] + o1 * e2[0] + o2 * cx;
+  g[1] = o0 * e1[1] + o1 * e2[1] + o2 * cy;
+  g[2] = o0 * e1[2] + o1 * e2[2] + o2 * cz;
+}
+
+// G(d) from d^2, eqs. (Gextonsurface) / (Gintonsurface), one logarithm each:
+//   exterior: G_E = u - log(1 + u),           u = 2/d
+//   interior: G_I = u + log 4 - log(d^2 + 2d)
+template <int MODE>
+__device__ __forceinline__ double green64(double d2) {
+  const double rinv = rsqrt(d2);
+  const double u = 2.0 * rinv;
+  if (MODE == 0) return u - log1p(u);
+  const double d = d2 * rinv;
+  return u + kLn4 - log(fma(2.0, d, d2));
+}
+
+template <int MODE>
+__device__ __forceinline__ float green32(float d2) {
+  const float rinv = rsqrtf(d2);
+  const float u = 2.0f * rinv;
+  if (MODE == 0) return u - kLn2f * __log2f(1.0f + u);
+  const float d = d2 * rinv;
+  return u + kLn4f - kLn2f * __log2f(fmaf(2.0f, d, d2));
+}
+
+}  // namespace ncs

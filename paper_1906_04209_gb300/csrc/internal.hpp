@@ -1,0 +1,79 @@
+// Internal declarations shared by the host API and the CUDA launchers.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "ncs.h"
+#include "precompute.hpp"
+#include "tree.hpp"
+
+namespace ncs {
+
+// Device-resident data of one patch layout plus the precompute.
+struct DeviceData {
+  int K = 0, Kstar = 0, p = 0;
+  int64_t N = 0;
+  double* centres = nullptr;   // N*3
+  double* zloc = nullptr;      // Kstar*3 local offsets of the Zernike nodes
+  double* sloc = nullptr;      // p*3 local offsets of the skeleton points
+  double* TT64 = nullptr;      // K*p, T transposed
+  float* TT32 = nullptr;
+  double* PT64 = nullptr;      // Kstar*K, P transposed
+  float* PT32 = nullptr;
+  double* soff64 = nullptr;    // N*p*3 skeleton offsets (global frame) from each centre
+  float* soff32 = nullptr;
+  double* rho64 = nullptr;     // N*p outgoing coefficients
+  float* rho32 = nullptr;
+  double* z = nullptr;         // N*Kstar field at the Zernike nodes
+  double* I = nullptr;         // K
+};
+
+// ---- launchers (kernels.cu)
+cudaError_t launch_skeleton_offsets(const DeviceData& d, cudaStream_t s);
+cudaError_t launch_outgoing(const DeviceData& d, const double* x, int prec, cudaStream_t s);
+cudaError_t launch_direct_field(const DeviceData& d, int mode, int prec, cudaStream_t s);
+cudaError_t launch_apply_P(const DeviceData& d, const double* x, double* y, cudaStream_t s);
+cudaError_t launch_eval(const DeviceData& d, int mode, int64_t M, const double* targets,
+                        double* out, cudaStream_t s);
+
+// ---- dense-vector kernels for GMRES (blas.cu)
+cudaError_t launch_dots(int64_t n, int k, const double* V, int64_t ld, const double* w,
+                        double* partial, double* out, cudaStream_t s);
+cudaError_t launch_sub_combination(int64_t n, int k, const double* V, int64_t ld, const double* h,
+                                   double* w, double sign, cudaStream_t s);
+cudaError_t launch_scale_copy(int64_t n, const double* w, double a, double* v, cudaStream_t s);
+cudaError_t launch_axpby(int64_t n, double a, const double* x, double b, double* y, cudaStream_t s);
+cudaError_t launch_nonfinite_count(int64_t n, const double* x, int* out, cudaStream_t s);
+cudaError_t launch_periodic_dot(int64_t n, int K, const double* x, const double* I, double* partial,
+                                double* out, cudaStream_t s);
+constexpr int kDotChunks = 64;
+
+}  // namespace ncs
+
+// The opaque context of the C ABI.
+struct ncs_ctx {
+  ncs_params prm{};
+  ncs::Precomputed pc;
+  bool from_operator = false;
+  std::string err;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<double> centres;
+  int method = NCS_METHOD_AUTO;
+  ncs::DeviceData d;
+  ncs::TreeHost tree;
+  ncs::TreeDevice tdev;
+  bool tree_built = false;      // host tree ready
+  bool tree_uploaded = false;   // device copy ready
+  bool device_ready = false;    // operator uploaded, stream created
+  bool layout_dirty = false;    // centres changed since the last upload
+  // GMRES workspace
+  double* V = nullptr;
+  int Vcap = 0;
+  double* work = nullptr;      // 4 vectors of N*K
+  double* partial = nullptr;   // kDotChunks * (maxit+2)
+  double* hdev = nullptr;      // maxit+2
+};

@@ -1,0 +1,276 @@
+// Hot-path kernels of the direct (no tree) matrix-vector product of Kaye & Greengard,
+// Section 6 eq. (opinteqnsdisc) with the compressed outgoing representation of
+// Section 7.1:
+//   rho_j = T f_j                                      (eq. Tmap, Step 3.1)
+//   z_i(k) = sum_{j != i} sum_m G(x^z_{i,k}, x_{j,pi(m)}) rho_{j,m}   (Section 7.1)
+//   y_i = f_i + P z_i                                  (Step 3.5)
+// and the single-layer potential at off-surface targets (Section 2, eqs. urep,
+// intBVPansatz with eqs. Gextoffsurface / Gintoffsurface).
+#include <cstdint>
+
+#include "device_common.cuh"
+#include "internal.hpp"
+
+namespace ncs {
+
+template <typename R>
+struct Vec4;
+template <>
+struct Vec4<float> {
+  using type = float4;
+};
+template <>
+struct Vec4<double> {
+  using type = double4;
+};
+
+// ---------------------------------------------------------------------------
+// Skeleton offsets s_{j,m} - c_j in the global frame (FP64 and an FP32 copy).
+__global__ void skeleton_offsets_kernel(int64_t N, int p, const double* __restrict__ centres,
+                                        const double* __restrict__ sloc, double* __restrict__ soff64,
+                                        float* __restrict__ soff32) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= N * p) return;
+  const int64_t j = idx / p;
+  const int m = (int)(idx % p);
+  const double cx = centres[3 * j], cy = centres[3 * j + 1], cz = centres[3 * j + 2];
+  double e1[3], e2[3], g[3];
+  patch_frame(cx, cy, cz, e1, e2);
+  frame_apply(e1, e2, cx, cy, cz, sloc[3 * m], sloc[3 * m + 1], sloc[3 * m + 2], g);
+  for (int c = 0; c < 3; ++c) {
+    soff64[3 * idx + c] = g[c];
+    soff32[3 * idx + c] = (float)g[c];
+  }
+}
+
+cudaError_t launch_skeleton_offsets(const DeviceData& d, cudaStream_t s) {
+  const int64_t n = d.N * d.p;
+  const int th = 256;
+  skeleton_offsets_kernel<<<(unsigned)((n + th - 1) / th), th, 0, s>>>(d.N, d.p, d.centres, d.sloc,
+                                                                       d.soff64, d.soff32);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Step 3.1: rho_i = T f_i for PB patches per block; TT is T transposed (K x p) so
+// that consecutive threads read consecutive skeleton rows.
+constexpr int OG_PB = 8;
+
+template <typename R>
+__global__ void __launch_bounds__(256) outgoing_kernel(int64_t N, int p, int K, const R* __restrict__ TT,
+                                                       const double* __restrict__ x, R* __restrict__ rho) {
+  extern __shared__ unsigned char og_smem[];
+  R* xs = reinterpret_cast<R*>(og_smem);  // OG_PB x K
+  const int64_t i0 = (int64_t)blockIdx.x * OG_PB;
+  const int np = (int)min((int64_t)OG_PB, N - i0);
+  for (int idx = threadIdx.x; idx < np * K; idx += blockDim.x) xs[idx] = (R)x[i0 * K + idx];
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < np * p; idx += blockDim.x) {
+    const int ii = idx / p, m = idx - ii * p;
+    const R* xr = xs + ii * K;
+    R acc = 0;
+    for (int k = 0; k < K; ++k) acc = fma(TT[(int64_t)k * p + m], xr[k], acc);
+    rho[(i0 + ii) * p + m] = acc;
+  }
+}
+
+cudaError_t launch_outgoing(const DeviceData& d, const double* x, int prec, cudaStream_t s) {
+  const unsigned blocks = (unsigned)((d.N + OG_PB - 1) / OG_PB);
+  if (prec == NCS_FP64)
+    outgoing_kernel<double><<<blocks, 256, OG_PB * d.K * sizeof(double), s>>>(d.N, d.p, d.K, d.TT64, x,
+                                                                                d.rho64);
+  else
+    outgoing_kernel<float><<<blocks, 256, OG_PB * d.K * sizeof(float), s>>>(d.N, d.p, d.K, d.TT32, x,
+                                                                              d.rho32);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Direct far-field sums at the Zernike nodes (Section 7.1, without the tree).
+// One block row per target patch i; each thread owns DF_NT target nodes. Source
+// patches are staged JT at a time in shared memory as (offset from c_i, rho)
+// quadruples; the self patch gets rho = 0 at a distant dummy position. Offsets are
+// formed in FP64 (c_j - c_i) before rounding, so the FP32 path keeps relative
+// accuracy even for neighbours 2 eps apart. FP32 partial sums are folded into an
+// FP64 accumulator once per tile.
+constexpr int DF_THREADS = 256;
+constexpr int DF_NT = 2;
+constexpr int DF_JTMAX = 8;
+
+template <typename R, int MODE>
+__global__ void __launch_bounds__(DF_THREADS) direct_field_kernel(
+    int64_t N, int p, int Kstar, int JT, const double* __restrict__ centres,
+    const double* __restrict__ zloc, const R* __restrict__ soff, const R* __restrict__ rho,
+    double* __restrict__ z) {
+  using V4 = typename Vec4<R>::type;
+  extern __shared__ unsigned char df_smem[];
+  V4* S = reinterpret_cast<V4*>(df_smem);  // JT * p
+  __shared__ double D[DF_JTMAX][3];
+  const int64_t i = blockIdx.x;
+  const double cx = centres[3 * i], cy = centres[3 * i + 1], cz = centres[3 * i + 2];
+  double e1[3], e2[3];
+  patch_frame(cx, cy, cz, e1, e2);
+  R ax[DF_NT], ay[DF_NT], az[DF_NT];
+  double acc[DF_NT];
+  int kk[DF_NT];
+#pragma unroll
+  for (int t = 0; t < DF_NT; ++t) {
+    kk[t] = (blockIdx.y * DF_NT + t) * DF_THREADS + threadIdx.x;
+    double g[3] = {0.0, 0.0, 0.0};
+    if (kk[t] < Kstar) frame_apply(e1, e2, cx, cy, cz, zloc[3 * kk[t]], zloc[3 * kk[t] + 1], zloc[3 * kk[t] + 2], g);
+    ax[t] = (R)g[0];
+    ay[t] = (R)g[1];
+    az[t] = (R)g[2];
+    acc[t] = 0.0;
+  }
+  for (int64_t j0 = 0; j0 < N; j0 += JT) {
+    const int nj = (int)min((int64_t)JT, N - j0);
+    if (threadIdx.x < nj * 3) {
+      const int jj = threadIdx.x / 3, c = threadIdx.x - 3 * jj;
+      D[jj][c] = centres[3 * (j0 + jj) + c] - centres[3 * i + c];
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nj * p; idx += DF_THREADS) {
+      const int jj = idx / p;
+      const int64_t j = j0 + jj;
+      const int64_t g = j * p + (idx - jj * p);
+      V4 v;
+      if (j != i) {
+        v.x = (R)D[jj][0] + soff[3 * g];
+        v.y = (R)D[jj][1] + soff[3 * g + 1];
+        v.z = (R)D[jj][2] + soff[3 * g + 2];
+        v.w = rho[g];
+      } else {
+        v.x = (R)4;
+        v.y = (R)4;
+        v.z = (R)4;
+        v.w = (R)0;
+      }
+      S[idx] = v;
+    }
+    __syncthreads();
+    const int ns = nj * p;
+    R part[DF_NT];
+#pragma unroll
+    for (int t = 0; t < DF_NT; ++t) part[t] = 0;
+    for (int s = 0; s < ns; ++s) {
+      const V4 v = S[s];
+#pragma unroll
+      for (int t = 0; t < DF_NT; ++t) {
+        const R dx = ax[t] - v.x, dy = ay[t] - v.y, dz = az[t] - v.z;
+        const R d2 = fma(dx, dx, fma(dy, dy, dz * dz));
+        R gval;
+        if constexpr (sizeof(R) == 8)
+          gval = green64<MODE>(d2);
+        else
+          gval = green32<MODE>(d2);
+        part[t] = fma(gval, v.w, part[t]);
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < DF_NT; ++t) acc[t] += (double)part[t];
+    __syncthreads();
+  }
+#pragma unroll
+  for (int t = 0; t < DF_NT; ++t)
+    if (kk[t] < Kstar) z[i * Kstar + kk[t]] = acc[t];
+}
+
+cudaError_t launch_direct_field(const DeviceData& d, int mode, int prec, cudaStream_t s) {
+  const size_t v4 = (prec == NCS_FP64) ? sizeof(double4) : sizeof(float4);
+  int JT = (int)std::min<size_t>(DF_JTMAX, (40 * 1024) / (v4 * (size_t)d.p));
+  if (JT < 1) JT = 1;
+  const size_t smem = (size_t)JT * d.p * v4;
+  dim3 grid((unsigned)d.N, (unsigned)((d.Kstar + DF_THREADS * DF_NT - 1) / (DF_THREADS * DF_NT)));
+  if (prec == NCS_FP64) {
+    if (mode == 0)
+      direct_field_kernel<double, 0><<<grid, DF_THREADS, smem, s>>>(d.N, d.p, d.Kstar, JT, d.centres, d.zloc,
+                                                                    d.soff64, d.rho64, d.z);
+    else
+      direct_field_kernel<double, 1><<<grid, DF_THREADS, smem, s>>>(d.N, d.p, d.Kstar, JT, d.centres, d.zloc,
+                                                                    d.soff64, d.rho64, d.z);
+  } else {
+    if (mode == 0)
+      direct_field_kernel<float, 0><<<grid, DF_THREADS, smem, s>>>(d.N, d.p, d.Kstar, JT, d.centres, d.zloc,
+                                                                   d.soff32, d.rho32, d.z);
+    else
+      direct_field_kernel<float, 1><<<grid, DF_THREADS, smem, s>>>(d.N, d.p, d.Kstar, JT, d.centres, d.zloc,
+                                                                   d.soff32, d.rho32, d.z);
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Step 3.5: y_i = x_i + P z_i. PT is P transposed (Kstar x K).
+constexpr int AP_PB = 4;
+
+__global__ void __launch_bounds__(256) apply_P_kernel(int64_t N, int K, int Kstar, const double* __restrict__ PT,
+                                                      const double* __restrict__ z, const double* __restrict__ x,
+                                                      double* __restrict__ y) {
+  extern __shared__ unsigned char ap_smem[];
+  double* zs = reinterpret_cast<double*>(ap_smem);  // AP_PB x Kstar
+  const int64_t i0 = (int64_t)blockIdx.x * AP_PB;
+  const int np = (int)min((int64_t)AP_PB, N - i0);
+  for (int idx = threadIdx.x; idx < np * Kstar; idx += blockDim.x) zs[idx] = z[i0 * Kstar + idx];
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < np * K; idx += blockDim.x) {
+    const int ii = idx / K, j = idx - ii * K;
+    const double* zr = zs + ii * Kstar;
+    double acc = 0.0;
+    for (int q = 0; q < Kstar; ++q) acc = fma(PT[(int64_t)q * K + j], zr[q], acc);
+    y[(i0 + ii) * K + j] = x[(i0 + ii) * K + j] + acc;
+  }
+}
+
+cudaError_t launch_apply_P(const DeviceData& d, const double* x, double* y, cudaStream_t s) {
+  const unsigned blocks = (unsigned)((d.N + AP_PB - 1) / AP_PB);
+  apply_P_kernel<<<blocks, 256, AP_PB * d.Kstar * sizeof(double), s>>>(d.N, d.K, d.Kstar, d.PT64, d.z, x, y);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Off-surface single-layer potential u(x) = sum_j sum_m G(x, s_jm) rho_jm, FP64,
+// one block per target with a block reduction.
+template <int MODE>
+__global__ void __launch_bounds__(256) eval_kernel(int64_t N, int p, const double* __restrict__ centres,
+                                                   const double* __restrict__ soff, const double* __restrict__ rho,
+                                                   const double* __restrict__ targets, double* __restrict__ out) {
+  __shared__ double red[256];
+  const int64_t t = blockIdx.x;
+  const double x0 = targets[3 * t], x1 = targets[3 * t + 1], x2 = targets[3 * t + 2];
+  const double rx = sqrt(x0 * x0 + x1 * x1 + x2 * x2);
+  double acc = 0.0;
+  for (int64_t g = threadIdx.x; g < N * p; g += blockDim.x) {
+    const int64_t j = g / p;
+    const double s0 = centres[3 * j] + soff[3 * g], s1 = centres[3 * j + 1] + soff[3 * g + 1],
+                 s2 = centres[3 * j + 2] + soff[3 * g + 2];
+    const double d0 = x0 - s0, d1 = x1 - s1, d2 = x2 - s2;
+    const double d = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+    const double xx = x0 * s0 + x1 * s1 + x2 * s2;
+    double gval;
+    if (MODE == 0)
+      gval = 2.0 / d + log((rx - xx) / (1.0 - xx + d));  // eq. (Gextoffsurface)
+    else
+      gval = 2.0 / d + log(2.0 / (1.0 - xx + d));  // eq. (Gintoffsurface)
+    acc = fma(gval, rho[g], acc);
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[t] = red[0];
+}
+
+cudaError_t launch_eval(const DeviceData& d, int mode, int64_t M, const double* targets, double* out,
+                        cudaStream_t s) {
+  if (M == 0) return cudaSuccess;
+  if (mode == 0)
+    eval_kernel<0><<<(unsigned)M, 256, 0, s>>>(d.N, d.p, d.centres, d.soff64, d.rho64, targets, out);
+  else
+    eval_kernel<1><<<(unsigned)M, 256, 0, s>>>(d.N, d.p, d.centres, d.soff64, d.rho64, targets, out);
+  return cudaGetLastError();
+}
+
+}  // namespace ncs

@@ -1,0 +1,599 @@
+// One-patch precompute for the narrow capture / escape solver (Kaye & Greengard):
+//   * Zernike basis, sampling nodes and the discrete transform P (Section 4, Section 6);
+//   * modal reduction of the one-patch equation (Section 8, eq. modalinteqn), with the
+//     modal kernel split as G_n = G^(1) + s G^(2) - G^(3), s = -1 exterior, +1 interior
+//     (from the on-surface forms eqs. Gextonsurface / Gintonsurface);
+//       G^(1): Coulomb kernel, written through the Legendre function of half-integer
+//              degree Q_{n-1/2}(chi) (toroidal function), evaluated from complete elliptic
+//              integrals and the three-term recurrence (forward near chi = 1, Miller's
+//              backward recurrence otherwise);
+//       G^(2): the closed form printed in Section 8.1;
+//       G^(3): graded Gauss quadrature in theta;
+//   * dyadic panels refined toward t = eps with a Gauss-Jacobi (alpha=-1/2, beta=0) last
+//     panel, collocation, one LU per mode (Section 8.2);
+//   * fine grid, weights w, B and I = w^T B (Section 5, eq. getI);
+//   * interpolative decomposition of the far field by a Gaussian sketch followed by
+//     column-pivoted Householder QR, T = Pi W B (Section 7.1, eq. Tmap).
+#include "precompute.hpp"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <stdexcept>
+
+#include "numerics.hpp"
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace ncs {
+
+namespace {
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+double jacobi_value(int n, double a, double b, double x) {
+  double p0 = 1.0, p1 = 0.5 * (a - b + (a + b + 2.0) * x);
+  if (n == 0) return 1.0;
+  for (int k = 2; k <= n; ++k) {
+    double s = 2.0 * k + a + b;
+    double c1 = 2.0 * k * (k + a + b) * (s - 2.0);
+    double c2 = (s - 1.0) * (s * (s - 2.0) * x + a * a - b * b);
+    double c3 = 2.0 * (k + a - 1.0) * (k + b - 1.0) * s;
+    double p2 = (c2 * p1 - c3 * p0) / c1;
+    p0 = p1;
+    p1 = p2;
+  }
+  return p1;
+}
+
+// Composite rule on [a,b]: n-point Gauss-Legendre pieces graded dyadically (nlev levels)
+// toward the endpoint `toward_a ? a : b`; pieces longer than hmax (if > 0) are split.
+void graded(double a, double b, bool toward_a, int nlev, int n, std::vector<double>& x,
+            std::vector<double>& w, double hmax = 0.0) {
+  static thread_local std::vector<double> gx, gw;
+  static thread_local int gn = -1;
+  if (gn != n) {
+    gauss_legendre(n, gx, gw);
+    gn = n;
+  }
+  double L = b - a;
+  double lo = 0.0;
+  for (int k = nlev; k >= 0; --k) {
+    double hi = (k == 0) ? L : L * std::ldexp(1.0, -k);
+    const int split = (hmax > 0.0) ? std::max(1, (int)std::ceil((hi - lo) / hmax)) : 1;
+    for (int sp = 0; sp < split; ++sp) {
+      double u0 = lo + (hi - lo) * sp / split, u1 = lo + (hi - lo) * (sp + 1) / split;
+      double c = 0.5 * (u0 + u1), h = 0.5 * (u1 - u0);
+      for (int q = 0; q < n; ++q) {
+        double u = c + h * gx[q];
+        x.push_back(toward_a ? a + u : b - u);
+        w.push_back(h * gw[q]);
+      }
+    }
+    lo = hi;
+  }
+}
+
+// Rule on [a,b] for an integrand with a (log-type) singularity at the real point s.
+// Interior singular points are graded toward until the innermost piece would be shorter
+// than hmin (hmin <= 0: 2e-13 max|a,b,s|), so that no node rounds onto s.
+void singular_rule(double a, double b, double s, std::vector<double>& x, std::vector<double>& w,
+                   double hmin = 0.0) {
+  const int n_far = 20, n_grad = 10, nlev_sing = 40;
+  x.clear();
+  w.clear();
+  if (s > a && s < b) {
+    const double fl =
+        hmin > 0.0 ? hmin : 2e-13 * std::max(std::fabs(s), std::max(std::fabs(a), std::fabs(b)));
+    const int n1 = std::min(nlev_sing, std::max(1, (int)std::floor(std::log2((s - a) / fl))));
+    const int n2 = std::min(nlev_sing, std::max(1, (int)std::floor(std::log2((b - s) / fl))));
+    graded(a, s, false, n1, n_grad, x, w);
+    graded(s, b, true, n2, n_grad, x, w);
+    return;
+  }
+  double L = b - a;
+  double delta = (s <= a) ? a - s : s - b;
+  if (delta >= L) {
+    std::vector<double> gx, gw;
+    gauss_legendre(n_far, gx, gw);
+    for (int q = 0; q < n_far; ++q) {
+      x.push_back(0.5 * (a + b) + 0.5 * L * gx[q]);
+      w.push_back(0.5 * L * gw[q]);
+    }
+    return;
+  }
+  int nlev = (delta <= 0.0) ? nlev_sing : (int)std::ceil(std::log2(L / delta)) + 1;
+  graded(a, b, s <= a, nlev, n_grad, x, w);
+}
+
+struct ThetaRule {
+  std::vector<double> th, w, half_sin2;  // half_sin2 = sin^2(th/2)
+  int nmax = -1;
+  std::vector<double> cosn;             // (nth) x (nmax+1), weights/pi folded in
+  void build(int nmax_) {
+    // graded toward 0 (40 levels, 8 nodes), pieces split to at most pi/32 so that
+    // cos(n theta) stays resolved
+    th.clear();
+    w.clear();
+    graded(0.0, kPi, true, 40, 8, th, w, kPi / 32.0);
+    half_sin2.resize(th.size());
+    for (size_t i = 0; i < th.size(); ++i) {
+      double s = std::sin(0.5 * th[i]);
+      half_sin2[i] = s * s;
+    }
+    nmax = nmax_;
+    cosn.assign(th.size() * (nmax + 1), 0.0);
+    for (size_t i = 0; i < th.size(); ++i)
+      for (int n = 0; n <= nmax; ++n) cosn[i * (nmax + 1) + n] = std::cos(n * th[i]) * w[i] / kPi;
+  }
+};
+
+const ThetaRule& theta_rule(int nmax) {
+  static thread_local ThetaRule r;
+  if (r.nmax < nmax) r.build(std::max(nmax, 32));
+  return r;
+}
+
+}  // namespace
+
+void zernike_basis(int K, std::vector<int>& bn, std::vector<int>& bm, std::vector<int>& bc) {
+  bn.clear();
+  bm.clear();
+  bc.clear();
+  for (int n = 0; (int)bn.size() < K; ++n)
+    for (int m = n % 2; m <= n && (int)bn.size() < K; m += 2) {
+      bn.push_back(n);
+      bm.push_back(m);
+      bc.push_back(0);
+      if (m > 0 && (int)bn.size() < K) {
+        bn.push_back(n);
+        bm.push_back(m);
+        bc.push_back(1);
+      }
+    }
+}
+
+double zernike_radial(int n, int m, double r) {
+  int k = (n - m) / 2;
+  double v = std::pow(r, m) * jacobi_value(k, (double)m, 0.0, 1.0 - 2.0 * r * r);
+  return (k & 1) ? -v : v;
+}
+
+static double zernike_norm2(int n, int m) {
+  return (m == 0 ? 2.0 : 1.0) * kPi / (2.0 * n + 2.0);
+}
+
+void local_offset(double t, double th, double* o) {
+  double st = std::sin(t), sh = std::sin(0.5 * t);
+  o[0] = st * std::cos(th);
+  o[1] = st * std::sin(th);
+  o[2] = -2.0 * sh * sh;
+}
+
+void modal_coulomb(double t, double tp, int nmax, double* out) {
+  const double st = std::sin(t) * std::sin(tp);
+  const double sh = std::sin(0.5 * (t - tp));
+  const double chim1 = 2.0 * sh * sh / st;  // chi - 1, accurate for t ~ t'
+  const double chi = 1.0 + chim1;
+  const double k2 = 2.0 / (2.0 + chim1), kp2 = chim1 / (2.0 + chim1);
+  double K, E;
+  ellipke(k2, kp2, &K, &E);
+  const double k = std::sqrt(k2);
+  const double Q0 = k * K;  // Q_{-1/2}(chi)
+  const double pref = 2.0 / (kPi * std::sqrt(st));
+  out[0] = pref * Q0;
+  if (nmax == 0) return;
+  const double lnal = std::log(chi + std::sqrt(chim1 * (2.0 + chim1)));
+  if (2.0 * nmax * lnal < std::log(100.0)) {
+    // forward recurrence (at most two digits of growth)
+    double qm = Q0, q = chi * k * K - 2.0 * E / k;  // Q_{1/2}
+    out[1] = pref * q;
+    for (int n = 1; n < nmax; ++n) {
+      double qn = (2.0 * n * chi * q - (n - 0.5) * qm) / (n + 0.5);
+      qm = q;
+      q = qn;
+      out[n + 1] = pref * q;
+    }
+    return;
+  }
+  // Miller backward recurrence normalised by Q_{-1/2}
+  const int N = nmax + (int)std::ceil(18.5 / lnal) + 10;
+  double qp = 0.0, q = 1.0;
+  double tmp[512];
+  if (nmax >= 512) throw std::runtime_error("modal_coulomb: nmax too large");
+  for (int n = N; n >= 1; --n) {
+    double qm = (2.0 * n * chi * q - (n + 0.5) * qp) / (n - 0.5);
+    qp = q;
+    q = qm;
+    if (n - 1 <= nmax) tmp[n - 1] = q;
+    if (n <= nmax) tmp[n] = qp;
+    if (std::fabs(q) > 1e250) {
+      q *= 1e-250;
+      qp *= 1e-250;
+      for (int j = n - 1; j <= nmax; ++j) tmp[j] *= 1e-250;
+    }
+  }
+  const double scale = Q0 / tmp[0];
+  for (int n = 0; n <= nmax; ++n) out[n] = pref * tmp[n] * scale;
+}
+
+void modal_log(double t, double tp, int nmax, double* out) {
+  const double t1 = std::min(t, tp), t2 = std::max(t, tp);
+  out[0] = -std::log(std::cos(0.5 * t1) * std::sin(0.5 * t2));
+  const double ratio = std::tan(0.5 * t1) / std::tan(0.5 * t2);
+  double pw = 1.0;
+  for (int n = 1; n <= nmax; ++n) {
+    pw *= ratio;
+    out[n] = pw / (2.0 * n);
+  }
+}
+
+void modal_log1p(double t, double tp, int nmax, double* out) {
+  const ThetaRule& R = theta_rule(nmax);
+  const double sh = std::sin(0.5 * (t - tp));
+  const double A = 4.0 * sh * sh, B = 4.0 * std::sin(t) * std::sin(tp);
+  for (int n = 0; n <= nmax; ++n) out[n] = 0.0;
+  const int stride = R.nmax + 1;
+  for (size_t i = 0; i < R.th.size(); ++i) {
+    double d = std::sqrt(A + B * R.half_sin2[i]);
+    double g = std::log1p(0.5 * d);
+    const double* c = &R.cosn[i * stride];
+    for (int n = 0; n <= nmax; ++n) out[n] += g * c[n];
+  }
+}
+
+void modal_kernels(double t, double tp, int nmax, int mode, double* out) {
+  double g1[512], g2[512], g3[512];
+  modal_coulomb(t, tp, nmax, g1);
+  modal_log(t, tp, nmax, g2);
+  modal_log1p(t, tp, nmax, g3);
+  const double s = (mode == 0) ? -1.0 : 1.0;
+  for (int n = 0; n <= nmax; ++n) out[n] = g1[n] + s * g2[n] - g3[n];
+}
+
+void precompute_zernike(double eps, int K, Precomputed& out) {
+  out.eps = eps;
+  out.K = K;
+  zernike_basis(K, out.bn, out.bm, out.bc);
+  out.M = *std::max_element(out.bn.begin(), out.bn.end());
+  const int M = out.M, nth = 2 * M + 1;
+  std::vector<double> gx, gw;
+  gauss_legendre(M + 1, gx, gw);
+  out.Kstar = (M + 1) * nth;
+  out.zr.resize(out.Kstar);
+  out.zth.resize(out.Kstar);
+  out.zloc.resize(3 * (size_t)out.Kstar);
+  out.P.assign((size_t)K * out.Kstar, 0.0);
+  for (int a = 0; a <= M; ++a)
+    for (int b = 0; b < nth; ++b) {
+      int q = a * nth + b;
+      double r = 0.5 * (gx[a] + 1.0), th = 2.0 * kPi * b / nth;
+      double wq = 0.5 * gw[a] * r * 2.0 * kPi / nth;
+      out.zr[q] = r;
+      out.zth[q] = th;
+      local_offset(eps * r, th, &out.zloc[3 * (size_t)q]);
+      for (int j = 0; j < K; ++j) {
+        double trig = out.bc[j] ? std::sin(out.bm[j] * th) : std::cos(out.bm[j] * th);
+        double qj = zernike_radial(out.bn[j], out.bm[j], r) * trig /
+                    std::sqrt(zernike_norm2(out.bn[j], out.bm[j]));
+        out.P[(size_t)j * out.Kstar + q] = wq * qj;
+      }
+    }
+}
+
+void precompute(double eps, int mode, int K, const PrecomputeOptions& opt, Precomputed& out) {
+  if (!(eps > 0.0 && eps < 1.0)) throw std::runtime_error("precompute: eps must be in (0, 1)");
+  if (K < 1 || K > 2000) throw std::runtime_error("precompute: K out of range");
+  if (mode != 0 && mode != 1) throw std::runtime_error("precompute: mode must be 0 or 1");
+#ifdef _OPENMP
+  if (opt.threads > 0) omp_set_num_threads(opt.threads);
+#endif
+  const double t0 = now_s();
+  precompute_zernike(eps, K, out);
+  out.mode = mode;
+  const int M = out.M;
+  int mmax = 0;
+  for (int j = 0; j < K; ++j) mmax = std::max(mmax, out.bm[j]);
+
+  // ---- radial panels and collocation nodes (Section 8.2)
+  const int npan = opt.npan, nord = opt.nord, nr = npan * nord;
+  std::vector<double> edges(npan + 1);
+  edges[0] = 0.0;
+  for (int j = 1; j < npan; ++j) edges[j] = (1.0 - std::ldexp(1.0, -j)) * eps;
+  edges[npan] = eps;
+  std::vector<double> gx, gw, jx, jw;
+  gauss_legendre(nord, gx, gw);
+  gauss_jacobi(nord, -0.5, 0.0, jx, jw);  // weight (1-x)^(-1/2): singular end at t = eps
+  std::vector<double> tr(nr), wsig(nr), pnorm(nr);
+  for (int j = 0; j < npan; ++j) {
+    double a = edges[j], b = edges[j + 1], h = b - a;
+    for (int k = 0; k < nord; ++k) {
+      int i = j * nord + k;
+      if (j < npan - 1) {
+        tr[i] = a + 0.5 * (gx[k] + 1.0) * h;
+        wsig[i] = 0.5 * h * gw[k];
+        pnorm[i] = gx[k];
+      } else {
+        tr[i] = a + 0.5 * (jx[k] + 1.0) * h;
+        // int phi (eps-t)^(-1/2) dt = sqrt(h/2) sum w_k phi(t_k); sigma stored pointwise
+        wsig[i] = std::sqrt(0.5 * h) * jw[k] * std::sqrt(eps - tr[i]);
+        pnorm[i] = jx[k];
+      }
+    }
+  }
+  std::vector<double> nodes_gl(gx), nodes_gj(jx);
+  const Lagrange lag_gl(nodes_gl), lag_gj(nodes_gj);
+
+  // ---- collocation matrices A_n (n = 0..mmax), row-major nr x nr each
+  std::vector<double> A((size_t)(mmax + 1) * nr * nr, 0.0);
+#pragma omp parallel
+  {
+    std::vector<double> xq, wq, Gn(mmax + 1), L(nord);
+#pragma omp for schedule(dynamic, 1)
+    for (int i = 0; i < nr; ++i) {
+      const double ti = tr[i];
+      for (int j = 0; j < npan; ++j) {
+        const double a = edges[j], b = edges[j + 1];
+        const double mid = 0.5 * (a + b), half = 0.5 * (b - a);
+        const bool jac = (j == npan - 1);
+        if (!jac) {
+          singular_rule(a, b, ti, xq, wq);
+        } else {
+          // t' = eps - u^2 on u in [0, sqrt(eps - a)]: (eps - t')^(-1/2) dt' = 2 du
+          const double U = std::sqrt(eps - a), su = std::sqrt(std::max(eps - ti, 0.0));
+          // dt'/du = -2u: keep t' >= ~30 ulp away from t_i near u = su
+          const double hu = su > 0.0 ? std::max(2e-13 * U, 2e-13 * eps / su) : 0.0;
+          singular_rule(0.0, U, su, xq, wq, hu);
+          for (size_t q = 0; q < xq.size(); ++q) {
+            double u = xq[q];
+            xq[q] = eps - u * u;
+            wq[q] *= 2.0;
+          }
+        }
+        for (size_t q = 0; q < xq.size(); ++q) {
+          const double tq = xq[q];
+          modal_kernels(ti, tq, mmax, mode, Gn.data());
+          (jac ? lag_gj : lag_gl).eval((tq - mid) / half, L.data());
+          const double wt = 2.0 * kPi * wq[q] * std::sin(tq);
+          for (int k = 0; k < nord; ++k) {
+            double lk = L[k];
+            if (jac) lk *= std::sqrt(eps - tr[j * nord + k]);  // g(t_k) = sigma(t_k) sqrt(eps - t_k)
+            const double c = wt * lk;
+            for (int n = 0; n <= mmax; ++n) A[((size_t)n * nr + i) * nr + j * nord + k] += c * Gn[n];
+          }
+        }
+      }
+    }
+  }
+
+  // ---- one LU per mode; beta_j solves the mode-m_j system with rhs c_j R(t/eps)
+  if (opt.keep_collocation) out.colloc = A;
+  std::vector<LU> lus(mmax + 1);
+  for (int n = 0; n <= mmax; ++n) lus[n].factor(&A[(size_t)n * nr * nr], nr);
+  out.nrad = nr;
+  out.trad = tr;
+  out.beta.assign((size_t)nr * K, 0.0);
+  {
+    std::vector<double> rhs(nr);
+    for (int j = 0; j < K; ++j) {
+      const double c = 1.0 / std::sqrt(zernike_norm2(out.bn[j], out.bm[j]));
+      for (int i = 0; i < nr; ++i) rhs[i] = c * zernike_radial(out.bn[j], out.bm[j], tr[i] / eps);
+      lus[out.bm[j]].solve(rhs.data());
+      for (int i = 0; i < nr; ++i) out.beta[(size_t)i * K + j] = rhs[i];
+    }
+  }
+
+  // ---- fine grid, weights and I = w^T B
+  int nth = opt.ntheta_fine > 0 ? opt.ntheta_fine : M + 40;
+  nth += nth % 2;
+  out.ntheta = nth;
+  const int nf = nr * nth;
+  out.nf = nf;
+  out.w.resize(nf);
+  std::vector<double> thf(nth);
+  for (int a = 0; a < nth; ++a) thf[a] = 2.0 * kPi * a / nth;
+  for (int r = 0; r < nr; ++r)
+    for (int a = 0; a < nth; ++a) out.w[(size_t)r * nth + a] = wsig[r] * std::sin(tr[r]) * 2.0 * kPi / nth;
+  std::vector<double> trig((size_t)nth * K);
+  for (int a = 0; a < nth; ++a)
+    for (int j = 0; j < K; ++j)
+      trig[(size_t)a * K + j] = out.bc[j] ? std::sin(out.bm[j] * thf[a]) : std::cos(out.bm[j] * thf[a]);
+  // WB(l, j) = w_l beta_j(t_r) trig_j(theta_a), l = r*nth + a
+  auto WB = [&](int l, double* row) {
+    const int r = l / nth, a = l % nth;
+    const double wl = out.w[l];
+    for (int j = 0; j < K; ++j) row[j] = wl * out.beta[(size_t)r * K + j] * trig[(size_t)a * K + j];
+  };
+  out.I.assign(K, 0.0);
+  {
+    std::vector<double> row(K);
+    for (int l = 0; l < nf; ++l) {
+      WB(l, row.data());
+      for (int j = 0; j < K; ++j) out.I[j] += row[j];
+    }
+  }
+  const double t1 = now_s();
+  out.seconds_onepatch = t1 - t0;
+
+  // ---- interpolative decomposition of the far field (Section 7.1)
+  // training grid on {rho > id_rho_min * eps}: dyadic radial panels, azimuthal count
+  // from the (eps/rho)^m decay of fields generated inside the patch
+  std::vector<double> xt;
+  {
+    std::vector<double> e2;
+    e2.push_back(opt.id_rho_min * eps);
+    while (e2.back() * 2.0 < kPi) e2.push_back(e2.back() * 2.0);
+    e2.push_back(kPi);
+    std::vector<double> px, pw;
+    gauss_legendre(opt.id_nper, px, pw);
+    for (size_t s = 0; s + 1 < e2.size(); ++s) {
+      double a = e2[s], b = e2[s + 1];
+      int m = (int)std::ceil(std::log(opt.id_tol / 10.0) / std::log(eps / a));
+      m = std::max(m, 8);
+      int nphi = 2 * m + 1;
+      for (int q = 0; q < opt.id_nper; ++q) {
+        double rho = 0.5 * (a + b) + 0.5 * (b - a) * px[q];
+        for (int f = 0; f < nphi; ++f) {
+          double phi = 2.0 * kPi * f / nphi;
+          xt.push_back(std::sin(rho) * std::cos(phi));
+          xt.push_back(std::sin(rho) * std::sin(phi));
+          xt.push_back(std::cos(rho));
+        }
+      }
+    }
+  }
+  const int nt = (int)(xt.size() / 3);
+  std::vector<double> xf(3 * (size_t)nf);
+  for (int r = 0; r < nr; ++r)
+    for (int a = 0; a < nth; ++a) {
+      size_t l = (size_t)r * nth + a;
+      xf[3 * l + 0] = std::sin(tr[r]) * std::cos(thf[a]);
+      xf[3 * l + 1] = std::sin(tr[r]) * std::sin(thf[a]);
+      xf[3 * l + 2] = std::cos(tr[r]);
+    }
+  const double sgn = (mode == 0) ? -1.0 : 1.0;
+  auto Gsurf = [sgn](double d) { return 2.0 / d + sgn * std::log(2.0 / d) - std::log1p(0.5 * d); };
+
+  int ks = std::min(256, nt);
+  std::vector<double> Y;      // column-major ks x nf
+  std::vector<int> piv;
+  int p = 0;
+  for (;;) {
+    // Y = Omega A, Omega Gaussian ks x nt (counter-based), A(j,l) = G(x^t_j, x^f_l)
+    std::vector<double> Om((size_t)ks * nt);
+    for (int r = 0; r < ks; ++r)
+      for (int j = 0; j < nt; ++j) Om[(size_t)r * nt + j] = normal_variate(((uint64_t)r << 32) + j + 0x5eedull);
+    Y.assign((size_t)ks * nf, 0.0);
+    const int CB = 32;
+#pragma omp parallel
+    {
+      std::vector<double> Ab((size_t)nt * CB);
+#pragma omp for schedule(dynamic, 1)
+      for (int cb = 0; cb < (nf + CB - 1) / CB; ++cb) {
+        const int l0 = cb * CB, nl = std::min(CB, nf - l0);
+        for (int j = 0; j < nt; ++j)
+          for (int c = 0; c < nl; ++c) {
+            const double* a = &xt[3 * (size_t)j];
+            const double* b = &xf[3 * (size_t)(l0 + c)];
+            double dx = a[0] - b[0], dy = a[1] - b[1], dz = a[2] - b[2];
+            Ab[(size_t)j * CB + c] = Gsurf(std::sqrt(dx * dx + dy * dy + dz * dz));
+          }
+        for (int c = 0; c < nl; ++c) {
+          double* ycol = &Y[(size_t)(l0 + c) * ks];
+          for (int r = 0; r < ks; ++r) {
+            const double* om = &Om[(size_t)r * nt];
+            double s = 0.0;
+            for (int j = 0; j < nt; ++j) s += om[j] * Ab[(size_t)j * CB + c];
+            ycol[r] = s;
+          }
+        }
+      }
+    }
+    // column-pivoted Householder QR of Y, stopped at |R_kk| < tol |R_00|
+    piv.resize(nf);
+    for (int l = 0; l < nf; ++l) piv[l] = l;
+    std::vector<double> cn(nf), cn0(nf);
+    for (int l = 0; l < nf; ++l) {
+      double s = 0.0;
+      for (int r = 0; r < ks; ++r) s += Y[(size_t)l * ks + r] * Y[(size_t)l * ks + r];
+      cn[l] = cn0[l] = s;
+    }
+    double r00 = 0.0;
+    p = 0;
+    std::vector<double> v(ks);
+    for (int s = 0; s < ks; ++s) {
+      int best = s;
+      for (int l = s + 1; l < nf; ++l)
+        if (cn[l] > cn[best]) best = l;
+      if (best != s) {
+        std::swap(piv[s], piv[best]);
+        std::swap(cn[s], cn[best]);
+        std::swap(cn0[s], cn0[best]);
+        std::swap_ranges(&Y[(size_t)s * ks], &Y[(size_t)s * ks] + ks, &Y[(size_t)best * ks]);
+      }
+      double* col = &Y[(size_t)s * ks];
+      double nrm = 0.0;
+      for (int r = s; r < ks; ++r) nrm += col[r] * col[r];
+      nrm = std::sqrt(nrm);
+      const double rss = (col[s] >= 0.0) ? -nrm : nrm;
+      if (s == 0) r00 = std::fabs(rss);
+      if (std::fabs(rss) < opt.id_tol * r00 || nrm == 0.0) {
+        p = s;
+        break;
+      }
+      for (int r = s; r < ks; ++r) v[r] = col[r];
+      v[s] -= rss;
+      double vv = 0.0;
+      for (int r = s; r < ks; ++r) vv += v[r] * v[r];
+      col[s] = rss;
+      for (int r = s + 1; r < ks; ++r) col[r] = 0.0;
+#pragma omp parallel for schedule(static)
+      for (int l = s + 1; l < nf; ++l) {
+        double* y = &Y[(size_t)l * ks];
+        double dot = 0.0;
+        for (int r = s; r < ks; ++r) dot += v[r] * y[r];
+        const double f = 2.0 * dot / vv;
+        for (int r = s; r < ks; ++r) y[r] -= f * v[r];
+        double nn = cn[l] - y[s] * y[s];
+        if (nn < 1e-10 * cn0[l]) {  // recompute after cancellation
+          nn = 0.0;
+          for (int r = s + 1; r < ks; ++r) nn += y[r] * y[r];
+          cn0[l] = nn;
+        }
+        cn[l] = nn;
+      }
+      p = s + 1;
+    }
+    if (p < ks - 16 || ks >= nt) break;
+    ks = std::min(2 * ks, nt);  // rank not revealed by the sketch: enlarge it
+  }
+  if (p < 1) throw std::runtime_error("precompute: ID rank is zero");
+  out.p = p;
+  // Pi = [I, R11^-1 R12] in pivoted order; T = Pi W B
+  const int nrest = nf - p;
+  std::vector<double> X((size_t)p * nrest);  // X(m, c) row-major
+#pragma omp parallel for schedule(static)
+  for (int c = 0; c < nrest; ++c) {
+    const double* y = &Y[(size_t)(p + c) * ks];
+    std::vector<double> xcol(p);
+    for (int m = p - 1; m >= 0; --m) {
+      double s = y[m];
+      for (int q = m + 1; q < p; ++q) s -= Y[(size_t)q * ks + m] * xcol[q];
+      xcol[m] = s / Y[(size_t)m * ks + m];
+    }
+    for (int m = 0; m < p; ++m) X[(size_t)m * nrest + c] = xcol[m];
+  }
+  out.T.assign((size_t)p * K, 0.0);
+#pragma omp parallel
+  {
+    std::vector<double> row(K);
+#pragma omp for schedule(static)
+    for (int m = 0; m < p; ++m) {
+      double* Tm = &out.T[(size_t)m * K];
+      WB(piv[m], row.data());
+      for (int j = 0; j < K; ++j) Tm[j] = row[j];
+      for (int c = 0; c < nrest; ++c) {
+        const double x = X[(size_t)m * nrest + c];
+        if (x == 0.0) continue;
+        WB(piv[p + c], row.data());
+        for (int j = 0; j < K; ++j) Tm[j] += x * row[j];
+      }
+    }
+  }
+  out.st.resize(p);
+  out.sth.resize(p);
+  out.sloc.resize(3 * (size_t)p);
+  for (int m = 0; m < p; ++m) {
+    const int l = piv[m];
+    out.st[m] = tr[l / nth];
+    out.sth[m] = thf[l % nth];
+    local_offset(out.st[m], out.sth[m], &out.sloc[3 * (size_t)m]);
+  }
+  out.seconds_id = now_s() - t1;
+}
+
+}  // namespace ncs

@@ -1,0 +1,207 @@
+"""ctypes binding of the C ABI in include/ncs.h (argument marshalling only).
+
+Every computation runs in libncs.so (host precompute in C++, products and GMRES in
+CUDA kernels). Loading fails loudly if the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libncs.so")
+
+NCS_OK = 0
+NCS_E_INPUT = -1
+NCS_E_NOCONV = -2
+NCS_E_NUMERIC = -3
+NCS_E_CUDA = -4
+NCS_E_TIMEOUT = -5
+NCS_E_OOM = -6
+NCS_E_STATE = -7
+EXTERIOR, INTERIOR = 0, 1
+FP64, FP32, MIXED = 0, 1, 2
+METHOD_AUTO, METHOD_DIRECT, METHOD_TREE = 0, 1, 2
+
+EXPORTS = ["ncs_default_params", "ncs_create", "ncs_create_from_operator", "ncs_info", "ncs_timings",
+           "ncs_get_operator", "ncs_get_onepatch", "ncs_set_patches", "ncs_set_method", "ncs_matvec",
+           "ncs_matvec_dev", "ncs_field_dev", "ncs_solve", "ncs_eval", "ncs_last_error", "ncs_destroy"]
+
+
+class ncs_params(ctypes.Structure):
+    _fields_ = [("npan", ctypes.c_int), ("nord", ctypes.c_int), ("ntheta_fine", ctypes.c_int),
+                ("id_tol", ctypes.c_double), ("threads", ctypes.c_int), ("grid_tol", ctypes.c_double),
+                ("method", ctypes.c_int), ("tree_min_patches", ctypes.c_int), ("gmres_maxit", ctypes.c_int),
+                ("verbose", ctypes.c_int)]
+
+
+class NcsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"ncs error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+D = ctypes.POINTER(ctypes.c_double)
+VP = ctypes.c_void_p
+
+
+def load(path: str = LIB_PATH):
+    """Loads libncs.so (raises if it is missing: there is no fallback path)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} not built: run paper_1906_04209_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    lib.ncs_default_params.argtypes = [ctypes.POINTER(ncs_params)]
+    lib.ncs_default_params.restype = None
+    lib.ncs_create.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ncs_params),
+                               ctypes.POINTER(VP)]
+    lib.ncs_create_from_operator.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, D, D, D, D,
+                                             ctypes.POINTER(ncs_params), ctypes.POINTER(VP)]
+    lib.ncs_info.argtypes = [VP, ctypes.POINTER(ctypes.c_int64), ctypes.c_int]
+    lib.ncs_timings.argtypes = [VP, D, ctypes.c_int]
+    lib.ncs_get_operator.argtypes = [VP, D, D, D, D, D, D, D]
+    lib.ncs_get_onepatch.argtypes = [VP, D, D]
+    lib.ncs_set_patches.argtypes = [VP, ctypes.c_int64, D]
+    lib.ncs_set_method.argtypes = [VP, ctypes.c_int]
+    lib.ncs_matvec.argtypes = [VP, D, D, ctypes.c_int]
+    lib.ncs_matvec_dev.argtypes = [VP, VP, VP, ctypes.c_int, VP]
+    lib.ncs_field_dev.argtypes = [VP, VP, VP, ctypes.c_int, VP]
+    lib.ncs_solve.argtypes = [VP, ctypes.c_double, ctypes.c_int, D, D, D, ctypes.POINTER(ctypes.c_int), D]
+    lib.ncs_eval.argtypes = [VP, ctypes.c_int64, D, D, D]
+    lib.ncs_last_error.argtypes = [VP]
+    lib.ncs_last_error.restype = ctypes.c_char_p
+    lib.ncs_destroy.argtypes = [VP]
+    lib.ncs_destroy.restype = None
+    for name in EXPORTS:
+        if name not in ("ncs_default_params", "ncs_last_error", "ncs_destroy"):
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(D)
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def default_params(**kw) -> ncs_params:
+    p = ncs_params()
+    load().ncs_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+class Context:
+    """One solver context (precompute for (eps, mode, K) plus a patch layout)."""
+
+    def __init__(self, eps, mode, K, params=None, operator=None, **kw):
+        lib = load()
+        prm = params or default_params(**kw)
+        h = VP()
+        if operator is None:
+            rc = lib.ncs_create(eps, mode, K, ctypes.byref(prm), ctypes.byref(h))
+        else:
+            T, st, sth, I = (_f64(a) for a in operator)
+            p = T.shape[0]
+            rc = lib.ncs_create_from_operator(eps, mode, K, p, _ptr(T), _ptr(st), _ptr(sth), _ptr(I),
+                                              ctypes.byref(prm), ctypes.byref(h))
+        if rc != NCS_OK:
+            raise NcsError(rc, "ncs_create failed")
+        self.h = h
+        self.eps, self.mode, self.K = eps, mode, K
+        self.N = 0
+
+    def _check(self, rc):
+        if rc != NCS_OK:
+            raise NcsError(rc, load().ncs_last_error(self.h).decode())
+        return rc
+
+    def close(self):
+        if self.h:
+            load().ncs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        out = (ctypes.c_int64 * 11)()
+        load().ncs_info(self.h, out, 11)
+        keys = ["K", "Kstar", "p", "M", "nf", "N", "nrad", "levels", "grid_points", "tree_pairs", "direct_pairs"]
+        return dict(zip(keys, [int(v) for v in out]))
+
+    def timings(self):
+        out = np.zeros(2)
+        load().ncs_timings(self.h, _ptr(out), 2)
+        return out
+
+    def operator(self):
+        i = self.info()
+        T = np.zeros((i["p"], i["K"]))
+        st, sth = np.zeros(i["p"]), np.zeros(i["p"])
+        I = np.zeros(i["K"])
+        P = np.zeros((i["K"], i["Kstar"]))
+        zr, zth = np.zeros(i["Kstar"]), np.zeros(i["Kstar"])
+        self._check(load().ncs_get_operator(self.h, _ptr(T), _ptr(st), _ptr(sth), _ptr(I), _ptr(P), _ptr(zr),
+                                            _ptr(zth)))
+        return dict(T=T, skel_t=st, skel_theta=sth, I=I, P=P, znode_r=zr, znode_theta=zth)
+
+    def onepatch(self):
+        i = self.info()
+        tr = np.zeros(i["nrad"])
+        beta = np.zeros((i["nrad"], i["K"]))
+        self._check(load().ncs_get_onepatch(self.h, _ptr(tr), _ptr(beta)))
+        return tr, beta
+
+    def set_patches(self, centres):
+        c = _f64(centres).reshape(-1, 3)
+        self._check(load().ncs_set_patches(self.h, c.shape[0], _ptr(c)))
+        self.N = c.shape[0]
+
+    def set_method(self, method):
+        self._check(load().ncs_set_method(self.h, method))
+
+    def matvec(self, x, precision=FP64):
+        x = _f64(x).ravel()
+        y = np.empty_like(x)
+        self._check(load().ncs_matvec(self.h, _ptr(x), _ptr(y), precision))
+        return y
+
+    def matvec_dev(self, x_ptr, y_ptr, precision=FP64, stream=0):
+        """x_ptr, y_ptr: device addresses (e.g. torch tensor.data_ptr())."""
+        self._check(load().ncs_matvec_dev(self.h, VP(x_ptr), VP(y_ptr), precision, VP(stream)))
+
+    def field_dev(self, x_ptr, z_ptr, precision=FP64, stream=0):
+        self._check(load().ncs_field_dev(self.h, VP(x_ptr), VP(z_ptr), precision, VP(stream)))
+
+    def solve(self, tol=1e-10, precision=FP64, want_fhat=True, allow_noconv=False):
+        fhat = np.zeros(self.N * self.K) if want_fhat else None
+        sc, Is, rr = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        it = ctypes.c_int()
+        rc = load().ncs_solve(self.h, tol, precision, _ptr(fhat), ctypes.byref(sc), ctypes.byref(Is),
+                              ctypes.byref(it), ctypes.byref(rr))
+        if rc != NCS_OK and not (allow_noconv and rc == NCS_E_NOCONV):
+            self._check(rc)
+        return dict(fhat=fhat, scalar=sc.value, Isigma=Is.value, iterations=it.value, relres=rr.value, rc=rc)
+
+    def eval(self, targets, fhat):
+        t = _f64(targets).reshape(-1, 3)
+        f = _f64(fhat).ravel()
+        out = np.zeros(t.shape[0])
+        self._check(load().ncs_eval(self.h, t.shape[0], _ptr(t), _ptr(f), _ptr(out)))
+        return out

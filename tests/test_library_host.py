@@ -1,0 +1,78 @@
+"""Host-side logic of the C-ABI library, checked on CPU against the oracle: symbol
+exports, one-patch precompute (B, I, P), the library's own ID/outgoing operator, and
+input validation. No GPU call is made here."""
+import re
+import os
+
+import numpy as np
+import pytest
+
+from oracle import onepatch, zernike, idcomp
+from oracle.kernels import G_on_surface, chord, EXTERIOR, INTERIOR
+from paper_1906_04209_gb300 import ncs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_exports_match_header(libncs):
+    hdr = open(os.path.join(ROOT, "include", "ncs.h")).read()
+    names = set(re.findall(r"\b(ncs_[a-z_]+)\s*\(", hdr))
+    assert names, "no declarations found"
+    for n in names:
+        assert hasattr(libncs, n), n
+    assert set(ncs.EXPORTS) == names
+
+
+@pytest.mark.parametrize("mode", [EXTERIOR, INTERIOR])
+def test_onepatch_matches_oracle(libncs, mode):
+    eps, K, npan, nord, nth = 0.05, 21, 7, 12, 30
+    c = ncs.Context(eps, mode, K, npan=npan, nord=nord, ntheta_fine=nth)
+    tr, beta = c.onepatch()
+    op = onepatch.solve_one_patch(eps, mode, K, npan, nord, nth)
+    assert np.abs(tr - op.rad.t).max() < 1e-15
+    assert np.abs(beta - op.beta).max() < 1e-11 * np.abs(op.beta).max()
+    o = c.operator()
+    assert np.abs(o["I"] - op.I).max() < 1e-11 * np.abs(op.I).max()
+    P, r, th = zernike.transform(K)
+    assert np.abs(o["P"] - P).max() < 1e-13
+    assert np.abs(o["znode_r"] - r).max() < 1e-15 and np.abs(o["znode_theta"] - th).max() < 1e-15
+
+
+@pytest.mark.parametrize("mode", [EXTERIOR, INTERIOR])
+def test_library_outgoing_operator(libncs, mode):
+    """The library's own ID (sketched CPQR) reproduces the far field of the oracle's
+    fine-grid quadrature (eq. outgoingcompressed) at held-out far targets."""
+    eps, K = 0.05, 21
+    c = ncs.Context(eps, mode, K, npan=7, nord=12, ntheta_fine=30)
+    o = c.operator()
+    op = onepatch.solve_one_patch(eps, mode, K, 7, 12, 30)
+    xt = idcomp.training_grid(eps, 1e-11, nper=5, rho_min_factor=2.07)
+    xf = idcomp.fine_points(op)
+    st, sth = o["skel_t"], o["skel_theta"]
+    xs = np.stack([np.sin(st) * np.cos(sth), np.sin(st) * np.sin(sth), np.cos(st)], 1)
+    f = np.random.default_rng(5).standard_normal(K)
+    ref = G_on_surface(chord(xt[:, None], xf[None]), mode) @ (op.w * (op.B @ f))
+    lib = G_on_surface(chord(xt[:, None], xs[None]), mode) @ (o["T"] @ f)
+    assert np.abs(lib - ref).max() < 1e-9 * np.abs(ref).max()
+
+
+def test_create_validation(libncs):
+    for args in [(0.0, 0, 10), (1.5, 0, 10), (0.1, 2, 10), (0.1, 0, 0)]:
+        with pytest.raises(ncs.NcsError) as e:
+            ncs.Context(*args, npan=4, nord=6)
+        assert e.value.code == ncs.NCS_E_INPUT
+
+
+def test_set_patches_validation(libncs):
+    c = ncs.Context(0.1, 1, 3, npan=4, nord=6, ntheta_fine=8)
+    with pytest.raises(ncs.NcsError) as e:  # geodesic distance 0.25 < 3 eps
+        c.set_patches([[0, 0, 1.0], [np.sin(0.25), 0, np.cos(0.25)]])
+    assert e.value.code == ncs.NCS_E_INPUT
+    with pytest.raises(ncs.NcsError) as e:
+        c.set_patches([[0, 0, 1.1]])
+    assert e.value.code == ncs.NCS_E_INPUT
+    c.set_patches([[0, 0, 1.0], [np.sin(0.31), 0, np.cos(0.31)]])
+    assert c.info()["N"] == 2
+    with pytest.raises(ncs.NcsError) as e:  # arguments are checked before any device work
+        c.solve(tol=0)
+    assert e.value.code == ncs.NCS_E_INPUT
