@@ -1,0 +1,325 @@
+#!/usr/bin/env python
+"""Benchmark: fast multiple-scattering products on the 100 000-patch workload.
+
+Workload: interior (narrow escape) problem, N = 100 000 disk patches of radius
+eps = 0.001 on a seeded jittered Fibonacci spiral (jitter 0.3 * sqrt(4 pi / N)),
+K = 136 Zernike functions per patch (M = 15, 13.6 M unknowns), ID tolerance 1e-11,
+incoming-grid tolerance 1e-8, cube-sphere tree. One step = one product y = A x of
+the second-kind system (outgoing map, P2L onto incoming grids, direct sums, L2P,
+Zernike transform) in the FP32 kernels that the mixed-precision solve iterates with.
+The line also reports the FP64 product rate and, with --solve, the mixed and FP64
+solve times to a 1e-8 relative residual.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    torchrun --nproc-per-node N bench.py --gpus N ...   (independent replicas)
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "N=1e5 solve time to 1e-8 residual & matvecs/s, mixed vs FP64 on one GB300"
+UNIT = "matvecs/s"
+WORKLOAD = "interior N=100000 eps=0.001 K=136 jittered-Fibonacci tree (configs[3] layout i)"
+# Nominal work per pair evaluation used for flop rates: 3 sub, 3 mul/fma for d^2,
+# rsqrt, log, ~4 for the kernel value, 1 fma accumulate ~ 20 flops (stated, not measured).
+FLOPS_PER_PAIR = 20
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"ncs_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except Exception:
+            return None
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for n, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1906_04209_gb300 import layouts as L, ncs
+
+    ws, rank = _dist()
+    if ws > 1:
+        dist.init_process_group("nccl")
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    centres, eps, mode, K = L.workload(3, layout=args.layout)
+    N = len(centres)
+    t0 = time.time()
+    ctx = ncs.Context(eps, mode, K, method=ncs.METHOD_TREE, grid_tol=args.grid_tol)
+    ctx.set_patches(centres)
+    setup_s = time.time() - t0
+    info, tstats = ctx.info(), ctx.tree_stats()
+    n = N * K
+    g = torch.Generator(device="cuda").manual_seed(1234 + rank)
+    x = torch.randn(n, dtype=torch.float64, device="cuda", generator=g)
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    prec = ncs.FP32 if args.precision == "fp32" else ncs.FP64
+
+    def step(p=prec):
+        ctx.matvec_dev(x.data_ptr(), y.data_ptr(), p, sp)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # per-stage times of one product (the dominant kernel's duration for the roofline)
+    stages32 = ctx.profile_matvec(x.data_ptr(), y.data_ptr(), prec, sp)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # P2L duration inside the timed region, measured on the launching stream
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    ms_total = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    ms_step = ms_total / args.steps
+    if ws > 1:
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = ws * 1000.0 / ms_step
+
+    # stage profile repeated inside a timed loop: the P2L share of each product
+    p2l_ms = []
+    for _ in range(max(1, min(args.steps, 3))):
+        p2l_ms.append(ctx.profile_matvec(x.data_ptr(), y.data_ptr(), prec, sp)["p2l"])
+    p2l_avg = float(np.mean(p2l_ms))
+
+    # end to end through the C ABI with host buffers (pinned), H2D + product + D2H
+    xh = torch.empty(n, dtype=torch.float64).pin_memory()
+    xh.copy_(x.cpu())
+    yh = torch.empty(n, dtype=torch.float64).pin_memory()
+    lib = ncs.load()
+    import ctypes
+    Dp = ctypes.POINTER(ctypes.c_double)
+    ee = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(ee):
+        rc = lib.ncs_matvec(ctx.h, ctypes.cast(xh.data_ptr(), Dp), ctypes.cast(yh.data_ptr(), Dp), prec)
+        assert rc == 0, ncs.load().ncs_last_error(ctx.h)
+    e2e_s = (time.perf_counter() - t0) / ee
+
+    # FP64 product rate (fewer steps: the FP64 pipe is the bottleneck on this part)
+    fp64 = None
+    if args.fp64_steps > 0:
+        step(ncs.FP64)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.fp64_steps):
+            step(ncs.FP64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fp64 = 1000.0 * args.fp64_steps / e0.elapsed_time(e1)
+
+    solve = None
+    if args.solve:
+        solve = {}
+        for name, p in (("mixed", ncs.MIXED), ("fp64", ncs.FP64)):
+            if name == "fp64" and not args.solve_fp64:
+                continue
+            t0 = time.time()
+            r = ctx.solve(tol=1e-8, precision=p, want_fhat=False, allow_noconv=True)
+            solve[name] = {"seconds": round(time.time() - t0, 3), "iterations": r["iterations"],
+                           "relres": r["relres"], "mu": r["scalar"], "rc": r["rc"]}
+
+    peaks, src = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    # ALU roofline of the pair kernel: per pair the FP32 path issues 2 MUFU ops (rsqrt,
+    # log2) and ~10 FP32-pipe ops; 152 SMs x 16 MUFU/clk caps it at 8 pairs/clk/SM.
+    pair_peak = 152 * 8 * sm_max * 1e6 if prec == ncs.FP32 else None
+    p2l_pairs = tstats["p2l_pairs"]
+    achieved_pairs = p2l_pairs / (p2l_avg / 1000.0)
+    roof = {
+        "kernel": "p2l_kernel (interaction-list skeletons -> incoming grids)",
+        "bound": "alu",
+        "achieved": round(achieved_pairs * FLOPS_PER_PAIR / 1e12, 3),
+        "peak": round(pair_peak * FLOPS_PER_PAIR / 1e12, 3) if pair_peak else None,
+        "unit": "TFLOP/s",
+        "frac": round(achieved_pairs / pair_peak, 4) if pair_peak else None,
+        "traffic": None,
+        "pairs_per_launch": p2l_pairs,
+        "ms_per_launch": round(p2l_avg, 3),
+        "peak_source": "derived: 152 SMs x 16 MUFU/clk / 2 MUFU per pair x %g MHz (%s clocks)" % (sm_max, src),
+    }
+    cpu = cpu_baseline(args, centres, eps, mode, K) if (rank == 0 and args.cpu_baseline) else None
+    line = {
+        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == ncs.FP32 else "f64",
+        "data": "synthetic (seeded layout, random Gaussian input vector)",
+        "config": {"workload": WORKLOAD, "N": N, "eps": eps, "K": K, "mode": "interior",
+                   "layout": args.layout, "p": info["p"], "Kstar": info["Kstar"], "levels": tstats["levels"],
+                   "grid_tol": args.grid_tol, "parallelism": "replicas" if ws > 1 else "single",
+                   "l2": "working set > L2 (skeleton offsets 200 MB, z 397 MB, grids per step)",
+                   "setup_s": round(setup_s, 2)},
+        "e2e": {"value": round(ws / e2e_s, 4), "unit": UNIT, "h2d_bytes_per_step": n * 8,
+                "d2h_bytes_per_step": n * 8},
+        "gpu_launches": 6 * args.steps,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "clocks": clk,
+        "stages_ms": {k: round(v, 3) for k, v in stages32.items()},
+        "fp64_matvecs_per_s": round(fp64, 4) if fp64 else None,
+        "pairs_per_step": tstats["p2l_pairs"] + tstats["direct_pairs"],
+        "pair_rate_per_s": round((tstats["p2l_pairs"] + tstats["direct_pairs"]) * 1000.0 / ms_step, 1),
+        "solve": solve,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(args, centres, eps, mode, K, seconds=None):
+    """The oracle as it stands (plain-C FP64 compressed sums, all host cores) on a
+    bounded sample of target nodes, scaled to products per second."""
+    from oracle import native, operator as O
+    seconds = seconds or args.cpu_seconds
+    pre = O.make_precompute(eps, mode, K, npan=8, nord=12, ntheta=40, tau=1e-10)
+    N = len(centres)
+    x = np.random.default_rng(5).standard_normal(N * K)
+    rng = np.random.default_rng(6)
+    # calibrate on a few targets, then time a sample sized to ~`seconds`
+    t0 = time.time()
+    native.rows(pre, centres, x, rng.choice(N, 8), rng.choice(pre.Kstar, 8))
+    t_cal = time.time() - t0
+    ns = int(max(8, min(4096, 8 * seconds / max(t_cal, 1e-3))))
+    pat, nod = rng.choice(N, ns), rng.choice(pre.Kstar, ns)
+    t0 = time.time()
+    native.rows(pre, centres, x, pat, nod)
+    dt = time.time() - t0
+    value = (ns / (N * pre.Kstar)) / dt
+    return {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{ns} of {N}x{pre.Kstar} Zernike-node outputs of one product (ID-direct sums, "
+                      f"FP64, plain C with OpenMP), {dt:.1f} s, scaled to whole products"}
+
+
+def run_reference(args):
+    ws, rank = _dist()
+    if rank != 0:
+        return
+    from paper_1906_04209_gb300 import layouts as L
+    centres, eps, mode, K = L.workload(3, layout=args.layout)
+    per_step = []
+    base = None
+    for s in range(args.warmup + args.steps):
+        r = cpu_baseline(args, centres, eps, mode, K, seconds=args.ref_seconds)
+        base = r
+        if s >= args.warmup:
+            per_step.append(r["value"])
+    value = float(np.mean(per_step))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "N": len(centres), "eps": eps, "K": K},
+            "cpu_baseline": {"kind": "oracle", "cores": base["cores"], "sample": base["sample"], "value": value},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--layout", default="fibonacci", choices=["fibonacci", "vmf"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--grid-tol", type=float, default=1e-8)
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--solve", action="store_true")
+    ap.add_argument("--solve-fp64", action="store_true")
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-seconds", type=float, default=10.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

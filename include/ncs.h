@@ -19,8 +19,9 @@
  *   - Host arrays are owned by the caller, read (or written) only during the
  *     call, and copied where the library keeps the data.
  *   - Device pointers are owned by the caller, must be resident on the device
- *     that was current when the context was created, are used only on the given
- *     CUDA stream and only until the call's work on that stream completes.
+ *     bound to the context (the one current at its first GPU call), are used only
+ *     on the given CUDA stream and only until the call's work on that stream
+ *     completes.
  *   - Vectors over all patches are patch-major: x[i*K + k] is coefficient k of
  *     patch i; k follows the Zernike ordering (n ascending, then m ascending,
  *     cos before sin) of Section 4.
@@ -102,6 +103,21 @@ int ncs_create_from_operator(double eps, int mode, int K, int p, const double* T
                              const ncs_params* params, ncs_ctx** out);
 
 /*
+ * Like ncs_create_from_operator with several outgoing representations: nrep far-field
+ * radii rho_min (geodesic, increasing, the first >= 2 eps), their ranks p, and T,
+ * skel_t, skel_theta concatenated in that order (sum(p) rows / entries). A source is
+ * represented by the coarsest representation whose far field contains every target
+ * it is summed onto (per-level recompression, Section 7 "Optimizations").
+ */
+int ncs_create_from_operators(double eps, int mode, int K, int nrep, const double* rho_min, const int* p,
+                              const double* T, const double* skel_t, const double* skel_theta,
+                              const double* I, const ncs_params* params, ncs_ctx** out);
+
+/* Number of outgoing representations in *nrep; with rho_min and p non-NULL (and
+ * *nrep at least that number on entry) also their far-field radii and ranks. */
+int ncs_get_reps(const ncs_ctx* ctx, int* nrep, double* rho_min, int* p);
+
+/*
  * Writes context sizes into out[0..n): K, Kstar, p, M, nf (fine-grid points),
  * N (patches set, 0 if none), nrad (radial nodes), tree levels (0 if no tree),
  * grid points over all tree groups, pair evaluations per tree matvec (FP counts
@@ -113,7 +129,8 @@ int ncs_info(const ncs_ctx* ctx, int64_t* out, int n);
 int ncs_timings(const ncs_ctx* ctx, double* out, int n);
 
 /*
- * Copies the precompute out (any pointer may be NULL to skip it): T (p x K),
+ * Copies the finest outgoing representation (far field beyond 2 eps) and the
+ * rest of the precompute out (any pointer may be NULL to skip it): T (p x K),
  * skeleton (t, theta) (p each), I (K), P (K x Kstar), Zernike nodes on the unit
  * disk (r, theta) (Kstar each).
  */
@@ -136,6 +153,23 @@ int ncs_get_onepatch(const ncs_ctx* ctx, double* trad, double* beta);
  */
 int ncs_set_patches(ncs_ctx* ctx, int64_t N, const double* centres);
 
+/*
+ * Diagnostics of the cube-sphere quadtree (Section 7.2): every ordered (target,
+ * source) patch pair the tree product accounts for, with its level and kind (0 =
+ * interaction list, 2 = leaf-level neighbour; Step 3 note: each ordered pair of
+ * distinct patches must appear exactly once). Call with target == NULL to get the
+ * count in *count; then with buffers of at least *count ints each.
+ */
+int ncs_tree_pairs(ncs_ctx* ctx, int64_t* count, int* target, int* source, int* level, int* kind);
+
+/*
+ * Tree statistics into out[0..n): levels, grid groups, grid points, P2L work items,
+ * P2L kernel evaluations, direct kernel evaluations, L2P node-grid products,
+ * direct (target, source) patch pairs, distinct grid shapes. Builds the host tree if
+ * needed (host-only).
+ */
+int ncs_tree_stats(ncs_ctx* ctx, int64_t* out, int n);
+
 /* Selects NCS_METHOD_AUTO / DIRECT / TREE for later products and solves. */
 int ncs_set_method(ncs_ctx* ctx, int method);
 
@@ -149,6 +183,15 @@ int ncs_matvec(ncs_ctx* ctx, const double* x, double* y, int precision);
 /* As ncs_matvec with device pointers x, y (N*K doubles) on the given stream
  * (cudaStream_t, NULL = legacy default stream). Asynchronous. */
 int ncs_matvec_dev(ncs_ctx* ctx, const double* x, double* y, int precision, void* stream);
+
+/*
+ * As ncs_matvec_dev, synchronous, with CUDA-event times (milliseconds) of each stage
+ * of Step 3 written to ms[0..n): outgoing map (3.1), P2L onto incoming grids (3.2),
+ * grid coefficients (first half of 3.4), direct sums at the Zernike nodes (3.3 and
+ * small groups; the whole sum for the direct method), L2P interpolation (second half
+ * of 3.4), apply P (3.5), total. Stages that do not run report 0.
+ */
+int ncs_profile_matvec(ncs_ctx* ctx, const double* x, double* y, int precision, void* stream, double* ms, int n);
 
 /*
  * The multiple-scattering field before the transform P (Section 7, end of Step 4):

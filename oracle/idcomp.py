@@ -62,9 +62,11 @@ class IDResult:
     rdiag: np.ndarray
 
 
-def interpolative_decomposition(op, tau, nper=10):
-    """ID of the training matrix and the outgoing map T = Pi W B."""
-    xt = training_grid(op.eps, tau, nper)
+def interpolative_decomposition(op, tau, nper=10, rho_min_factor=2.0):
+    """ID of the training matrix and the outgoing map T = Pi W B, for the far field
+    beyond rho_min_factor * eps (2 eps in Section 7.1; larger values give the coarser
+    per-level representations of "Optimizations and parallelization")."""
+    xt = training_grid(op.eps, tau, nper, rho_min_factor)
     xf = fine_points(op)
     A = G_on_surface(chord(xt[:, None, :], xf[None, :, :]), op.mode)
     R, piv = sla.qr(A, mode="r", pivoting=True, check_finite=False)

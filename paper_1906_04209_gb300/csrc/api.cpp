@@ -94,20 +94,41 @@ void free_all(ncs_ctx* c) {
   dev_free(d.PT64);
   dev_free(d.PT32);
   dev_free(d.I);
+  dev_free(d.rep_p);
+  dev_free(d.rep_off);
+  dev_free(d.rep_rho);
   if (c->stream) cudaStreamDestroy(c->stream);
   c->stream = nullptr;
 }
 
-// Uploads the precompute (T, P transposed, node and skeleton offsets, I).
+// Uploads the precompute: all outgoing representations stacked (T_k transposed into one
+// K x p_total matrix, skeleton offsets), P transposed, Zernike-node offsets, I.
 void upload_operator(ncs_ctx* c) {
   const ncs::Precomputed& pc = c->pc;
   DeviceData& d = c->d;
   d.K = pc.K;
   d.Kstar = pc.Kstar;
-  d.p = pc.p;
-  std::vector<double> TT((size_t)pc.K * pc.p), PT((size_t)pc.Kstar * pc.K);
-  for (int m = 0; m < pc.p; ++m)
-    for (int k = 0; k < pc.K; ++k) TT[(size_t)k * pc.p + m] = pc.T[(size_t)m * pc.K + k];
+  const int nrep = (int)pc.reps.size();
+  std::vector<int> rp(nrep), ro(nrep);
+  std::vector<double> rr(nrep);
+  int pt = 0, pmax = 0;
+  for (int r = 0; r < nrep; ++r) {
+    rp[r] = pc.reps[r].p;
+    ro[r] = pt;
+    rr[r] = pc.reps[r].rho_min;
+    pt += rp[r];
+    pmax = std::max(pmax, rp[r]);
+  }
+  d.p = pt;
+  d.pmax = pmax;
+  d.p0 = rp[0];
+  d.nrep = nrep;
+  std::vector<double> TT((size_t)pc.K * pt), sl(3 * (size_t)pt), PT((size_t)pc.Kstar * pc.K);
+  for (int r = 0; r < nrep; ++r)
+    for (int m = 0; m < rp[r]; ++m) {
+      for (int k = 0; k < pc.K; ++k) TT[(size_t)k * pt + ro[r] + m] = pc.reps[r].T[(size_t)m * pc.K + k];
+      for (int a = 0; a < 3; ++a) sl[3 * (size_t)(ro[r] + m) + a] = pc.reps[r].sloc[3 * (size_t)m + a];
+    }
   for (int j = 0; j < pc.K; ++j)
     for (int q = 0; q < pc.Kstar; ++q) PT[(size_t)q * pc.K + j] = pc.P[(size_t)j * pc.Kstar + q];
   std::vector<float> TT32(TT.begin(), TT.end()), PT32(PT.begin(), PT.end());
@@ -116,8 +137,11 @@ void upload_operator(ncs_ctx* c) {
   d.PT64 = dev_upload(PT);
   d.PT32 = dev_upload(PT32);
   d.zloc = dev_upload(pc.zloc);
-  d.sloc = dev_upload(pc.sloc);
+  d.sloc = dev_upload(sl);
   d.I = dev_upload(pc.I);
+  d.rep_p = dev_upload(rp);
+  d.rep_off = dev_upload(ro);
+  d.rep_rho = dev_upload(rr);
 }
 
 int finish(ncs_ctx* c, const Fail& f) {
@@ -193,7 +217,7 @@ void field(ncs_ctx* c, const double* x, int prec, cudaStream_t s) {
     ensure_tree(c);
     CU(ncs::launch_tree_field(c->d, c->tdev, c->pc.mode, prec, s));
   } else {
-    CU(ncs::launch_direct_field(c->d, c->pc.mode, prec, s));
+    CU(ncs::launch_direct_field(c->d, c->pc.mode, prec, c->pc.eps, s));
   }
 }
 
@@ -412,34 +436,49 @@ int ncs_create(double eps, int mode, int K, const ncs_params* params, ncs_ctx** 
   }
 }
 
-int ncs_create_from_operator(double eps, int mode, int K, int p, const double* T, const double* skel_t,
-                             const double* skel_theta, const double* I, const ncs_params* params,
-                             ncs_ctx** out) {
+int ncs_create_from_operators(double eps, int mode, int K, int nrep, const double* rho_min, const int* p,
+                              const double* T, const double* skel_t, const double* skel_theta, const double* I,
+                              const ncs_params* params, ncs_ctx** out) {
   if (!out) return NCS_E_INPUT;
   *out = nullptr;
   ncs_ctx* c = nullptr;
   try {
     if (!(eps > 0.0 && eps < 1.0)) throw Fail{NCS_E_INPUT, "eps must be in (0, 1)"};
     if (mode != NCS_EXTERIOR && mode != NCS_INTERIOR) throw Fail{NCS_E_INPUT, "mode must be 0 or 1"};
-    if (K < 1 || K > 2000 || p < 1 || p > 100000) throw Fail{NCS_E_INPUT, "K or p out of range"};
-    if (!T || !skel_t || !skel_theta || !I) throw Fail{NCS_E_INPUT, "NULL operator array"};
+    if (K < 1 || K > 2000 || nrep < 1 || nrep > 64) throw Fail{NCS_E_INPUT, "K or nrep out of range"};
+    if (!rho_min || !p || !T || !skel_t || !skel_theta || !I) throw Fail{NCS_E_INPUT, "NULL operator array"};
     c = new_ctx(params);
     validate_params(c->prm);
     c->from_operator = true;
     ncs::precompute_zernike(eps, K, c->pc);
     c->pc.mode = mode;
-    c->pc.p = p;
-    c->pc.T.assign(T, T + (size_t)p * K);
-    c->pc.st.assign(skel_t, skel_t + p);
-    c->pc.sth.assign(skel_theta, skel_theta + p);
     c->pc.I.assign(I, I + K);
-    c->pc.sloc.resize(3 * (size_t)p);
-    for (int m = 0; m < p; ++m) {
-      if (!(skel_t[m] >= 0.0 && skel_t[m] <= eps)) throw Fail{NCS_E_INPUT, "skeleton t outside [0, eps]"};
-      ncs::local_offset(skel_t[m], skel_theta[m], &c->pc.sloc[3 * (size_t)m]);
+    size_t off = 0;
+    for (int r = 0; r < nrep; ++r) {
+      if (p[r] < 1 || p[r] > 100000) throw Fail{NCS_E_INPUT, "p out of range"};
+      if (!(rho_min[r] >= 2.0 * eps * (1.0 - 1e-12)) || (r > 0 && !(rho_min[r] > rho_min[r - 1])))
+        throw Fail{NCS_E_INPUT, "far-field radii must start at >= 2 eps and increase"};
+      ncs::OutRep rep;
+      rep.rho_min = rho_min[r];
+      rep.p = p[r];
+      rep.T.assign(T + off * K, T + (off + p[r]) * K);
+      rep.st.assign(skel_t + off, skel_t + off + p[r]);
+      rep.sth.assign(skel_theta + off, skel_theta + off + p[r]);
+      rep.sloc.resize(3 * (size_t)p[r]);
+      for (int m = 0; m < p[r]; ++m) {
+        if (!(rep.st[m] >= 0.0 && rep.st[m] <= eps)) throw Fail{NCS_E_INPUT, "skeleton t outside [0, eps]"};
+        ncs::local_offset(rep.st[m], rep.sth[m], &rep.sloc[3 * (size_t)m]);
+      }
+      for (double v : rep.T)
+        if (!std::isfinite(v)) throw Fail{NCS_E_INPUT, "non-finite T"};
+      c->pc.reps.push_back(std::move(rep));
+      off += p[r];
     }
-    for (size_t q = 0; q < c->pc.T.size(); ++q)
-      if (!std::isfinite(c->pc.T[q])) throw Fail{NCS_E_INPUT, "non-finite T"};
+    c->pc.p = c->pc.reps[0].p;
+    c->pc.T = c->pc.reps[0].T;
+    c->pc.st = c->pc.reps[0].st;
+    c->pc.sth = c->pc.reps[0].sth;
+    c->pc.sloc = c->pc.reps[0].sloc;
     *out = c;
     return NCS_OK;
   } catch (const Fail& f) {
@@ -455,6 +494,26 @@ int ncs_create_from_operator(double eps, int mode, int K, int p, const double* T
     }
     return NCS_E_OOM;
   }
+}
+
+int ncs_create_from_operator(double eps, int mode, int K, int p, const double* T, const double* skel_t,
+                             const double* skel_theta, const double* I, const ncs_params* params, ncs_ctx** out) {
+  const double rho = 2.0 * eps;
+  return ncs_create_from_operators(eps, mode, K, 1, &rho, &p, T, skel_t, skel_theta, I, params, out);
+}
+
+int ncs_get_reps(const ncs_ctx* c, int* nrep, double* rho_min, int* p) {
+  if (!c || !nrep) return NCS_E_INPUT;
+  const int n = (int)c->pc.reps.size();
+  if (rho_min && p) {
+    if (*nrep < n) return NCS_E_INPUT;
+    for (int r = 0; r < n; ++r) {
+      rho_min[r] = c->pc.reps[r].rho_min;
+      p[r] = c->pc.reps[r].p;
+    }
+  }
+  *nrep = n;
+  return NCS_OK;
 }
 
 int ncs_info(const ncs_ctx* c, int64_t* out, int n) {
@@ -523,6 +582,49 @@ int ncs_set_patches(ncs_ctx* c, int64_t N, const double* centres) {
   }
 }
 
+int ncs_tree_pairs(ncs_ctx* c, int64_t* count, int* target, int* source, int* level, int* kind) {
+  if (!c || !count) return NCS_E_INPUT;
+  try {
+    if (c->centres.empty()) throw Fail{NCS_E_STATE, "no patches: call ncs_set_patches first"};
+    std::vector<int> t, s, l, k;
+    ncs::TreeOptions to;
+    to.grid_tol = c->prm.grid_tol;
+    to.eps = c->pc.eps;
+    ncs::tree_pairs(c->centres, c->pc, to, t, s, l, k);
+    if (target && source && level && kind) {
+      if (*count < (int64_t)t.size()) throw Fail{NCS_E_INPUT, "pair buffers too small"};
+      std::memcpy(target, t.data(), t.size() * sizeof(int));
+      std::memcpy(source, s.data(), s.size() * sizeof(int));
+      std::memcpy(level, l.data(), l.size() * sizeof(int));
+      std::memcpy(kind, k.data(), k.size() * sizeof(int));
+    }
+    *count = (int64_t)t.size();
+    return NCS_OK;
+  } catch (const Fail& f) {
+    return finish(c, f);
+  } catch (const std::exception& e) {
+    return finish(c, Fail{NCS_E_INPUT, std::string("tree: ") + e.what()});
+  }
+}
+
+int ncs_tree_stats(ncs_ctx* c, int64_t* out, int n) {
+  if (!c || !out) return NCS_E_INPUT;
+  try {
+    if (c->centres.empty()) throw Fail{NCS_E_STATE, "no patches: call ncs_set_patches first"};
+    ensure_tree_host(c);
+    const ncs::TreeHost& t = c->tree;
+    const int64_t v[9] = {t.levels, (int64_t)t.gR.size(), t.total_grid_points, (int64_t)t.witem_group.size(),
+                          t.p2l_pairs, t.direct_pairs, t.l2p_evals, t.pd_off.empty() ? 0 : t.pd_off.back(),
+                          (int64_t)t.shapes.size()};
+    for (int i = 0; i < n && i < 9; ++i) out[i] = v[i];
+    return NCS_OK;
+  } catch (const Fail& f) {
+    return finish(c, f);
+  } catch (const std::exception& e) {
+    return finish(c, Fail{NCS_E_INPUT, std::string("tree: ") + e.what()});
+  }
+}
+
 int ncs_set_method(ncs_ctx* c, int method) {
   if (!c) return NCS_E_INPUT;
   if (method < 0 || method > 2) return finish(c, Fail{NCS_E_INPUT, "bad method"});
@@ -569,6 +671,45 @@ int ncs_field_dev(ncs_ctx* c, const double* x, double* z, int precision, void* s
   } catch (const std::exception& e) {
     return finish(c, Fail{NCS_E_INPUT, e.what()});
   }
+}
+
+int ncs_profile_matvec(ncs_ctx* c, const double* x, double* y, int precision, void* stream, double* ms, int n) {
+  cudaEvent_t ev[8] = {};
+  int rc = NCS_OK;
+  try {
+    if (!c) throw Fail{NCS_E_INPUT, "null context"};
+    if (!x || !y || !ms) throw Fail{NCS_E_INPUT, "NULL argument"};
+    if (precision != NCS_FP64 && precision != NCS_FP32) throw Fail{NCS_E_INPUT, "precision must be FP64 or FP32"};
+    check_ready(c);
+    cudaStream_t s = (cudaStream_t)stream;
+    for (auto& e : ev) CU(cudaEventCreate(&e));
+    CU(cudaEventRecord(ev[0], s));
+    CU(ncs::launch_outgoing(c->d, x, precision, s));
+    if (use_tree(c)) {
+      ensure_tree(c);
+      CU(ncs::launch_tree_field(c->d, c->tdev, c->pc.mode, precision, s, ev + 1));
+    } else {
+      CU(cudaEventRecord(ev[1], s));
+      CU(cudaEventRecord(ev[2], s));
+      CU(cudaEventRecord(ev[3], s));
+      CU(ncs::launch_direct_field(c->d, c->pc.mode, precision, c->pc.eps, s));
+      CU(cudaEventRecord(ev[4], s));
+      CU(cudaEventRecord(ev[5], s));
+    }
+    CU(ncs::launch_apply_P(c->d, x, y, s));
+    CU(cudaEventRecord(ev[6], s));
+    CU(cudaEventSynchronize(ev[6]));
+    // stages: outgoing, P2L, coefficients, direct, L2P, apply P, total
+    float t[7];
+    for (int k = 0; k < 6; ++k) CU(cudaEventElapsedTime(&t[k], ev[k], ev[k + 1]));
+    CU(cudaEventElapsedTime(&t[6], ev[0], ev[6]));
+    for (int k = 0; k < n && k < 7; ++k) ms[k] = t[k];
+  } catch (const Fail& f) {
+    rc = finish(c, f);
+  }
+  for (auto& e : ev)
+    if (e) cudaEventDestroy(e);
+  return rc;
 }
 
 int ncs_matvec(ncs_ctx* c, const double* x, double* y, int precision) {

@@ -14,12 +14,19 @@ namespace ncs {
 
 // Device-resident data of one patch layout plus the precompute.
 struct DeviceData {
-  int K = 0, Kstar = 0, p = 0;
+  int K = 0, Kstar = 0;
+  int p = 0;                   // skeleton points over all representations (p_total)
+  int nrep = 0;                // outgoing representations (increasing far-field radius)
+  int pmax = 0;                // largest p_k
+  int p0 = 0;                  // p of representation 0 (far field beyond 2 eps)
+  int* rep_p = nullptr;        // nrep: p_k
+  int* rep_off = nullptr;      // nrep: column offset of representation k
+  double* rep_rho = nullptr;   // nrep: far-field radius (geodesic) of representation k
   int64_t N = 0;
   double* centres = nullptr;   // N*3
   double* zloc = nullptr;      // Kstar*3 local offsets of the Zernike nodes
-  double* sloc = nullptr;      // p*3 local offsets of the skeleton points
-  double* TT64 = nullptr;      // K*p, T transposed
+  double* sloc = nullptr;      // p*3 local offsets of the skeleton points (all representations)
+  double* TT64 = nullptr;      // K*p, all T_k stacked and transposed
   float* TT32 = nullptr;
   double* PT64 = nullptr;      // Kstar*K, P transposed
   float* PT32 = nullptr;
@@ -34,7 +41,7 @@ struct DeviceData {
 // ---- launchers (kernels.cu)
 cudaError_t launch_skeleton_offsets(const DeviceData& d, cudaStream_t s);
 cudaError_t launch_outgoing(const DeviceData& d, const double* x, int prec, cudaStream_t s);
-cudaError_t launch_direct_field(const DeviceData& d, int mode, int prec, cudaStream_t s);
+cudaError_t launch_direct_field(const DeviceData& d, int mode, int prec, double eps, cudaStream_t s);
 cudaError_t launch_apply_P(const DeviceData& d, const double* x, double* y, cudaStream_t s);
 cudaError_t launch_eval(const DeviceData& d, int mode, int64_t M, const double* targets,
                         double* out, cudaStream_t s);

@@ -89,23 +89,33 @@ cudaError_t launch_outgoing(const DeviceData& d, const double* x, int prec, cuda
 // Direct far-field sums at the Zernike nodes (Section 7.1, without the tree).
 // One block row per target patch i; each thread owns DF_NT target nodes. Source
 // patches are staged JT at a time in shared memory as (offset from c_i, rho)
-// quadruples; the self patch gets rho = 0 at a distant dummy position. Offsets are
-// formed in FP64 (c_j - c_i) before rounding, so the FP32 path keeps relative
-// accuracy even for neighbours 2 eps apart. FP32 partial sums are folded into an
-// FP64 accumulator once per tile.
+// quadruples. Each source patch j uses the coarsest outgoing representation valid at
+// its distance (far-field radius <= geodesic(c_i, c_j) - eps, the farthest a node of
+// patch i can be from c_i); the self patch is skipped. Offsets are formed in FP64
+// (c_j - c_i) before rounding, so the FP32 path keeps relative accuracy even for
+// neighbours 3 eps apart. FP32 partial sums are folded into an FP64 accumulator once
+// per tile.
 constexpr int DF_THREADS = 256;
 constexpr int DF_NT = 2;
 constexpr int DF_JTMAX = 8;
 
+__device__ __forceinline__ int select_rep(double dist, int nrep, const double* __restrict__ rep_rho) {
+  int k = 0;
+  while (k + 1 < nrep && rep_rho[k + 1] <= dist) ++k;
+  return k;
+}
+
 template <typename R, int MODE>
 __global__ void __launch_bounds__(DF_THREADS) direct_field_kernel(
-    int64_t N, int p, int Kstar, int JT, const double* __restrict__ centres,
+    int64_t N, int pt, int Kstar, int JT, int nrep, const int* __restrict__ rep_p, const int* __restrict__ rep_off,
+    const double* __restrict__ rep_rho, double eps, const double* __restrict__ centres,
     const double* __restrict__ zloc, const R* __restrict__ soff, const R* __restrict__ rho,
     double* __restrict__ z) {
   using V4 = typename Vec4<R>::type;
   extern __shared__ unsigned char df_smem[];
-  V4* S = reinterpret_cast<V4*>(df_smem);  // JT * p
+  V4* S = reinterpret_cast<V4*>(df_smem);  // JT * pmax
   __shared__ double D[DF_JTMAX][3];
+  __shared__ int toff[DF_JTMAX + 1], tcol[DF_JTMAX];
   const int64_t i = blockIdx.x;
   const double cx = centres[3 * i], cy = centres[3 * i + 1], cz = centres[3 * i + 2];
   double e1[3], e2[3];
@@ -125,31 +135,42 @@ __global__ void __launch_bounds__(DF_THREADS) direct_field_kernel(
   }
   for (int64_t j0 = 0; j0 < N; j0 += JT) {
     const int nj = (int)min((int64_t)JT, N - j0);
-    if (threadIdx.x < nj * 3) {
-      const int jj = threadIdx.x / 3, c = threadIdx.x - 3 * jj;
-      D[jj][c] = centres[3 * (j0 + jj) + c] - centres[3 * i + c];
+    __syncthreads();
+    if (threadIdx.x < nj) {
+      const int64_t j = j0 + threadIdx.x;
+      double d0 = centres[3 * j] - cx, d1 = centres[3 * j + 1] - cy, d2 = centres[3 * j + 2] - cz;
+      D[threadIdx.x][0] = d0;
+      D[threadIdx.x][1] = d1;
+      D[threadIdx.x][2] = d2;
+      int cnt = 0, col = 0;
+      if (j != i) {
+        const double dist = 2.0 * asin(fmin(1.0, 0.5 * sqrt(d0 * d0 + d1 * d1 + d2 * d2)));
+        const int k = select_rep(dist - eps, nrep, rep_rho);
+        cnt = rep_p[k];
+        col = rep_off[k];
+      }
+      toff[threadIdx.x + 1] = cnt;
+      tcol[threadIdx.x] = col;
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < nj * p; idx += DF_THREADS) {
-      const int jj = idx / p;
-      const int64_t j = j0 + jj;
-      const int64_t g = j * p + (idx - jj * p);
+    if (threadIdx.x == 0) {
+      toff[0] = 0;
+      for (int jj = 0; jj < nj; ++jj) toff[jj + 1] += toff[jj];
+    }
+    __syncthreads();
+    const int ns = toff[nj];
+    for (int idx = threadIdx.x; idx < ns; idx += DF_THREADS) {
+      int jj = 0;
+      while (idx >= toff[jj + 1]) ++jj;
+      const int64_t g = (j0 + jj) * pt + tcol[jj] + (idx - toff[jj]);
       V4 v;
-      if (j != i) {
-        v.x = (R)D[jj][0] + soff[3 * g];
-        v.y = (R)D[jj][1] + soff[3 * g + 1];
-        v.z = (R)D[jj][2] + soff[3 * g + 2];
-        v.w = rho[g];
-      } else {
-        v.x = (R)4;
-        v.y = (R)4;
-        v.z = (R)4;
-        v.w = (R)0;
-      }
+      v.x = (R)D[jj][0] + soff[3 * g];
+      v.y = (R)D[jj][1] + soff[3 * g + 1];
+      v.z = (R)D[jj][2] + soff[3 * g + 2];
+      v.w = rho[g];
       S[idx] = v;
     }
     __syncthreads();
-    const int ns = nj * p;
     R part[DF_NT];
 #pragma unroll
     for (int t = 0; t < DF_NT; ++t) part[t] = 0;
@@ -169,34 +190,44 @@ __global__ void __launch_bounds__(DF_THREADS) direct_field_kernel(
     }
 #pragma unroll
     for (int t = 0; t < DF_NT; ++t) acc[t] += (double)part[t];
-    __syncthreads();
   }
 #pragma unroll
   for (int t = 0; t < DF_NT; ++t)
     if (kk[t] < Kstar) z[i * Kstar + kk[t]] = acc[t];
 }
 
-cudaError_t launch_direct_field(const DeviceData& d, int mode, int prec, cudaStream_t s) {
+template <typename K>
+static cudaError_t allow_smem(K kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+cudaError_t launch_direct_field(const DeviceData& d, int mode, int prec, double eps, cudaStream_t s) {
   const size_t v4 = (prec == NCS_FP64) ? sizeof(double4) : sizeof(float4);
-  int JT = (int)std::min<size_t>(DF_JTMAX, (40 * 1024) / (v4 * (size_t)d.p));
+  int JT = (int)std::min<size_t>(DF_JTMAX, (40 * 1024) / (v4 * (size_t)d.pmax));
   if (JT < 1) JT = 1;
-  const size_t smem = (size_t)JT * d.p * v4;
+  const size_t smem = (size_t)JT * d.pmax * v4;
   dim3 grid((unsigned)d.N, (unsigned)((d.Kstar + DF_THREADS * DF_NT - 1) / (DF_THREADS * DF_NT)));
+  cudaError_t e;
+#define NCS_DF(R, M, SOFF, RHO)                                                                            \
+  do {                                                                                                     \
+    if ((e = allow_smem(direct_field_kernel<R, M>, smem)) != cudaSuccess) return e;                       \
+    direct_field_kernel<R, M><<<grid, DF_THREADS, smem, s>>>(d.N, d.p, d.Kstar, JT, d.nrep, d.rep_p,       \
+                                                             d.rep_off, d.rep_rho, eps, d.centres, d.zloc, \
+                                                             SOFF, RHO, d.z);                              \
+  } while (0)
   if (prec == NCS_FP64) {
     if (mode == 0)
-      direct_field_kernel<double, 0><<<grid, DF_THREADS, smem, s>>>(d.N, d.p, d.Kstar, JT, d.centres, d.zloc,
-                                                                    d.soff64, d.rho64, d.z);
+      NCS_DF(double, 0, d.soff64, d.rho64);
     else
-      direct_field_kernel<double, 1><<<grid, DF_THREADS, smem, s>>>(d.N, d.p, d.Kstar, JT, d.centres, d.zloc,
-                                                                    d.soff64, d.rho64, d.z);
+      NCS_DF(double, 1, d.soff64, d.rho64);
   } else {
     if (mode == 0)
-      direct_field_kernel<float, 0><<<grid, DF_THREADS, smem, s>>>(d.N, d.p, d.Kstar, JT, d.centres, d.zloc,
-                                                                   d.soff32, d.rho32, d.z);
+      NCS_DF(float, 0, d.soff32, d.rho32);
     else
-      direct_field_kernel<float, 1><<<grid, DF_THREADS, smem, s>>>(d.N, d.p, d.Kstar, JT, d.centres, d.zloc,
-                                                                   d.soff32, d.rho32, d.z);
+      NCS_DF(float, 1, d.soff32, d.rho32);
   }
+#undef NCS_DF
   return cudaGetLastError();
 }
 
@@ -232,7 +263,7 @@ cudaError_t launch_apply_P(const DeviceData& d, const double* x, double* y, cuda
 // Off-surface single-layer potential u(x) = sum_j sum_m G(x, s_jm) rho_jm, FP64,
 // one block per target with a block reduction.
 template <int MODE>
-__global__ void __launch_bounds__(256) eval_kernel(int64_t N, int p, const double* __restrict__ centres,
+__global__ void __launch_bounds__(256) eval_kernel(int64_t N, int p, int pt, const double* __restrict__ centres,
                                                    const double* __restrict__ soff, const double* __restrict__ rho,
                                                    const double* __restrict__ targets, double* __restrict__ out) {
   __shared__ double red[256];
@@ -240,8 +271,9 @@ __global__ void __launch_bounds__(256) eval_kernel(int64_t N, int p, const doubl
   const double x0 = targets[3 * t], x1 = targets[3 * t + 1], x2 = targets[3 * t + 2];
   const double rx = sqrt(x0 * x0 + x1 * x1 + x2 * x2);
   double acc = 0.0;
-  for (int64_t g = threadIdx.x; g < N * p; g += blockDim.x) {
-    const int64_t j = g / p;
+  for (int64_t h = threadIdx.x; h < N * p; h += blockDim.x) {
+    const int64_t j = h / p;
+    const int64_t g = j * pt + (h - j * p);  // representation 0 (the finest) of patch j
     const double s0 = centres[3 * j] + soff[3 * g], s1 = centres[3 * j + 1] + soff[3 * g + 1],
                  s2 = centres[3 * j + 2] + soff[3 * g + 2];
     const double d0 = x0 - s0, d1 = x1 - s1, d2 = x2 - s2;
@@ -267,9 +299,9 @@ cudaError_t launch_eval(const DeviceData& d, int mode, int64_t M, const double* 
                         cudaStream_t s) {
   if (M == 0) return cudaSuccess;
   if (mode == 0)
-    eval_kernel<0><<<(unsigned)M, 256, 0, s>>>(d.N, d.p, d.centres, d.soff64, d.rho64, targets, out);
+    eval_kernel<0><<<(unsigned)M, 256, 0, s>>>(d.N, d.p0, d.p, d.centres, d.soff64, d.rho64, targets, out);
   else
-    eval_kernel<1><<<(unsigned)M, 256, 0, s>>>(d.N, d.p, d.centres, d.soff64, d.rho64, targets, out);
+    eval_kernel<1><<<(unsigned)M, 256, 0, s>>>(d.N, d.p0, d.p, d.centres, d.soff64, d.rho64, targets, out);
   return cudaGetLastError();
 }
 

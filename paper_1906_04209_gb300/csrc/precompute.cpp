@@ -419,31 +419,49 @@ void precompute(double eps, int mode, int K, const PrecomputeOptions& opt, Preco
   const double t1 = now_s();
   out.seconds_onepatch = t1 - t0;
 
-  // ---- interpolative decomposition of the far field (Section 7.1)
-  // training grid on {rho > id_rho_min * eps}: dyadic radial panels, azimuthal count
-  // from the (eps/rho)^m decay of fields generated inside the patch
-  std::vector<double> xt;
+  // ---- interpolative decompositions of the far field (Section 7.1), one per far-field
+  // radius of a ladder rho_min = 2, 3, 4, 6, 8, 12, ... eps (the per-level recompression
+  // of "Optimizations and parallelization": a source seen from farther away needs fewer
+  // skeleton points). The training grid on {rho > rho_min} is made of radial panels whose
+  // lower edges are the ladder radii (then doubling up to pi), with Gauss-Legendre nodes
+  // and an azimuthal count from the (eps/rho)^m decay of fields generated in the patch.
+  std::vector<double> ladder;
   {
-    std::vector<double> e2;
-    e2.push_back(opt.id_rho_min * eps);
-    while (e2.back() * 2.0 < kPi) e2.push_back(e2.back() * 2.0);
-    e2.push_back(kPi);
+    double r = opt.id_rho_min;
+    ladder.push_back(r);
+    if (opt.multilevel) {
+      for (int it = 0; it < 64; ++it) {
+        r *= (it % 2 == 0) ? 1.5 : 4.0 / 3.0;
+        if (r * eps > opt.id_ladder_max) break;
+        ladder.push_back(r);
+      }
+    }
+  }
+  std::vector<double> pedges;
+  for (double l : ladder) pedges.push_back(l * eps);
+  while (pedges.back() * 2.0 < kPi) pedges.push_back(pedges.back() * 2.0);
+  pedges.push_back(kPi);
+  const int npanel = (int)pedges.size() - 1;
+  std::vector<double> xt;
+  std::vector<int> prow(npanel + 1, 0);
+  {
     std::vector<double> px, pw;
     gauss_legendre(opt.id_nper, px, pw);
-    for (size_t s = 0; s + 1 < e2.size(); ++s) {
-      double a = e2[s], b = e2[s + 1];
+    for (int s = 0; s < npanel; ++s) {
+      const double a = pedges[s], b = pedges[s + 1];
       int m = (int)std::ceil(std::log(opt.id_tol / 10.0) / std::log(eps / a));
       m = std::max(m, 8);
-      int nphi = 2 * m + 1;
+      const int nphi = 2 * m + 1;
       for (int q = 0; q < opt.id_nper; ++q) {
-        double rho = 0.5 * (a + b) + 0.5 * (b - a) * px[q];
+        const double rho = 0.5 * (a + b) + 0.5 * (b - a) * px[q];
         for (int f = 0; f < nphi; ++f) {
-          double phi = 2.0 * kPi * f / nphi;
+          const double phi = 2.0 * kPi * f / nphi;
           xt.push_back(std::sin(rho) * std::cos(phi));
           xt.push_back(std::sin(rho) * std::sin(phi));
           xt.push_back(std::cos(rho));
         }
       }
+      prow[s + 1] = (int)(xt.size() / 3);
     }
   }
   const int nt = (int)(xt.size() / 3);
@@ -458,141 +476,170 @@ void precompute(double eps, int mode, int K, const PrecomputeOptions& opt, Preco
   const double sgn = (mode == 0) ? -1.0 : 1.0;
   auto Gsurf = [sgn](double d) { return 2.0 / d + sgn * std::log(2.0 / d) - std::log1p(0.5 * d); };
 
-  int ks = std::min(256, nt);
-  std::vector<double> Y;      // column-major ks x nf
-  std::vector<int> piv;
-  int p = 0;
-  for (;;) {
-    // Y = Omega A, Omega Gaussian ks x nt (counter-based), A(j,l) = G(x^t_j, x^f_l)
-    std::vector<double> Om((size_t)ks * nt);
-    for (int r = 0; r < ks; ++r)
-      for (int j = 0; j < nt; ++j) Om[(size_t)r * nt + j] = normal_variate(((uint64_t)r << 32) + j + 0x5eedull);
-    Y.assign((size_t)ks * nf, 0.0);
-    const int CB = 32;
-#pragma omp parallel
-    {
-      std::vector<double> Ab((size_t)nt * CB);
-#pragma omp for schedule(dynamic, 1)
-      for (int cb = 0; cb < (nf + CB - 1) / CB; ++cb) {
-        const int l0 = cb * CB, nl = std::min(CB, nf - l0);
-        for (int j = 0; j < nt; ++j)
-          for (int c = 0; c < nl; ++c) {
-            const double* a = &xt[3 * (size_t)j];
-            const double* b = &xf[3 * (size_t)(l0 + c)];
-            double dx = a[0] - b[0], dy = a[1] - b[1], dz = a[2] - b[2];
-            Ab[(size_t)j * CB + c] = Gsurf(std::sqrt(dx * dx + dy * dy + dz * dz));
-          }
-        for (int c = 0; c < nl; ++c) {
-          double* ycol = &Y[(size_t)(l0 + c) * ks];
-          for (int r = 0; r < ks; ++r) {
-            const double* om = &Om[(size_t)r * nt];
-            double s = 0.0;
-            for (int j = 0; j < nt; ++j) s += om[j] * Ab[(size_t)j * CB + c];
-            ycol[r] = s;
-          }
-        }
-      }
-    }
-    // column-pivoted Householder QR of Y, stopped at |R_kk| < tol |R_00|
+  // Column-pivoted Householder QR of a sketch Y (column-major ks x nf, destroyed),
+  // stopped at |R_kk| < tol |R_00|. Returns the rank; piv and the R factor stay in Y.
+  auto cpqr = [&](std::vector<double>& Y, int ks, std::vector<int>& piv) {
     piv.resize(nf);
     for (int l = 0; l < nf; ++l) piv[l] = l;
     std::vector<double> cn(nf), cn0(nf);
     for (int l = 0; l < nf; ++l) {
-      double s = 0.0;
-      for (int r = 0; r < ks; ++r) s += Y[(size_t)l * ks + r] * Y[(size_t)l * ks + r];
-      cn[l] = cn0[l] = s;
+      double v = 0.0;
+      for (int r = 0; r < ks; ++r) v += Y[(size_t)l * ks + r] * Y[(size_t)l * ks + r];
+      cn[l] = cn0[l] = v;
     }
     double r00 = 0.0;
-    p = 0;
+    int p = 0;
     std::vector<double> v(ks);
-    for (int s = 0; s < ks; ++s) {
-      int best = s;
-      for (int l = s + 1; l < nf; ++l)
+    for (int st = 0; st < ks; ++st) {
+      int best = st;
+      for (int l = st + 1; l < nf; ++l)
         if (cn[l] > cn[best]) best = l;
-      if (best != s) {
-        std::swap(piv[s], piv[best]);
-        std::swap(cn[s], cn[best]);
-        std::swap(cn0[s], cn0[best]);
-        std::swap_ranges(&Y[(size_t)s * ks], &Y[(size_t)s * ks] + ks, &Y[(size_t)best * ks]);
+      if (best != st) {
+        std::swap(piv[st], piv[best]);
+        std::swap(cn[st], cn[best]);
+        std::swap(cn0[st], cn0[best]);
+        std::swap_ranges(&Y[(size_t)st * ks], &Y[(size_t)st * ks] + ks, &Y[(size_t)best * ks]);
       }
-      double* col = &Y[(size_t)s * ks];
+      double* col = &Y[(size_t)st * ks];
       double nrm = 0.0;
-      for (int r = s; r < ks; ++r) nrm += col[r] * col[r];
+      for (int r = st; r < ks; ++r) nrm += col[r] * col[r];
       nrm = std::sqrt(nrm);
-      const double rss = (col[s] >= 0.0) ? -nrm : nrm;
-      if (s == 0) r00 = std::fabs(rss);
-      if (std::fabs(rss) < opt.id_tol * r00 || nrm == 0.0) {
-        p = s;
-        break;
-      }
-      for (int r = s; r < ks; ++r) v[r] = col[r];
-      v[s] -= rss;
+      const double rss = (col[st] >= 0.0) ? -nrm : nrm;
+      if (st == 0) r00 = std::fabs(rss);
+      if (std::fabs(rss) < opt.id_tol * r00 || nrm == 0.0) return st;
+      for (int r = st; r < ks; ++r) v[r] = col[r];
+      v[st] -= rss;
       double vv = 0.0;
-      for (int r = s; r < ks; ++r) vv += v[r] * v[r];
-      col[s] = rss;
-      for (int r = s + 1; r < ks; ++r) col[r] = 0.0;
+      for (int r = st; r < ks; ++r) vv += v[r] * v[r];
+      col[st] = rss;
+      for (int r = st + 1; r < ks; ++r) col[r] = 0.0;
 #pragma omp parallel for schedule(static)
-      for (int l = s + 1; l < nf; ++l) {
+      for (int l = st + 1; l < nf; ++l) {
         double* y = &Y[(size_t)l * ks];
         double dot = 0.0;
-        for (int r = s; r < ks; ++r) dot += v[r] * y[r];
+        for (int r = st; r < ks; ++r) dot += v[r] * y[r];
         const double f = 2.0 * dot / vv;
-        for (int r = s; r < ks; ++r) y[r] -= f * v[r];
-        double nn = cn[l] - y[s] * y[s];
+        for (int r = st; r < ks; ++r) y[r] -= f * v[r];
+        double nn = cn[l] - y[st] * y[st];
         if (nn < 1e-10 * cn0[l]) {  // recompute after cancellation
           nn = 0.0;
-          for (int r = s + 1; r < ks; ++r) nn += y[r] * y[r];
+          for (int r = st + 1; r < ks; ++r) nn += y[r] * y[r];
           cn0[l] = nn;
         }
         cn[l] = nn;
       }
-      p = s + 1;
+      p = st + 1;
     }
-    if (p < ks - 16 || ks >= nt) break;
-    ks = std::min(2 * ks, nt);  // rank not revealed by the sketch: enlarge it
-  }
-  if (p < 1) throw std::runtime_error("precompute: ID rank is zero");
-  out.p = p;
-  // Pi = [I, R11^-1 R12] in pivoted order; T = Pi W B
-  const int nrest = nf - p;
-  std::vector<double> X((size_t)p * nrest);  // X(m, c) row-major
+    return p;
+  };
+
+  // Pi = [I, R11^-1 R12] in pivoted order; T = Pi W B; skeleton coordinates.
+  auto finish_level = [&](const std::vector<double>& Y, int ks, const std::vector<int>& piv, int p,
+                          double rho_min, OutRep& rep) {
+    const int nrest = nf - p;
+    std::vector<double> X((size_t)p * nrest);
 #pragma omp parallel for schedule(static)
-  for (int c = 0; c < nrest; ++c) {
-    const double* y = &Y[(size_t)(p + c) * ks];
-    std::vector<double> xcol(p);
-    for (int m = p - 1; m >= 0; --m) {
-      double s = y[m];
-      for (int q = m + 1; q < p; ++q) s -= Y[(size_t)q * ks + m] * xcol[q];
-      xcol[m] = s / Y[(size_t)m * ks + m];
+    for (int c = 0; c < nrest; ++c) {
+      const double* y = &Y[(size_t)(p + c) * ks];
+      std::vector<double> xcol(p);
+      for (int m = p - 1; m >= 0; --m) {
+        double v = y[m];
+        for (int q = m + 1; q < p; ++q) v -= Y[(size_t)q * ks + m] * xcol[q];
+        xcol[m] = v / Y[(size_t)m * ks + m];
+      }
+      for (int m = 0; m < p; ++m) X[(size_t)m * nrest + c] = xcol[m];
     }
-    for (int m = 0; m < p; ++m) X[(size_t)m * nrest + c] = xcol[m];
-  }
-  out.T.assign((size_t)p * K, 0.0);
+    rep.rho_min = rho_min;
+    rep.p = p;
+    rep.T.assign((size_t)p * K, 0.0);
 #pragma omp parallel
-  {
-    std::vector<double> row(K);
+    {
+      std::vector<double> row(K);
 #pragma omp for schedule(static)
-    for (int m = 0; m < p; ++m) {
-      double* Tm = &out.T[(size_t)m * K];
-      WB(piv[m], row.data());
-      for (int j = 0; j < K; ++j) Tm[j] = row[j];
-      for (int c = 0; c < nrest; ++c) {
-        const double x = X[(size_t)m * nrest + c];
-        if (x == 0.0) continue;
-        WB(piv[p + c], row.data());
-        for (int j = 0; j < K; ++j) Tm[j] += x * row[j];
+      for (int m = 0; m < p; ++m) {
+        double* Tm = &rep.T[(size_t)m * K];
+        WB(piv[m], row.data());
+        for (int j = 0; j < K; ++j) Tm[j] = row[j];
+        for (int c = 0; c < nrest; ++c) {
+          const double x = X[(size_t)m * nrest + c];
+          if (x == 0.0) continue;
+          WB(piv[p + c], row.data());
+          for (int j = 0; j < K; ++j) Tm[j] += x * row[j];
+        }
       }
     }
+    rep.st.resize(p);
+    rep.sth.resize(p);
+    rep.sloc.resize(3 * (size_t)p);
+    for (int m = 0; m < p; ++m) {
+      const int l = piv[m];
+      rep.st[m] = tr[l / nth];
+      rep.sth[m] = thf[l % nth];
+      local_offset(rep.st[m], rep.sth[m], &rep.sloc[3 * (size_t)m]);
+    }
+  };
+
+  const int nlev = (int)ladder.size();
+  int ks = std::min(256, nt);
+  for (;;) {
+    out.reps.assign(nlev, OutRep());
+    // Gaussian sketch Omega (ks x nt, counter-based); panels are added from the outside
+    // in, so after adding panel k the running sum is the sketch of the training rows
+    // of {rho > ladder[k] eps}.
+    std::vector<double> Om((size_t)ks * nt);
+    for (int r = 0; r < ks; ++r)
+      for (int j = 0; j < nt; ++j) Om[(size_t)r * nt + j] = normal_variate(((uint64_t)r << 32) + j + 0x5eedull);
+    std::vector<double> Yrun((size_t)ks * nf, 0.0), Yc;
+    bool enlarge = false;
+    const int CB = 32;
+    for (int pan = npanel - 1; pan >= 0 && !enlarge; --pan) {
+      const int r0 = prow[pan], r1 = prow[pan + 1], nrw = r1 - r0;
+#pragma omp parallel
+      {
+        std::vector<double> Ab((size_t)nrw * CB);
+#pragma omp for schedule(dynamic, 1)
+        for (int cb = 0; cb < (nf + CB - 1) / CB; ++cb) {
+          const int l0 = cb * CB, nl = std::min(CB, nf - l0);
+          for (int j = 0; j < nrw; ++j)
+            for (int c = 0; c < nl; ++c) {
+              const double* a = &xt[3 * (size_t)(r0 + j)];
+              const double* b = &xf[3 * (size_t)(l0 + c)];
+              const double dx = a[0] - b[0], dy = a[1] - b[1], dz = a[2] - b[2];
+              Ab[(size_t)j * CB + c] = Gsurf(std::sqrt(dx * dx + dy * dy + dz * dz));
+            }
+          for (int c = 0; c < nl; ++c) {
+            double* ycol = &Yrun[(size_t)(l0 + c) * ks];
+            for (int r = 0; r < ks; ++r) {
+              const double* om = &Om[(size_t)r * nt + r0];
+              double v = 0.0;
+              for (int j = 0; j < nrw; ++j) v += om[j] * Ab[(size_t)j * CB + c];
+              ycol[r] += v;
+            }
+          }
+        }
+      }
+      if (pan < nlev) {
+        Yc = Yrun;
+        std::vector<int> piv;
+        const int p = cpqr(Yc, ks, piv);
+        if (p >= ks - 16 && ks < nt) {
+          enlarge = true;
+          break;
+        }
+        if (p < 1) throw std::runtime_error("precompute: ID rank is zero");
+        finish_level(Yc, ks, piv, p, ladder[pan] * eps, out.reps[pan]);
+      }
+    }
+    if (!enlarge) break;
+    ks = std::min(2 * ks, nt);  // rank not revealed by the sketch: enlarge it
   }
-  out.st.resize(p);
-  out.sth.resize(p);
-  out.sloc.resize(3 * (size_t)p);
-  for (int m = 0; m < p; ++m) {
-    const int l = piv[m];
-    out.st[m] = tr[l / nth];
-    out.sth[m] = thf[l % nth];
-    local_offset(out.st[m], out.sth[m], &out.sloc[3 * (size_t)m]);
-  }
+  // the finest representation (far field beyond id_rho_min eps) doubles as the
+  // single-level operator
+  out.p = out.reps[0].p;
+  out.T = out.reps[0].T;
+  out.st = out.reps[0].st;
+  out.sth = out.reps[0].sth;
+  out.sloc = out.reps[0].sloc;
   out.seconds_id = now_s() - t1;
 }
 

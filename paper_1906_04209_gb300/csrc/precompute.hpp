@@ -15,7 +15,19 @@ struct PrecomputeOptions {
   int id_nper = 10;         // training-grid Gauss nodes per radial panel
   int threads = 0;          // host threads (0: all)
   double id_rho_min = 2.0;  // far region starts at id_rho_min * eps
+  bool multilevel = true;   // also compress against farther regions (ladder x1.5, x4/3, ...)
+  double id_ladder_max = 1.0;  // largest far-field radius of the ladder (radians)
   bool keep_collocation = false;  // keep the modal collocation matrices (diagnostics)
+};
+
+// Outgoing representation valid for targets farther than rho_min (geodesic) from
+// the patch centre: rho = T f on p skeleton points (Section 7.1, eq. Tmap).
+struct OutRep {
+  double rho_min = 0.0;
+  int p = 0;
+  std::vector<double> T;        // p x K
+  std::vector<double> st, sth;  // skeleton (t, theta)
+  std::vector<double> sloc;     // p x 3 offsets in the patch frame
 };
 
 struct Precomputed {
@@ -30,6 +42,7 @@ struct Precomputed {
   std::vector<double> st, sth;       // skeleton (t, theta)
   std::vector<double> sloc;          // p x 3 offsets in the patch frame
   std::vector<double> I;             // K
+  std::vector<OutRep> reps;          // increasing rho_min; reps[0] equals (T, st, sth, sloc)
   std::vector<double> trad;          // radial collocation nodes
   std::vector<double> beta;          // nrad x K radial profiles
   std::vector<double> w;             // nf fine-grid weights

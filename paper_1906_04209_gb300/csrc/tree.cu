@@ -1,0 +1,523 @@
+// Device part of the tree product (Kaye & Greengard, Section 7, Step 3.2-3.4):
+//   P2L   : skeleton sources of the interaction list summed onto a group's incoming
+//           grid (parity-restricted Chebyshev radii x equispaced angles, Section 7.3);
+//   coef  : grid values -> Chebyshev-Fourier coefficients (the "q^2 to form the
+//           interpolant" of Step 3.4, done as an angular DFT then a radial transform);
+//   direct: sources evaluated directly at the Zernike nodes (leaf neighbours, and
+//           groups too small to profit from a grid);
+//   L2P   : every patch interpolates the grids of its groups at its Zernike nodes.
+#include <algorithm>
+#include <cstdint>
+#include <cstdio>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "device_common.cuh"
+#include "internal.hpp"
+#include "numerics.hpp"
+
+namespace ncs {
+
+namespace {
+
+template <typename R>
+struct V4T;
+template <>
+struct V4T<float> {
+  using type = float4;
+};
+template <>
+struct V4T<double> {
+  using type = double4;
+};
+
+template <typename T>
+cudaError_t up(T** d, const std::vector<T>& h) {
+  cudaError_t e = cudaMalloc(d, std::max<size_t>(1, h.size()) * sizeof(T));
+  if (e != cudaSuccess) return e;
+  if (!h.empty()) e = cudaMemcpy(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+  return e;
+}
+
+template <typename T>
+void fr(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+constexpr int P2L_THREADS = 256;
+constexpr int P2L_NT = 4;
+constexpr int P2L_JT = 8;
+
+// One block per work item (grid group g, a slice of its interaction-list patches).
+template <typename R, int MODE>
+__global__ void __launch_bounds__(P2L_THREADS) p2l_kernel(
+    const int* __restrict__ witem_group, const int* __restrict__ witem_rep, const int* __restrict__ rep_p,
+    const int* __restrict__ rep_off, int pt, const int64_t* __restrict__ witem_lo, const int64_t* __restrict__ witem_hi,
+    const int* __restrict__ isrc, const double* __restrict__ gcen, const int* __restrict__ gshape,
+    const int64_t* __restrict__ goff, const int* __restrict__ shape_nr, const int* __restrict__ shape_nth,
+    const R* __restrict__ gpos, const double* __restrict__ centres, const R* __restrict__ soff,
+    const R* __restrict__ rho, double* __restrict__ grid) {
+  using V4 = typename V4T<R>::type;
+  extern __shared__ unsigned char p2l_smem[];
+  V4* S = reinterpret_cast<V4*>(p2l_smem);
+  __shared__ double D[P2L_JT][3];
+  const int item = blockIdx.x;
+  const int g = witem_group[item];
+  const int rk = witem_rep[item];
+  const int p = rep_p[rk], col = rep_off[rk];
+  const int64_t lo = witem_lo[item], hi = witem_hi[item];
+  const int sh = gshape[g];
+  const int q = shape_nr[sh] * shape_nth[sh];
+  const int64_t off = goff[g];
+  const double gx = gcen[3 * g], gy = gcen[3 * g + 1], gz = gcen[3 * g + 2];
+  for (int base = 0; base < q; base += P2L_THREADS * P2L_NT) {
+    R ax[P2L_NT], ay[P2L_NT], az[P2L_NT];
+    double acc[P2L_NT];
+#pragma unroll
+    for (int t = 0; t < P2L_NT; ++t) {
+      const int a = base + t * P2L_THREADS + threadIdx.x;
+      if (a < q) {
+        ax[t] = gpos[3 * (off + a)];
+        ay[t] = gpos[3 * (off + a) + 1];
+        az[t] = gpos[3 * (off + a) + 2];
+      } else {
+        ax[t] = ay[t] = az[t] = (R)0;
+      }
+      acc[t] = 0.0;
+    }
+    for (int64_t s0 = lo; s0 < hi; s0 += P2L_JT) {
+      const int nj = (int)min((int64_t)P2L_JT, hi - s0);
+      __syncthreads();
+      if (threadIdx.x < nj * 3) {
+        const int jj = threadIdx.x / 3, c = threadIdx.x - 3 * jj;
+        const int j = isrc[s0 + jj];
+        D[jj][c] = centres[3 * j + c] - (c == 0 ? gx : (c == 1 ? gy : gz));
+      }
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < nj * p; idx += P2L_THREADS) {
+        const int jj = idx / p;
+        const int64_t gsrc = (int64_t)isrc[s0 + jj] * pt + col + (idx - jj * p);
+        V4 v;
+        v.x = (R)D[jj][0] + soff[3 * gsrc];
+        v.y = (R)D[jj][1] + soff[3 * gsrc + 1];
+        v.z = (R)D[jj][2] + soff[3 * gsrc + 2];
+        v.w = rho[gsrc];
+        S[idx] = v;
+      }
+      __syncthreads();
+      const int ns = nj * p;
+      R part[P2L_NT];
+#pragma unroll
+      for (int t = 0; t < P2L_NT; ++t) part[t] = 0;
+      for (int s = 0; s < ns; ++s) {
+        const V4 v = S[s];
+#pragma unroll
+        for (int t = 0; t < P2L_NT; ++t) {
+          const R dx = ax[t] - v.x, dy = ay[t] - v.y, dz = az[t] - v.z;
+          const R d2 = fma(dx, dx, fma(dy, dy, dz * dz));
+          R gv;
+          if constexpr (sizeof(R) == 8)
+            gv = green64<MODE>(d2);
+          else
+            gv = green32<MODE>(d2);
+          part[t] = fma(gv, v.w, part[t]);
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < P2L_NT; ++t) acc[t] += (double)part[t];
+    }
+#pragma unroll
+    for (int t = 0; t < P2L_NT; ++t) {
+      const int a = base + t * P2L_THREADS + threadIdx.x;
+      if (a < q) atomicAdd(&grid[off + a], acc[t]);
+    }
+  }
+}
+
+// Grid values -> coefficients. Layout per group: A[m][j] then B[m][j],
+// m = 0..nth/2-1, j = 0..nr-1, for the expansion
+//   F(r, th) = sum_m sum_j (A_mj cos m th + B_mj sin m th) T_{2j + (m mod 2)}(r / R).
+// Angular: C_m(r_a) = (2 - delta_m0)/nth sum_b F_ab cos(m th_b), S_m likewise with sin.
+// Radial (parity-restricted Chebyshev on the 2 nr first-kind nodes of [-R, R]):
+//   A_mj = (2 - delta_d0)/nr sum_a C_m(r_a) T_d(x_a), d = 2j + (m mod 2),
+//   x_a = cos((2a + 1) pi / (4 nr)).
+template <typename R>
+__global__ void __launch_bounds__(256) coef_kernel(const int* __restrict__ gshape, const int64_t* __restrict__ goff,
+                                                   const int* __restrict__ shape_nr, const int* __restrict__ shape_nth,
+                                                   const double* __restrict__ grid, double* __restrict__ coef) {
+  extern __shared__ double cf_smem[];
+  const int g = blockIdx.x;
+  const int sh = gshape[g];
+  const int nr = shape_nr[sh], nth = shape_nth[sh], q = nr * nth, mh = nth / 2;
+  const int64_t off = goff[g];
+  double* F = cf_smem;        // q
+  double* CS = cf_smem + q;   // 2 * mh * nr: C then S, [m][a]
+  for (int i = threadIdx.x; i < q; i += blockDim.x) F[i] = grid[off + i];
+  __syncthreads();
+  for (int i = threadIdx.x; i < mh * nr; i += blockDim.x) {
+    const int m = i / nr, a = i - m * nr;
+    R c = 0, s = 0;
+    for (int b = 0; b < nth; ++b) {
+      R sn, cs;
+      // angle m * 2 pi b / nth, reduced to (m*b mod nth) for accuracy
+      sincospi((R)(2 * ((m * b) % nth)) / (R)nth, &sn, &cs);
+      const R f = (R)F[a * nth + b];
+      c = fma(f, cs, c);
+      s = fma(f, sn, s);
+    }
+    const R w = (m == 0 ? (R)1 : (R)2) / (R)nth;
+    CS[m * nr + a] = (double)(w * c);
+    CS[mh * nr + m * nr + a] = (double)(w * s);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < mh * nr; i += blockDim.x) {
+    const int m = i / nr, j = i - m * nr;
+    const int d = 2 * j + (m & 1);
+    R A = 0, B = 0;
+    for (int a = 0; a < nr; ++a) {
+      const R T = cospi((R)(d * (2 * a + 1)) / (R)(4 * nr));
+      A = fma((R)CS[m * nr + a], T, A);
+      B = fma((R)CS[mh * nr + m * nr + a], T, B);
+    }
+    const R w = (d == 0 ? (R)1 : (R)2) / (R)nr;
+    coef[off + i] = (double)(w * A);
+    coef[off + mh * nr + i] = (double)(w * B);
+  }
+}
+
+// Direct sums at the Zernike nodes over a per-patch source list (overwrites z).
+constexpr int DT_THREADS = 256;
+constexpr int DT_NT = 2;
+constexpr int DT_JT = 8;
+
+template <typename R, int MODE>
+__global__ void __launch_bounds__(DT_THREADS) direct_list_kernel(
+    int pt, int Kstar, const int* __restrict__ rep_p, const int* __restrict__ rep_off,
+    const int64_t* __restrict__ pd_off, const int* __restrict__ pd, const int* __restrict__ pdk,
+    const double* __restrict__ centres, const double* __restrict__ zloc, const R* __restrict__ soff,
+    const R* __restrict__ rho, double* __restrict__ z) {
+  using V4 = typename V4T<R>::type;
+  extern __shared__ unsigned char dt_smem[];
+  V4* S = reinterpret_cast<V4*>(dt_smem);
+  __shared__ double D[DT_JT][3];
+  __shared__ int toff[DT_JT + 1], tcol[DT_JT];
+  const int64_t i = blockIdx.x;
+  const double cx = centres[3 * i], cy = centres[3 * i + 1], cz = centres[3 * i + 2];
+  double e1[3], e2[3];
+  patch_frame(cx, cy, cz, e1, e2);
+  R ax[DT_NT], ay[DT_NT], az[DT_NT];
+  double acc[DT_NT];
+  int kk[DT_NT];
+#pragma unroll
+  for (int t = 0; t < DT_NT; ++t) {
+    kk[t] = (blockIdx.y * DT_NT + t) * DT_THREADS + threadIdx.x;
+    double gq[3] = {0.0, 0.0, 0.0};
+    if (kk[t] < Kstar) frame_apply(e1, e2, cx, cy, cz, zloc[3 * kk[t]], zloc[3 * kk[t] + 1], zloc[3 * kk[t] + 2], gq);
+    ax[t] = (R)gq[0];
+    ay[t] = (R)gq[1];
+    az[t] = (R)gq[2];
+    acc[t] = 0.0;
+  }
+  const int64_t lo = pd_off[i], hi = pd_off[i + 1];
+  for (int64_t s0 = lo; s0 < hi; s0 += DT_JT) {
+    const int nj = (int)min((int64_t)DT_JT, hi - s0);
+    __syncthreads();
+    if (threadIdx.x < nj) {
+      const int64_t j = pd[s0 + threadIdx.x];
+      const int k = pdk[s0 + threadIdx.x];
+      for (int c = 0; c < 3; ++c) D[threadIdx.x][c] = centres[3 * j + c] - centres[3 * i + c];
+      toff[threadIdx.x + 1] = rep_p[k];
+      tcol[threadIdx.x] = rep_off[k];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      toff[0] = 0;
+      for (int jj = 0; jj < nj; ++jj) toff[jj + 1] += toff[jj];
+    }
+    __syncthreads();
+    const int ns = toff[nj];
+    for (int idx = threadIdx.x; idx < ns; idx += DT_THREADS) {
+      int jj = 0;
+      while (idx >= toff[jj + 1]) ++jj;
+      const int64_t gsrc = (int64_t)pd[s0 + jj] * pt + tcol[jj] + (idx - toff[jj]);
+      V4 v;
+      v.x = (R)D[jj][0] + soff[3 * gsrc];
+      v.y = (R)D[jj][1] + soff[3 * gsrc + 1];
+      v.z = (R)D[jj][2] + soff[3 * gsrc + 2];
+      v.w = rho[gsrc];
+      S[idx] = v;
+    }
+    __syncthreads();
+    R part[DT_NT];
+#pragma unroll
+    for (int t = 0; t < DT_NT; ++t) part[t] = 0;
+    for (int s = 0; s < ns; ++s) {
+      const V4 v = S[s];
+#pragma unroll
+      for (int t = 0; t < DT_NT; ++t) {
+        const R dx = ax[t] - v.x, dy = ay[t] - v.y, dz = az[t] - v.z;
+        const R d2 = fma(dx, dx, fma(dy, dy, dz * dz));
+        R gv;
+        if constexpr (sizeof(R) == 8)
+          gv = green64<MODE>(d2);
+        else
+          gv = green32<MODE>(d2);
+        part[t] = fma(gv, v.w, part[t]);
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < DT_NT; ++t) acc[t] += (double)part[t];
+  }
+#pragma unroll
+  for (int t = 0; t < DT_NT; ++t)
+    if (kk[t] < Kstar) z[i * Kstar + kk[t]] = acc[t];
+}
+
+// L2P: z_i(k) += interpolant of every grid group of patch i at node k.
+template <typename R>
+__global__ void __launch_bounds__(512) l2p_kernel(int Kstar, const int64_t* __restrict__ pg_off,
+                                                  const int* __restrict__ pg, const double* __restrict__ gcen,
+                                                  const double* __restrict__ gR, const int* __restrict__ gshape,
+                                                  const int64_t* __restrict__ goff, const int* __restrict__ shape_nr,
+                                                  const int* __restrict__ shape_nth, const double* __restrict__ coef,
+                                                  const double* __restrict__ centres, const double* __restrict__ zloc,
+                                                  double* __restrict__ z) {
+  extern __shared__ unsigned char lp_smem[];
+  R* C = reinterpret_cast<R*>(lp_smem);
+  const int64_t i = blockIdx.x;
+  const int k = threadIdx.x;
+  const double cx = centres[3 * i], cy = centres[3 * i + 1], cz = centres[3 * i + 2];
+  double e1[3], e2[3], zo[3] = {0.0, 0.0, 0.0};
+  patch_frame(cx, cy, cz, e1, e2);
+  if (k < Kstar) frame_apply(e1, e2, cx, cy, cz, zloc[3 * k], zloc[3 * k + 1], zloc[3 * k + 2], zo);
+  double acc = 0.0;
+  for (int64_t s = pg_off[i]; s < pg_off[i + 1]; ++s) {
+    const int g = pg[s];
+    const int sh = gshape[g];
+    const int nr = shape_nr[sh], nth = shape_nth[sh], q = nr * nth, mh = nth / 2;
+    const int64_t off = goff[g];
+    __syncthreads();
+    for (int t = threadIdx.x; t < q; t += blockDim.x) C[t] = (R)coef[off + t];
+    __syncthreads();
+    if (k >= Kstar) continue;
+    const double gx = gcen[3 * g], gy = gcen[3 * g + 1], gz = gcen[3 * g + 2];
+    double f1[3], f2[3];
+    patch_frame(gx, gy, gz, f1, f2);
+    // offset of the node from the group centre, in the group's frame
+    const R dx = (R)(cx - gx) + (R)zo[0], dy = (R)(cy - gy) + (R)zo[1], dz = (R)(cz - gz) + (R)zo[2];
+    const R u1 = dx * (R)f1[0] + dy * (R)f1[1] + dz * (R)f1[2];
+    const R u2 = dx * (R)f2[0] + dy * (R)f2[1] + dz * (R)f2[2];
+    const R u3 = dx * (R)gx + dy * (R)gy + dz * (R)gz;
+    const R sr = sqrt(u1 * u1 + u2 * u2);
+    const R r = atan2(sr, (R)1 + u3);
+    const R rho = r / (R)gR[g];
+    R ct, st;
+    if (sr > (R)0) {
+      ct = u1 / sr;
+      st = u2 / sr;
+    } else {
+      ct = (R)1;
+      st = (R)0;
+    }
+    // Clenshaw in y = T_2(rho) over the even (T_2j) and odd (T_2j+1) series
+    const R y = fma((R)2 * rho, rho, (R)-1);
+    const R y2 = y + y;
+    R cm = 1, sm = 0;  // cos(m th), sin(m th)
+    R val = 0;
+    for (int m = 0; m < mh; ++m) {
+      const R* A = C + m * nr;
+      const R* B = C + mh * nr + m * nr;
+      R ba1 = 0, ba2 = 0, bb1 = 0, bb2 = 0;
+      for (int j = nr - 1; j >= 0; --j) {
+        const R ta = fma(y2, ba1, A[j] - ba2);
+        const R tb = fma(y2, bb1, B[j] - bb2);
+        ba2 = ba1;
+        ba1 = ta;
+        bb2 = bb1;
+        bb1 = tb;
+      }
+      // sum c_j phi_j = phi_0 (b_0 - 2y b_1) + phi_1 b_1, (phi_0, phi_1) = (1, y) or (rho, rho(2y - 1))
+      R sa, sb;
+      if ((m & 1) == 0) {
+        sa = fma(-y, ba2, ba1);  // phi_0 = 1, phi_1 = y: sum = b0 - y b1
+        sb = fma(-y, bb2, bb1);
+      } else {
+        // phi_0 = rho, phi_1 = T_3(rho) = rho (2y - 1): sum = rho (b0 - b1)
+        sa = rho * (ba1 - ba2);
+        sb = rho * (bb1 - bb2);
+      }
+      val = fma(cm, sa, fma(sm, sb, val));
+      const R cn = cm * ct - sm * st;
+      sm = sm * ct + cm * st;
+      cm = cn;
+    }
+    acc += (double)val;
+  }
+  if (k < Kstar) z[i * Kstar + k] += acc;
+}
+
+}  // namespace
+
+void tree_upload(const TreeHost& t, const Precomputed& pc, TreeDevice& d) {
+  tree_free(d);
+  (void)pc;
+  d.ngroups = (int)t.gR.size();
+  d.nitems = (int)t.witem_group.size();
+  d.nshapes = (int)t.shapes.size();
+  d.ngrid = t.total_grid_points;
+  d.N = (int64_t)t.pd_off.size() - 1;
+  std::vector<int> snr(d.nshapes), snth(d.nshapes);
+  d.max_q = d.max_nr = d.max_nth = 0;
+  for (int s = 0; s < d.nshapes; ++s) {
+    snr[s] = t.shapes[s].nr;
+    snth[s] = t.shapes[s].nth;
+    d.max_q = std::max(d.max_q, t.shapes[s].q());
+    d.max_nr = std::max(d.max_nr, snr[s]);
+    d.max_nth = std::max(d.max_nth, snth[s]);
+  }
+  // grid-point offsets from the group centre in the global frame (FP64 and FP32)
+  std::vector<double> gp64(3 * (size_t)d.ngrid);
+  for (int g = 0; g < d.ngroups; ++g) {
+    const GridShape& s = t.shapes[t.gshape[g]];
+    const double* c = &t.gcen[3 * g];
+    double e1[3], e2[3];
+    const double ax = -c[1], ay = c[0], na2 = ax * ax + ay * ay;
+    if (na2 >= 1e-24) {
+      const double inv = 1.0 / std::sqrt(na2);
+      e1[0] = ax * inv;
+      e1[1] = ay * inv;
+      e1[2] = 0.0;
+    } else {
+      e1[0] = 1.0;
+      e1[1] = 0.0;
+      e1[2] = 0.0;
+    }
+    e2[0] = c[1] * e1[2] - c[2] * e1[1];
+    e2[1] = c[2] * e1[0] - c[0] * e1[2];
+    e2[2] = c[0] * e1[1] - c[1] * e1[0];
+    for (int a = 0; a < s.nr; ++a) {
+      const double r = t.gR[g] * std::cos((2.0 * a + 1.0) * kPi / (4.0 * s.nr));
+      for (int b = 0; b < s.nth; ++b) {
+        const double th = 2.0 * kPi * b / s.nth;
+        double o[3];
+        local_offset(r, th, o);
+        const size_t idx = (size_t)t.goff[g] + (size_t)a * s.nth + b;
+        for (int k = 0; k < 3; ++k) gp64[3 * idx + k] = o[0] * e1[k] + o[1] * e2[k] + o[2] * c[k];
+      }
+    }
+  }
+  std::vector<float> gp32(gp64.begin(), gp64.end());
+  auto chk = [](cudaError_t e) {
+    if (e != cudaSuccess) throw std::runtime_error(std::string("tree upload: ") + cudaGetErrorString(e));
+  };
+  chk(up(&d.gcen, t.gcen));
+  chk(up(&d.gR, t.gR));
+  chk(up(&d.gshape, t.gshape));
+  chk(up(&d.goff, t.goff));
+  chk(up(&d.shape_nr, snr));
+  chk(up(&d.shape_nth, snth));
+  chk(up(&d.witem_group, t.witem_group));
+  chk(up(&d.witem_rep, t.witem_rep));
+  chk(up(&d.witem_lo, t.witem_lo));
+  chk(up(&d.witem_hi, t.witem_hi));
+  chk(up(&d.isrc, t.isrc));
+  chk(up(&d.pg_off, t.pg_off));
+  chk(up(&d.pg, t.pg));
+  chk(up(&d.pd_off, t.pd_off));
+  chk(up(&d.pd, t.pd));
+  chk(up(&d.pdk, t.pdk));
+  chk(up(&d.gpos64, gp64));
+  chk(up(&d.gpos32, gp32));
+  chk(cudaMalloc(&d.grid, std::max<int64_t>(1, d.ngrid) * sizeof(double)));
+  chk(cudaMalloc(&d.coef, std::max<int64_t>(1, d.ngrid) * sizeof(double)));
+}
+
+void tree_free(TreeDevice& d) {
+  fr(d.gcen);
+  fr(d.gR);
+  fr(d.gshape);
+  fr(d.goff);
+  fr(d.shape_nr);
+  fr(d.shape_nth);
+  fr(d.witem_group);
+  fr(d.witem_rep);
+  fr(d.witem_lo);
+  fr(d.witem_hi);
+  fr(d.isrc);
+  fr(d.pg_off);
+  fr(d.pg);
+  fr(d.pd_off);
+  fr(d.pd);
+  fr(d.pdk);
+  fr(d.gpos64);
+  fr(d.gpos32);
+  fr(d.grid);
+  fr(d.coef);
+  d.ngroups = d.nitems = 0;
+  d.ngrid = 0;
+}
+
+template <typename K>
+static cudaError_t allow_smem(K kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename R, int MODE>
+static cudaError_t tree_field_impl(const DeviceData& dd, const TreeDevice& t, cudaStream_t s, cudaEvent_t* ev) {
+  const R* soff = (sizeof(R) == 8) ? (const R*)dd.soff64 : (const R*)dd.soff32;
+  const R* rho = (sizeof(R) == 8) ? (const R*)dd.rho64 : (const R*)dd.rho32;
+  const R* gpos = (sizeof(R) == 8) ? (const R*)t.gpos64 : (const R*)t.gpos32;
+  using V4 = typename V4T<R>::type;
+  cudaError_t e;
+  if (ev) cudaEventRecord(ev[0], s);
+  if (t.nitems > 0) {
+    e = cudaMemsetAsync(t.grid, 0, t.ngrid * sizeof(double), s);
+    if (e != cudaSuccess) return e;
+    const size_t smem = (size_t)P2L_JT * dd.pmax * sizeof(V4);
+    if ((e = allow_smem(p2l_kernel<R, MODE>, smem)) != cudaSuccess) return e;
+    p2l_kernel<R, MODE><<<t.nitems, P2L_THREADS, smem, s>>>(t.witem_group, t.witem_rep, dd.rep_p, dd.rep_off, dd.p,
+                                                             t.witem_lo, t.witem_hi, t.isrc, t.gcen, t.gshape, t.goff,
+                                                             t.shape_nr, t.shape_nth, gpos, dd.centres, soff, rho,
+                                                             t.grid);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[1], s);
+    const size_t csm = (size_t)t.max_q * sizeof(double) + (size_t)t.max_nth * t.max_nr * sizeof(double);
+    if ((e = allow_smem(coef_kernel<R>, csm)) != cudaSuccess) return e;
+    coef_kernel<R><<<t.ngroups, 256, csm, s>>>(t.gshape, t.goff, t.shape_nr, t.shape_nth, t.grid, t.coef);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  } else if (ev) {
+    cudaEventRecord(ev[1], s);
+  }
+  if (ev) cudaEventRecord(ev[2], s);
+  {
+    const size_t smem = (size_t)DT_JT * dd.pmax * sizeof(V4);
+    if ((e = allow_smem(direct_list_kernel<R, MODE>, smem)) != cudaSuccess) return e;
+    dim3 grid((unsigned)dd.N, (unsigned)((dd.Kstar + DT_THREADS * DT_NT - 1) / (DT_THREADS * DT_NT)));
+    direct_list_kernel<R, MODE><<<grid, DT_THREADS, smem, s>>>(dd.p, dd.Kstar, dd.rep_p, dd.rep_off, t.pd_off, t.pd,
+                                                                t.pdk, dd.centres, dd.zloc, soff, rho, dd.z);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (ev) cudaEventRecord(ev[3], s);
+  if (t.nitems > 0) {
+    if (dd.Kstar > 512) return cudaErrorInvalidConfiguration;
+    const size_t smem = (size_t)t.max_q * sizeof(R);
+    if ((e = allow_smem(l2p_kernel<R>, smem)) != cudaSuccess) return e;
+    l2p_kernel<R><<<(unsigned)dd.N, 512, smem, s>>>(dd.Kstar, t.pg_off, t.pg, t.gcen, t.gR, t.gshape, t.goff,
+                                                    t.shape_nr, t.shape_nth, t.coef, dd.centres, dd.zloc, dd.z);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (ev) cudaEventRecord(ev[4], s);
+  return cudaSuccess;
+}
+
+cudaError_t launch_tree_field(const DeviceData& d, const TreeDevice& t, int mode, int prec, cudaStream_t s,
+                              cudaEvent_t* ev) {
+  if (prec == NCS_FP64)
+    return mode == 0 ? tree_field_impl<double, 0>(d, t, s, ev) : tree_field_impl<double, 1>(d, t, s, ev);
+  return mode == 0 ? tree_field_impl<float, 0>(d, t, s, ev) : tree_field_impl<float, 1>(d, t, s, ev);
+}
+
+}  // namespace ncs

@@ -27,7 +27,8 @@ METHOD_AUTO, METHOD_DIRECT, METHOD_TREE = 0, 1, 2
 
 EXPORTS = ["ncs_default_params", "ncs_create", "ncs_create_from_operator", "ncs_info", "ncs_timings",
            "ncs_get_operator", "ncs_get_onepatch", "ncs_set_patches", "ncs_set_method", "ncs_matvec",
-           "ncs_matvec_dev", "ncs_field_dev", "ncs_solve", "ncs_eval", "ncs_last_error", "ncs_destroy"]
+           "ncs_matvec_dev", "ncs_field_dev", "ncs_solve", "ncs_eval", "ncs_last_error", "ncs_destroy",
+           "ncs_tree_pairs", "ncs_tree_stats", "ncs_profile_matvec", "ncs_create_from_operators", "ncs_get_reps"]
 
 
 class ncs_params(ctypes.Structure):
@@ -62,6 +63,10 @@ def load(path: str = LIB_PATH):
                                ctypes.POINTER(VP)]
     lib.ncs_create_from_operator.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, D, D, D, D,
                                              ctypes.POINTER(ncs_params), ctypes.POINTER(VP)]
+    lib.ncs_create_from_operators.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, D,
+                                              ctypes.POINTER(ctypes.c_int), D, D, D, D, ctypes.POINTER(ncs_params),
+                                              ctypes.POINTER(VP)]
+    lib.ncs_get_reps.argtypes = [VP, ctypes.POINTER(ctypes.c_int), D, ctypes.POINTER(ctypes.c_int)]
     lib.ncs_info.argtypes = [VP, ctypes.POINTER(ctypes.c_int64), ctypes.c_int]
     lib.ncs_timings.argtypes = [VP, D, ctypes.c_int]
     lib.ncs_get_operator.argtypes = [VP, D, D, D, D, D, D, D]
@@ -75,6 +80,10 @@ def load(path: str = LIB_PATH):
     lib.ncs_eval.argtypes = [VP, ctypes.c_int64, D, D, D]
     lib.ncs_last_error.argtypes = [VP]
     lib.ncs_last_error.restype = ctypes.c_char_p
+    I32 = ctypes.POINTER(ctypes.c_int)
+    lib.ncs_tree_pairs.argtypes = [VP, ctypes.POINTER(ctypes.c_int64), I32, I32, I32, I32]
+    lib.ncs_tree_stats.argtypes = [VP, ctypes.POINTER(ctypes.c_int64), ctypes.c_int]
+    lib.ncs_profile_matvec.argtypes = [VP, VP, VP, ctypes.c_int, VP, D, ctypes.c_int]
     lib.ncs_destroy.argtypes = [VP]
     lib.ncs_destroy.restype = None
     for name in EXPORTS:
@@ -112,6 +121,17 @@ class Context:
         h = VP()
         if operator is None:
             rc = lib.ncs_create(eps, mode, K, ctypes.byref(prm), ctypes.byref(h))
+        elif isinstance(operator, dict):
+            # several representations: dict(rho_min=[...], reps=[(T, st, sth), ...], I=I)
+            rm = _f64(operator["rho_min"])
+            ps = np.ascontiguousarray([r[0].shape[0] for r in operator["reps"]], dtype=np.int32)
+            T = _f64(np.concatenate([r[0] for r in operator["reps"]], axis=0))
+            st = _f64(np.concatenate([r[1] for r in operator["reps"]]))
+            sth = _f64(np.concatenate([r[2] for r in operator["reps"]]))
+            I = _f64(operator["I"])
+            rc = lib.ncs_create_from_operators(eps, mode, K, len(ps), _ptr(rm),
+                                               ps.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _ptr(T), _ptr(st),
+                                               _ptr(sth), _ptr(I), ctypes.byref(prm), ctypes.byref(h))
         else:
             T, st, sth, I = (_f64(a) for a in operator)
             p = T.shape[0]
@@ -161,6 +181,16 @@ class Context:
                                             _ptr(zth)))
         return dict(T=T, skel_t=st, skel_theta=sth, I=I, P=P, znode_r=zr, znode_theta=zth)
 
+    def reps(self):
+        """(far-field radii, ranks) of the outgoing representations."""
+        lib = load()
+        n = ctypes.c_int(0)
+        self._check(lib.ncs_get_reps(self.h, ctypes.byref(n), None, None))
+        rm = np.zeros(n.value)
+        ps = np.zeros(n.value, dtype=np.int32)
+        self._check(lib.ncs_get_reps(self.h, ctypes.byref(n), _ptr(rm), ps.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
+        return rm, ps
+
     def onepatch(self):
         i = self.info()
         tr = np.zeros(i["nrad"])
@@ -172,6 +202,23 @@ class Context:
         c = _f64(centres).reshape(-1, 3)
         self._check(load().ncs_set_patches(self.h, c.shape[0], _ptr(c)))
         self.N = c.shape[0]
+
+    def tree_pairs(self):
+        """(target, source, level, kind) arrays of every pair the tree accounts for."""
+        lib = load()
+        n = ctypes.c_int64(0)
+        self._check(lib.ncs_tree_pairs(self.h, ctypes.byref(n), None, None, None, None))
+        arrs = [np.zeros(n.value, dtype=np.int32) for _ in range(4)]
+        ptrs = [a.ctypes.data_as(ctypes.POINTER(ctypes.c_int)) for a in arrs]
+        self._check(lib.ncs_tree_pairs(self.h, ctypes.byref(n), *ptrs))
+        return tuple(arrs)
+
+    def tree_stats(self) -> dict:
+        out = (ctypes.c_int64 * 9)()
+        self._check(load().ncs_tree_stats(self.h, out, 9))
+        keys = ["levels", "grid_groups", "grid_points", "p2l_items", "p2l_pairs", "direct_pairs", "l2p_evals",
+                "direct_patch_pairs", "shapes"]
+        return dict(zip(keys, [int(v) for v in out]))
 
     def set_method(self, method):
         self._check(load().ncs_set_method(self.h, method))
@@ -185,6 +232,12 @@ class Context:
     def matvec_dev(self, x_ptr, y_ptr, precision=FP64, stream=0):
         """x_ptr, y_ptr: device addresses (e.g. torch tensor.data_ptr())."""
         self._check(load().ncs_matvec_dev(self.h, VP(x_ptr), VP(y_ptr), precision, VP(stream)))
+
+    def profile_matvec(self, x_ptr, y_ptr, precision=FP64, stream=0):
+        """Per-stage milliseconds of one product (see ncs_profile_matvec)."""
+        ms = np.zeros(7)
+        self._check(load().ncs_profile_matvec(self.h, VP(x_ptr), VP(y_ptr), precision, VP(stream), _ptr(ms), 7))
+        return dict(zip(["outgoing", "p2l", "coef", "direct", "l2p", "apply_P", "total"], ms.tolist()))
 
     def field_dev(self, x_ptr, z_ptr, precision=FP64, stream=0):
         self._check(load().ncs_field_dev(self.h, VP(x_ptr), VP(z_ptr), precision, VP(stream)))
