@@ -53,7 +53,11 @@ extern "C" {
 
 #define NCS_FP64 0  /* all pair sums and transforms in FP64 */
 #define NCS_FP32 1  /* FP32 pair sums / transforms in patch- or group-local frames */
-#define NCS_MIXED 2 /* solve only: FP32 inner GMRES + FP64 iterative refinement */
+#define NCS_MIXED 2 /* solve only: FP32 inner GMRES + FP64-accurate iterative refinement */
+#define NCS_DF64 3  /* pair sums and interpolation in float-float (two FP32 words, ~48-bit
+                       significand, ~1e-14 relative) on the FP32 pipes; GEMMs, grid
+                       transforms and offsets in FP64: FP64-accurate products at a
+                       fraction of the FP64-pipe cost */
 
 #define NCS_METHOD_AUTO 0   /* tree when N >= tree_min_patches, else direct */
 #define NCS_METHOD_DIRECT 1 /* compressed sums over all other patches, O(N^2) (Section 7.1) */
@@ -72,6 +76,11 @@ typedef struct ncs_params {
   int tree_min_patches;/* AUTO switches to the tree at this N, default 2000 */
   int gmres_maxit;     /* GMRES iteration cap, default 200 */
   int verbose;         /* 0 silent .. 3 chatty (stderr) */
+  int mixed_residual;  /* precision of the refinement residual of NCS_MIXED:
+                          NCS_DF64 (default) or NCS_FP64 */
+  int tensor_cores;    /* 1: the FP32 product runs its dense contractions
+                          (rho = T x, y = x + P z) on the tcgen05 tensor cores (3xTF32);
+                          0 (default): FP32 SIMT kernels */
 } ncs_params;
 
 /* Fills *p with the defaults listed above. */
@@ -176,7 +185,7 @@ int ncs_set_method(ncs_ctx* ctx, int method);
 /*
  * y = A x for the system of eq. (opinteqnsdisc): y_i = x_i + P sum_{j != i} S_ij B x_j,
  * evaluated by the compressed representation (Section 7, Step 3). x, y: host,
- * N*K doubles. precision: NCS_FP64 or NCS_FP32 (FP32 kernels, FP64 in/out).
+ * N*K doubles. precision: NCS_FP64, NCS_DF64 or NCS_FP32 (FP32 kernels, FP64 in/out).
  */
 int ncs_matvec(ncs_ctx* ctx, const double* x, double* y, int precision);
 
@@ -202,8 +211,9 @@ int ncs_field_dev(ncs_ctx* ctx, const double* x, double* z, int precision, void*
 
 /*
  * Solves the system by GMRES (Section 7, Step 3; x0 = 0, relative residual tol).
- * precision: NCS_FP64 (all FP64), NCS_FP32 (FP32 products, FP64 Arnoldi) or
- * NCS_MIXED (FP32 inner GMRES wrapped in FP64 iterative refinement).
+ * precision: NCS_FP64 (all FP64), NCS_DF64 (float-float products, FP64 Arnoldi),
+ * NCS_FP32 (FP32 products, FP64 Arnoldi) or NCS_MIXED (FP32 inner GMRES wrapped in
+ * iterative refinement whose residuals use NCS_DF64 products).
  * Outputs (each may be NULL): fhat (N*K host doubles, the densities in the b_n
  * basis, Remark sigrep), scalar = mean first passage time mu = 1/(3 I_sigma) - 3/5
  * (interior, eq. mufromsigma2) or capacitance C = 4 pi I_sigma (exterior, |J|
@@ -224,6 +234,32 @@ int ncs_solve(ncs_ctx* ctx, double tol, int precision, double* fhat, double* sca
  * D = -I_sigma (eq. vtilde). Errors: NCS_E_INPUT for targets too close.
  */
 int ncs_eval(ncs_ctx* ctx, int64_t M, const double* targets, const double* fhat, double* out);
+
+/*
+ * The library's tensor-core GEMM on its own: D = A B^T with A (rows x kdim), B
+ * (cols x kdim) and D (rows x cols), all row-major FP32 device arrays, computed with
+ * tcgen05 kind::tf32 MMAs on hi/lo TF32 splits (3 products, ~FP32 accuracy) - the
+ * kernel behind the per-patch operator contractions (eq. Tmap, Step 3.5). Synchronous
+ * on `stream`. Errors: NCS_E_INPUT, NCS_E_CUDA, NCS_E_TIMEOUT (bounded wait gave up).
+ */
+int ncs_tc_gemm_f32(int64_t rows, int cols, int kdim, const float* A, const float* B, float* D, void* stream);
+
+/*
+ * Solves B independent spheres (each its own eps, mode, patch layout; common K) to
+ * relative residual tol at `precision`, as ncs_solve does for one (Section 7, Step 3):
+ * `workers` host threads (0 = all cores) each take instances from a shared queue,
+ * run the precompute and tree set-up for it on one host core, solve it on the GPU on
+ * its own stream, and release it, so set-up, transfers and GPU work of different
+ * instances overlap and at most `workers` instances hold device memory at once.
+ * centres[b] points to N[b] x 3 host doubles. Per-instance outputs (each may be NULL):
+ * scalar (mu or C), I_sigma, iterations, relres, status (NCS_OK or the instance's error
+ * code). seconds (may be NULL): [set-up summed over instances, solve summed over
+ * instances, wall clock of the batch]. Returns NCS_OK if every instance converged,
+ * else the first failing instance's code.
+ */
+int ncs_batch_solve(int B, const double* eps, const int* mode, const int64_t* N, const double* const* centres,
+                    int K, double tol, int precision, const ncs_params* params, int workers, double* scalar,
+                    double* Isigma, int* iterations, double* relres, int* status, double* seconds);
 
 /* Message of the last failure on ctx (static string if ctx is NULL). */
 const char* ncs_last_error(const ncs_ctx* ctx);

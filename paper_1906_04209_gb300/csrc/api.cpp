@@ -11,6 +11,9 @@
 #include <exception>
 #include <new>
 #include <string>
+#include <atomic>
+#include <chrono>
+#include <thread>
 #include <unordered_map>
 #include <vector>
 
@@ -97,6 +100,10 @@ void free_all(ncs_ctx* c) {
   dev_free(d.rep_p);
   dev_free(d.rep_off);
   dev_free(d.rep_rho);
+  dev_free(d.logtab);
+  dev_free(d.T32);
+  dev_free(d.P32);
+  dev_free(d.tc_err);
   if (c->stream) cudaStreamDestroy(c->stream);
   c->stream = nullptr;
 }
@@ -132,6 +139,15 @@ void upload_operator(ncs_ctx* c) {
   for (int j = 0; j < pc.K; ++j)
     for (int q = 0; q < pc.Kstar; ++q) PT[(size_t)q * pc.K + j] = pc.P[(size_t)j * pc.Kstar + q];
   std::vector<float> TT32(TT.begin(), TT.end()), PT32(PT.begin(), PT.end());
+  std::vector<float> T32((size_t)pt * pc.K);
+  for (int r = 0; r < nrep; ++r)
+    for (int m = 0; m < rp[r]; ++m)
+      for (int k = 0; k < pc.K; ++k) T32[(size_t)(ro[r] + m) * pc.K + k] = (float)pc.reps[r].T[(size_t)m * pc.K + k];
+  std::vector<float> P32(pc.P.begin(), pc.P.end());
+  d.T32 = dev_upload(T32);
+  d.P32 = dev_upload(P32);
+  d.tc_err = dev_alloc<int>(1);
+  CU(cudaMemset(d.tc_err, 0, sizeof(int)));
   d.TT64 = dev_upload(TT);
   d.TT32 = dev_upload(TT32);
   d.PT64 = dev_upload(PT);
@@ -139,6 +155,20 @@ void upload_operator(ncs_ctx* c) {
   d.zloc = dev_upload(pc.zloc);
   d.sloc = dev_upload(sl);
   d.I = dev_upload(pc.I);
+  {
+    // float-float log table: c_i = 1 + (i + 1/2)/64
+    std::vector<float> lt(4 * 64);
+    for (int i = 0; i < 64; ++i) {
+      const double ci = 1.0 + (i + 0.5) / 64.0;
+      const double L = std::log(ci), inv = 1.0 / ci;
+      lt[4 * i + 0] = (float)L;
+      lt[4 * i + 1] = (float)(L - (double)(float)L);
+      lt[4 * i + 2] = (float)inv;
+      lt[4 * i + 3] = (float)(inv - (double)(float)inv);
+    }
+    float* dl = dev_upload(lt);
+    d.logtab = reinterpret_cast<float4*>(dl);
+  }
   d.rep_p = dev_upload(rp);
   d.rep_off = dev_upload(ro);
   d.rep_rho = dev_upload(rr);
@@ -210,9 +240,35 @@ void ensure_tree(ncs_ctx* c) {
   }
 }
 
+void outgoing(ncs_ctx* c, const double* x, int prec, cudaStream_t s) {
+  if (prec == NCS_FP32 && c->prm.tensor_cores)
+    CU(ncs::launch_tc_outgoing(c->d, x, c->d.T32, c->d.tc_err, s));
+  else
+    CU(ncs::launch_outgoing(c->d, x, prec, s));
+}
+
+void apply_P(ncs_ctx* c, const double* x, double* y, int prec, cudaStream_t s) {
+  if (prec == NCS_FP32 && c->prm.tensor_cores)
+    CU(ncs::launch_tc_apply_P(c->d, x, y, c->d.P32, c->d.tc_err, s));
+  else
+    CU(ncs::launch_apply_P(c->d, x, y, s));
+}
+
+// A tensor-core kernel whose bounded wait gave up leaves the flag set (checked at
+// synchronisation points).
+void check_tc(ncs_ctx* c) {
+  if (!c->prm.tensor_cores || !c->d.tc_err) return;
+  int f = 0;
+  CU(cudaMemcpy(&f, c->d.tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (f) {
+    CU(cudaMemset(c->d.tc_err, 0, sizeof(int)));
+    throw Fail{NCS_E_TIMEOUT, "tensor-core GEMM: bounded wait on its mbarrier gave up"};
+  }
+}
+
 // z = field of x at the Zernike nodes (before P), on stream s.
 void field(ncs_ctx* c, const double* x, int prec, cudaStream_t s) {
-  CU(ncs::launch_outgoing(c->d, x, prec, s));
+  outgoing(c, x, prec, s);
   if (use_tree(c)) {
     ensure_tree(c);
     CU(ncs::launch_tree_field(c->d, c->tdev, c->pc.mode, prec, s));
@@ -223,7 +279,7 @@ void field(ncs_ctx* c, const double* x, int prec, cudaStream_t s) {
 
 void matvec(ncs_ctx* c, const double* x, double* y, int prec, cudaStream_t s) {
   field(c, x, prec, s);
-  CU(ncs::launch_apply_P(c->d, x, y, s));
+  apply_P(c, x, y, prec, s);
 }
 
 double dev_dot(ncs_ctx* c, const double* a, const double* b, cudaStream_t s) {
@@ -374,6 +430,8 @@ void validate_params(const ncs_params& p) {
   if (!(p.grid_tol > 0.0 && p.grid_tol < 1e-1)) throw Fail{NCS_E_INPUT, "grid_tol out of range"};
   if (p.gmres_maxit < 1 || p.gmres_maxit > 2000) throw Fail{NCS_E_INPUT, "gmres_maxit out of range"};
   if (p.method < 0 || p.method > 2) throw Fail{NCS_E_INPUT, "bad method"};
+  if (p.mixed_residual != NCS_FP64 && p.mixed_residual != NCS_DF64)
+    throw Fail{NCS_E_INPUT, "mixed_residual must be NCS_FP64 or NCS_DF64"};
 }
 
 }  // namespace
@@ -392,6 +450,8 @@ void ncs_default_params(ncs_params* p) {
   p->tree_min_patches = 2000;
   p->gmres_maxit = 200;
   p->verbose = 0;
+  p->mixed_residual = NCS_DF64;
+  p->tensor_cores = 0;
 }
 
 int ncs_create(double eps, int mode, int K, const ncs_params* params, ncs_ctx** out) {
@@ -645,7 +705,8 @@ int ncs_matvec_dev(ncs_ctx* c, const double* x, double* y, int precision, void* 
   try {
     if (!c) throw Fail{NCS_E_INPUT, "null context"};
     if (!x || !y) throw Fail{NCS_E_INPUT, "NULL vector"};
-    if (precision != NCS_FP64 && precision != NCS_FP32) throw Fail{NCS_E_INPUT, "precision must be FP64 or FP32"};
+    if (precision != NCS_FP64 && precision != NCS_FP32 && precision != NCS_DF64)
+      throw Fail{NCS_E_INPUT, "precision must be FP64, DF64 or FP32"};
     check_ready(c);
     matvec(c, x, y, precision, (cudaStream_t)stream);
     return NCS_OK;
@@ -660,7 +721,8 @@ int ncs_field_dev(ncs_ctx* c, const double* x, double* z, int precision, void* s
   try {
     if (!c) throw Fail{NCS_E_INPUT, "null context"};
     if (!x || !z) throw Fail{NCS_E_INPUT, "NULL vector"};
-    if (precision != NCS_FP64 && precision != NCS_FP32) throw Fail{NCS_E_INPUT, "precision must be FP64 or FP32"};
+    if (precision != NCS_FP64 && precision != NCS_FP32 && precision != NCS_DF64)
+      throw Fail{NCS_E_INPUT, "precision must be FP64, DF64 or FP32"};
     check_ready(c);
     cudaStream_t s = (cudaStream_t)stream;
     field(c, x, precision, s);
@@ -679,12 +741,13 @@ int ncs_profile_matvec(ncs_ctx* c, const double* x, double* y, int precision, vo
   try {
     if (!c) throw Fail{NCS_E_INPUT, "null context"};
     if (!x || !y || !ms) throw Fail{NCS_E_INPUT, "NULL argument"};
-    if (precision != NCS_FP64 && precision != NCS_FP32) throw Fail{NCS_E_INPUT, "precision must be FP64 or FP32"};
+    if (precision != NCS_FP64 && precision != NCS_FP32 && precision != NCS_DF64)
+      throw Fail{NCS_E_INPUT, "precision must be FP64, DF64 or FP32"};
     check_ready(c);
     cudaStream_t s = (cudaStream_t)stream;
     for (auto& e : ev) CU(cudaEventCreate(&e));
     CU(cudaEventRecord(ev[0], s));
-    CU(ncs::launch_outgoing(c->d, x, precision, s));
+    outgoing(c, x, precision, s);
     if (use_tree(c)) {
       ensure_tree(c);
       CU(ncs::launch_tree_field(c->d, c->tdev, c->pc.mode, precision, s, ev + 1));
@@ -696,9 +759,10 @@ int ncs_profile_matvec(ncs_ctx* c, const double* x, double* y, int precision, vo
       CU(cudaEventRecord(ev[4], s));
       CU(cudaEventRecord(ev[5], s));
     }
-    CU(ncs::launch_apply_P(c->d, x, y, s));
+    apply_P(c, x, y, precision, s);
     CU(cudaEventRecord(ev[6], s));
     CU(cudaEventSynchronize(ev[6]));
+    check_tc(c);
     // stages: outgoing, P2L, coefficients, direct, L2P, apply P, total
     float t[7];
     for (int k = 0; k < 6; ++k) CU(cudaEventElapsedTime(&t[k], ev[k], ev[k + 1]));
@@ -716,7 +780,8 @@ int ncs_matvec(ncs_ctx* c, const double* x, double* y, int precision) {
   try {
     if (!c) throw Fail{NCS_E_INPUT, "null context"};
     if (!x || !y) throw Fail{NCS_E_INPUT, "NULL vector"};
-    if (precision != NCS_FP64 && precision != NCS_FP32) throw Fail{NCS_E_INPUT, "precision must be FP64 or FP32"};
+    if (precision != NCS_FP64 && precision != NCS_FP32 && precision != NCS_DF64)
+      throw Fail{NCS_E_INPUT, "precision must be FP64, DF64 or FP32"};
     check_ready(c);
     ensure_krylov(c, 1);
     const int64_t n = c->d.N * c->d.K;
@@ -724,6 +789,7 @@ int ncs_matvec(ncs_ctx* c, const double* x, double* y, int precision) {
     matvec(c, c->work, c->work + n, precision, c->stream);
     CU(cudaMemcpyAsync(y, c->work + n, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CU(cudaStreamSynchronize(c->stream));
+    check_tc(c);
     return NCS_OK;
   } catch (const Fail& f) {
     return finish(c, f);
@@ -737,7 +803,7 @@ int ncs_solve(ncs_ctx* c, double tol, int precision, double* fhat, double* scala
   try {
     if (!c) throw Fail{NCS_E_INPUT, "null context"};
     if (!(tol > 0.0 && tol < 1.0)) throw Fail{NCS_E_INPUT, "tol must be in (0, 1)"};
-    if (precision != NCS_FP64 && precision != NCS_FP32 && precision != NCS_MIXED)
+    if (precision != NCS_FP64 && precision != NCS_FP32 && precision != NCS_MIXED && precision != NCS_DF64)
       throw Fail{NCS_E_INPUT, "bad precision"};
     check_ready(c);
     const int maxit = c->prm.gmres_maxit;
@@ -781,7 +847,7 @@ int ncs_solve(ncs_ctx* c, double tol, int precision, double* fhat, double* scala
         double inner_est = 1.0;
         total += gmres(c, r, corr, std::min(inner_tol, 0.5), NCS_FP32, maxit, &inner_est, s);
         CU(ncs::launch_axpby(n, 1.0, corr, 1.0, x, s));
-        matvec(c, x, r, NCS_FP64, s);
+        matvec(c, x, r, c->prm.mixed_residual, s);
         CU(ncs::launch_axpby(n, 1.0, b, -1.0, r, s));
         ++total;
         const double newrel = std::sqrt(dev_dot(c, r, r, s)) / bnorm;
@@ -799,6 +865,7 @@ int ncs_solve(ncs_ctx* c, double tol, int precision, double* fhat, double* scala
     CU(cudaMemcpyAsync(&Is, c->hdev, sizeof(double), cudaMemcpyDeviceToHost, s));
     if (fhat) CU(cudaMemcpyAsync(fhat, x, n * sizeof(double), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
+    check_tc(c);
     if (Isigma) *Isigma = Is;
     if (scalar) *scalar = (c->pc.mode == NCS_INTERIOR) ? 1.0 / (3.0 * Is) - 0.6 : 4.0 * M_PI * Is;
     if (iterations) *iterations = total;
@@ -868,6 +935,92 @@ int ncs_eval(ncs_ctx* c, int64_t M, const double* targets, const double* fhat, d
   } catch (const std::exception& e) {
     return finish(c, Fail{NCS_E_INPUT, e.what()});
   }
+}
+
+int ncs_tc_gemm_f32(int64_t rows, int cols, int kdim, const float* A, const float* B, float* D, void* stream) {
+  if (rows < 0 || cols < 0 || kdim < 1 || !A || !B || !D) return NCS_E_INPUT;
+  if (rows == 0 || cols == 0) return NCS_OK;
+  int* err = nullptr;
+  if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) return NCS_E_OOM;
+  int rc = NCS_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess ||
+      ncs::launch_tc_gemm_f32(rows, cols, kdim, A, B, D, err, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    rc = NCS_E_CUDA;
+  } else {
+    int f = 0;
+    if (cudaMemcpy(&f, err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) rc = NCS_E_CUDA;
+    else if (f) rc = NCS_E_TIMEOUT;
+  }
+  cudaFree(err);
+  return rc;
+}
+
+int ncs_batch_solve(int B, const double* eps, const int* mode, const int64_t* N, const double* const* centres,
+                    int K, double tol, int precision, const ncs_params* params, int workers, double* scalar,
+                    double* Isigma, int* iterations, double* relres, int* status, double* seconds) {
+  if (B < 1 || !eps || !mode || !N || !centres || K < 1 || !(tol > 0.0 && tol < 1.0)) return NCS_E_INPUT;
+  if (precision != NCS_FP64 && precision != NCS_FP32 && precision != NCS_MIXED && precision != NCS_DF64)
+    return NCS_E_INPUT;
+  for (int b = 0; b < B; ++b)
+    if (!centres[b] || N[b] < 1 || !(eps[b] > 0.0 && eps[b] < 1.0) || (mode[b] != 0 && mode[b] != 1))
+      return NCS_E_INPUT;
+  ncs_params prm;
+  if (params)
+    prm = *params;
+  else
+    ncs_default_params(&prm);
+  prm.threads = 1;  // one host thread per instance; instances run concurrently
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return NCS_E_CUDA;
+  unsigned hw = std::thread::hardware_concurrency();
+  int W = workers > 0 ? workers : (int)std::max(1u, hw);
+  W = std::min(W, B);
+  std::atomic<int> next(0);
+  std::atomic<double> t_pre(0.0), t_solve(0.0);
+  const auto t0 = std::chrono::steady_clock::now();
+  auto work = [&]() {
+    cudaSetDevice(dev);
+    for (;;) {
+      const int b = next.fetch_add(1);
+      if (b >= B) break;
+      const auto a0 = std::chrono::steady_clock::now();
+      ncs_ctx* c = nullptr;
+      int rc = ncs_create(eps[b], mode[b], K, &prm, &c);
+      if (rc == NCS_OK) rc = ncs_set_patches(c, N[b], centres[b]);
+      const auto a1 = std::chrono::steady_clock::now();
+      double sc = 0.0, is = 0.0, rr = 0.0;
+      int it = 0;
+      if (rc == NCS_OK) rc = ncs_solve(c, tol, precision, nullptr, &sc, &is, &it, &rr);
+      const auto a2 = std::chrono::steady_clock::now();
+      if (scalar) scalar[b] = sc;
+      if (Isigma) Isigma[b] = is;
+      if (iterations) iterations[b] = it;
+      if (relres) relres[b] = rr;
+      if (status) status[b] = rc;
+      ncs_destroy(c);
+      double cur = t_pre.load();
+      while (!t_pre.compare_exchange_weak(cur, cur + std::chrono::duration<double>(a1 - a0).count())) {
+      }
+      cur = t_solve.load();
+      while (!t_solve.compare_exchange_weak(cur, cur + std::chrono::duration<double>(a2 - a1).count())) {
+      }
+    }
+  };
+  std::vector<std::thread> th;
+  for (int w = 0; w < W; ++w) th.emplace_back(work);
+  for (auto& t : th) t.join();
+  const double total = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (seconds) {
+    seconds[0] = t_pre.load();    // summed over instances (set-up: precompute + tree)
+    seconds[1] = t_solve.load();  // summed over instances
+    seconds[2] = total;           // wall clock of the whole batch
+  }
+  if (status)
+    for (int b = 0; b < B; ++b)
+      if (status[b] != NCS_OK) return status[b];
+  return NCS_OK;
 }
 
 const char* ncs_last_error(const ncs_ctx* c) { return c ? c->err.c_str() : g_static_err; }

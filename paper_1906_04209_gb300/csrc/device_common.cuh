@@ -56,4 +56,29 @@ __device__ __forceinline__ float green32(float d2) {
   return u + kLn4f - kLn2f * __log2f(fmaf(2.0f, d, d2));
 }
 
+// One FP32 pair term with pre-scaled source weights w1 = 2 rho, w2 = -log(2) rho:
+//   exterior: G rho = r w1 + log2(1 + 2r) w2                   (r = 1/d)
+//   interior: G rho = r w1 + log2(d^2 (1 + 2r)) w2 + log(4) rho
+// (the constant log(4) rho of the interior kernel is added once per source tile by
+// the caller). Two MUFU operations (rsqrt, lg2) and ~8 FP32 operations per pair.
+template <int MODE>
+__device__ __forceinline__ float pair32(float d2, float w1, float w2, float acc) {
+  const float r = rsqrtf(d2);
+  const float t = fmaf(2.0f, r, 1.0f);
+  const float l = __log2f(MODE == 0 ? t : d2 * t);
+  return fmaf(r, w1, fmaf(l, w2, acc));
+}
+
+// Block-wide sum of a per-thread float (all threads must call; result valid in all threads).
+__device__ __forceinline__ float block_sum(float v, float* scratch32) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) scratch32[w] = v;
+  __syncthreads();
+  float s = 0.0f;
+  for (int i = 0; i < nw; ++i) s += scratch32[i];
+  return s;
+}
+
 }  // namespace ncs

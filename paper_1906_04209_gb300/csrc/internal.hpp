@@ -36,6 +36,10 @@ struct DeviceData {
   float* rho32 = nullptr;
   double* z = nullptr;         // N*Kstar field at the Zernike nodes
   double* I = nullptr;         // K
+  float4* logtab = nullptr;    // 64 x (log c hi, lo, 1/c hi, lo), c = 1 + (i + 0.5)/64
+  float* T32 = nullptr;        // p x K, all T_k stacked (row-major, tensor-core operand)
+  float* P32 = nullptr;        // K x Kstar (row-major, tensor-core operand)
+  int* tc_err = nullptr;       // set by a tensor-core kernel whose bounded wait gave up
 };
 
 // ---- launchers (kernels.cu)
@@ -45,6 +49,13 @@ cudaError_t launch_direct_field(const DeviceData& d, int mode, int prec, double 
 cudaError_t launch_apply_P(const DeviceData& d, const double* x, double* y, cudaStream_t s);
 cudaError_t launch_eval(const DeviceData& d, int mode, int64_t M, const double* targets,
                         double* out, cudaStream_t s);
+
+// ---- tensor-core GEMMs (tc_gemm.cu)
+cudaError_t launch_tc_outgoing(const DeviceData& d, const double* x, const float* T32, int* err, cudaStream_t s);
+cudaError_t launch_tc_apply_P(const DeviceData& d, const double* x, double* y, const float* P32, int* err,
+                              cudaStream_t s);
+cudaError_t launch_tc_gemm_f32(int64_t rows, int cols, int Kd, const float* A, const float* B, float* D, int* err,
+                               cudaStream_t s);
 
 // ---- dense-vector kernels for GMRES (blas.cu)
 cudaError_t launch_dots(int64_t n, int k, const double* V, int64_t ld, const double* w,

@@ -9,6 +9,7 @@
 #include <cstdint>
 
 #include "device_common.cuh"
+#include "df64.cuh"
 #include "internal.hpp"
 
 namespace ncs {
@@ -76,7 +77,7 @@ __global__ void __launch_bounds__(256) outgoing_kernel(int64_t N, int p, int K, 
 
 cudaError_t launch_outgoing(const DeviceData& d, const double* x, int prec, cudaStream_t s) {
   const unsigned blocks = (unsigned)((d.N + OG_PB - 1) / OG_PB);
-  if (prec == NCS_FP64)
+  if (prec == NCS_FP64 || prec == NCS_DF64)
     outgoing_kernel<double><<<blocks, 256, OG_PB * d.K * sizeof(double), s>>>(d.N, d.p, d.K, d.TT64, x,
                                                                                 d.rho64);
   else
@@ -107,15 +108,17 @@ __device__ __forceinline__ int select_rep(double dist, int nrep, const double* _
 
 template <typename R, int MODE>
 __global__ void __launch_bounds__(DF_THREADS) direct_field_kernel(
-    int64_t N, int pt, int Kstar, int JT, int nrep, const int* __restrict__ rep_p, const int* __restrict__ rep_off,
-    const double* __restrict__ rep_rho, double eps, const double* __restrict__ centres,
+    int64_t N, int pt, int Kstar, int JT, int pmax, int nrep, const int* __restrict__ rep_p,
+    const int* __restrict__ rep_off, const double* __restrict__ rep_rho, double eps, const double* __restrict__ centres,
     const double* __restrict__ zloc, const R* __restrict__ soff, const R* __restrict__ rho,
     double* __restrict__ z) {
   using V4 = typename Vec4<R>::type;
   extern __shared__ unsigned char df_smem[];
   V4* S = reinterpret_cast<V4*>(df_smem);  // JT * pmax
+  float* W2 = reinterpret_cast<float*>(S + (size_t)JT * pmax);  // FP32 path: -log(2) rho
   __shared__ double D[DF_JTMAX][3];
   __shared__ int toff[DF_JTMAX + 1], tcol[DF_JTMAX];
+  __shared__ float red32[DF_THREADS / 32];
   const int64_t i = blockIdx.x;
   const double cx = centres[3 * i], cy = centres[3 * i + 1], cz = centres[3 * i + 2];
   double e1[3], e2[3];
@@ -159,6 +162,7 @@ __global__ void __launch_bounds__(DF_THREADS) direct_field_kernel(
     }
     __syncthreads();
     const int ns = toff[nj];
+    float rsum = 0.0f;
     for (int idx = threadIdx.x; idx < ns; idx += DF_THREADS) {
       int jj = 0;
       while (idx >= toff[jj + 1]) ++jj;
@@ -167,9 +171,17 @@ __global__ void __launch_bounds__(DF_THREADS) direct_field_kernel(
       v.x = (R)D[jj][0] + soff[3 * g];
       v.y = (R)D[jj][1] + soff[3 * g + 1];
       v.z = (R)D[jj][2] + soff[3 * g + 2];
-      v.w = rho[g];
+      if constexpr (sizeof(R) == 4) {
+        v.w = 2.0f * rho[g];
+        W2[idx] = -kLn2f * rho[g];
+        rsum += rho[g];
+      } else {
+        v.w = rho[g];
+      }
       S[idx] = v;
     }
+    float tconst = 0.0f;
+    if constexpr (sizeof(R) == 4 && MODE == 1) tconst = kLn4f * block_sum(rsum, red32);
     __syncthreads();
     R part[DF_NT];
 #pragma unroll
@@ -180,16 +192,95 @@ __global__ void __launch_bounds__(DF_THREADS) direct_field_kernel(
       for (int t = 0; t < DF_NT; ++t) {
         const R dx = ax[t] - v.x, dy = ay[t] - v.y, dz = az[t] - v.z;
         const R d2 = fma(dx, dx, fma(dy, dy, dz * dz));
-        R gval;
         if constexpr (sizeof(R) == 8)
-          gval = green64<MODE>(d2);
+          part[t] = fma(green64<MODE>(d2), v.w, part[t]);
         else
-          gval = green32<MODE>(d2);
-        part[t] = fma(gval, v.w, part[t]);
+          part[t] = pair32<MODE>(d2, v.w, W2[s], part[t]);
       }
     }
 #pragma unroll
-    for (int t = 0; t < DF_NT; ++t) acc[t] += (double)part[t];
+    for (int t = 0; t < DF_NT; ++t) acc[t] += (double)part[t] + (double)tconst;
+  }
+#pragma unroll
+  for (int t = 0; t < DF_NT; ++t)
+    if (kk[t] < Kstar) z[i * Kstar + kk[t]] = acc[t];
+}
+
+// Float-float variant (FP64-accurate on the FP32 pipes); sources staged as (hi, lo).
+template <int MODE>
+__global__ void __launch_bounds__(DF_THREADS) direct_field_df_kernel(
+    int64_t N, int pt, int Kstar, int JT, int pmax, int nrep, const int* __restrict__ rep_p,
+    const int* __restrict__ rep_off, const double* __restrict__ rep_rho, double eps,
+    const double* __restrict__ centres, const double* __restrict__ zloc, const double* __restrict__ soff,
+    const double* __restrict__ rho, const float4* __restrict__ logtab, double* __restrict__ z) {
+  extern __shared__ float4 dfd_smem[];
+  __shared__ float4 tab[kLogTable];
+  __shared__ double D[DF_JTMAX][3];
+  __shared__ int toff[DF_JTMAX + 1], tcol[DF_JTMAX];
+  float4* Sh = dfd_smem;
+  float4* Sl = dfd_smem + JT * pmax;
+  for (int t = threadIdx.x; t < kLogTable; t += blockDim.x) tab[t] = logtab[t];
+  const int64_t i = blockIdx.x;
+  const double cx = centres[3 * i], cy = centres[3 * i + 1], cz = centres[3 * i + 2];
+  double e1[3], e2[3];
+  patch_frame(cx, cy, cz, e1, e2);
+  f2 a[DF_NT][3];
+  double acc[DF_NT];
+  int kk[DF_NT];
+#pragma unroll
+  for (int t = 0; t < DF_NT; ++t) {
+    kk[t] = (blockIdx.y * DF_NT + t) * DF_THREADS + threadIdx.x;
+    double g[3] = {0.0, 0.0, 0.0};
+    if (kk[t] < Kstar) frame_apply(e1, e2, cx, cy, cz, zloc[3 * kk[t]], zloc[3 * kk[t] + 1], zloc[3 * kk[t] + 2], g);
+    for (int c = 0; c < 3; ++c) a[t][c] = f2_from_double(g[c]);
+    acc[t] = 0.0;
+  }
+  for (int64_t j0 = 0; j0 < N; j0 += JT) {
+    const int nj = (int)min((int64_t)JT, N - j0);
+    __syncthreads();
+    if (threadIdx.x < nj) {
+      const int64_t j = j0 + threadIdx.x;
+      const double d0 = centres[3 * j] - cx, d1 = centres[3 * j + 1] - cy, d2 = centres[3 * j + 2] - cz;
+      D[threadIdx.x][0] = d0;
+      D[threadIdx.x][1] = d1;
+      D[threadIdx.x][2] = d2;
+      int cnt = 0, col = 0;
+      if (j != i) {
+        const double dist = 2.0 * asin(fmin(1.0, 0.5 * sqrt(d0 * d0 + d1 * d1 + d2 * d2)));
+        const int k = select_rep(dist - eps, nrep, rep_rho);
+        cnt = rep_p[k];
+        col = rep_off[k];
+      }
+      toff[threadIdx.x + 1] = cnt;
+      tcol[threadIdx.x] = col;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      toff[0] = 0;
+      for (int jj = 0; jj < nj; ++jj) toff[jj + 1] += toff[jj];
+    }
+    __syncthreads();
+    const int ns = toff[nj];
+    for (int idx = threadIdx.x; idx < ns; idx += DF_THREADS) {
+      int jj = 0;
+      while (idx >= toff[jj + 1]) ++jj;
+      const int64_t g = (j0 + jj) * pt + tcol[jj] + (idx - toff[jj]);
+      const f2 x = f2_from_double(D[jj][0] + soff[3 * g]), y = f2_from_double(D[jj][1] + soff[3 * g + 1]),
+               zz = f2_from_double(D[jj][2] + soff[3 * g + 2]), r = f2_from_double(rho[g]);
+      Sh[idx] = make_float4(x.hi, y.hi, zz.hi, r.hi);
+      Sl[idx] = make_float4(x.lo, y.lo, zz.lo, r.lo);
+    }
+    __syncthreads();
+    f2 part[DF_NT];
+#pragma unroll
+    for (int t = 0; t < DF_NT; ++t) part[t] = f2{0.0f, 0.0f};
+    for (int s = 0; s < ns; ++s) {
+      const float4 h = Sh[s], l = Sl[s];
+#pragma unroll
+      for (int t = 0; t < DF_NT; ++t) part[t] = f2_add(part[t], pair_f2<MODE>(a[t], h, l, tab));
+    }
+#pragma unroll
+    for (int t = 0; t < DF_NT; ++t) acc[t] += f2_to_double(part[t]);
   }
 #pragma unroll
   for (int t = 0; t < DF_NT; ++t)
@@ -203,16 +294,35 @@ static cudaError_t allow_smem(K kernel, size_t bytes) {
 }
 
 cudaError_t launch_direct_field(const DeviceData& d, int mode, int prec, double eps, cudaStream_t s) {
+  if (prec == NCS_DF64) {
+    int JT = (int)std::min<size_t>(DF_JTMAX, (40 * 1024) / (2 * sizeof(float4) * (size_t)d.pmax));
+    if (JT < 1) JT = 1;
+    const size_t smem = (size_t)2 * JT * d.pmax * sizeof(float4);
+    dim3 grid((unsigned)d.N, (unsigned)((d.Kstar + DF_THREADS * DF_NT - 1) / (DF_THREADS * DF_NT)));
+    cudaError_t e;
+    if (mode == 0) {
+      if ((e = allow_smem(direct_field_df_kernel<0>, smem)) != cudaSuccess) return e;
+      direct_field_df_kernel<0><<<grid, DF_THREADS, smem, s>>>(d.N, d.p, d.Kstar, JT, d.pmax, d.nrep, d.rep_p,
+                                                               d.rep_off, d.rep_rho, eps, d.centres, d.zloc,
+                                                               d.soff64, d.rho64, d.logtab, d.z);
+    } else {
+      if ((e = allow_smem(direct_field_df_kernel<1>, smem)) != cudaSuccess) return e;
+      direct_field_df_kernel<1><<<grid, DF_THREADS, smem, s>>>(d.N, d.p, d.Kstar, JT, d.pmax, d.nrep, d.rep_p,
+                                                               d.rep_off, d.rep_rho, eps, d.centres, d.zloc,
+                                                               d.soff64, d.rho64, d.logtab, d.z);
+    }
+    return cudaGetLastError();
+  }
   const size_t v4 = (prec == NCS_FP64) ? sizeof(double4) : sizeof(float4);
-  int JT = (int)std::min<size_t>(DF_JTMAX, (40 * 1024) / (v4 * (size_t)d.pmax));
+  int JT = (int)std::min<size_t>(DF_JTMAX, (40 * 1024) / ((v4 + 4) * (size_t)d.pmax));
   if (JT < 1) JT = 1;
-  const size_t smem = (size_t)JT * d.pmax * v4;
+  const size_t smem = (size_t)JT * d.pmax * (v4 + 4);
   dim3 grid((unsigned)d.N, (unsigned)((d.Kstar + DF_THREADS * DF_NT - 1) / (DF_THREADS * DF_NT)));
   cudaError_t e;
 #define NCS_DF(R, M, SOFF, RHO)                                                                            \
   do {                                                                                                     \
     if ((e = allow_smem(direct_field_kernel<R, M>, smem)) != cudaSuccess) return e;                       \
-    direct_field_kernel<R, M><<<grid, DF_THREADS, smem, s>>>(d.N, d.p, d.Kstar, JT, d.nrep, d.rep_p,       \
+    direct_field_kernel<R, M><<<grid, DF_THREADS, smem, s>>>(d.N, d.p, d.Kstar, JT, d.pmax, d.nrep, d.rep_p, \
                                                              d.rep_off, d.rep_rho, eps, d.centres, d.zloc, \
                                                              SOFF, RHO, d.z);                              \
   } while (0)

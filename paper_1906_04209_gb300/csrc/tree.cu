@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "device_common.cuh"
+#include "df64.cuh"
 #include "internal.hpp"
 #include "numerics.hpp"
 
@@ -61,12 +62,14 @@ __global__ void __launch_bounds__(P2L_THREADS) p2l_kernel(
     const R* __restrict__ rho, double* __restrict__ grid) {
   using V4 = typename V4T<R>::type;
   extern __shared__ unsigned char p2l_smem[];
-  V4* S = reinterpret_cast<V4*>(p2l_smem);
   __shared__ double D[P2L_JT][3];
+  __shared__ float red32[P2L_THREADS / 32];
   const int item = blockIdx.x;
   const int g = witem_group[item];
   const int rk = witem_rep[item];
   const int p = rep_p[rk], col = rep_off[rk];
+  V4* S = reinterpret_cast<V4*>(p2l_smem);
+  float* W2 = reinterpret_cast<float*>(S + (size_t)P2L_JT * p);  // FP32 path: -log(2) rho
   const int64_t lo = witem_lo[item], hi = witem_hi[item];
   const int sh = gshape[g];
   const int q = shape_nr[sh] * shape_nth[sh];
@@ -96,6 +99,7 @@ __global__ void __launch_bounds__(P2L_THREADS) p2l_kernel(
         D[jj][c] = centres[3 * j + c] - (c == 0 ? gx : (c == 1 ? gy : gz));
       }
       __syncthreads();
+      float rsum = 0.0f;
       for (int idx = threadIdx.x; idx < nj * p; idx += P2L_THREADS) {
         const int jj = idx / p;
         const int64_t gsrc = (int64_t)isrc[s0 + jj] * pt + col + (idx - jj * p);
@@ -103,9 +107,17 @@ __global__ void __launch_bounds__(P2L_THREADS) p2l_kernel(
         v.x = (R)D[jj][0] + soff[3 * gsrc];
         v.y = (R)D[jj][1] + soff[3 * gsrc + 1];
         v.z = (R)D[jj][2] + soff[3 * gsrc + 2];
-        v.w = rho[gsrc];
+        if constexpr (sizeof(R) == 4) {
+          v.w = 2.0f * rho[gsrc];
+          W2[idx] = -kLn2f * rho[gsrc];
+          rsum += rho[gsrc];
+        } else {
+          v.w = rho[gsrc];
+        }
         S[idx] = v;
       }
+      float tconst = 0.0f;
+      if constexpr (sizeof(R) == 4 && MODE == 1) tconst = kLn4f * block_sum(rsum, red32);
       __syncthreads();
       const int ns = nj * p;
       R part[P2L_NT];
@@ -117,16 +129,14 @@ __global__ void __launch_bounds__(P2L_THREADS) p2l_kernel(
         for (int t = 0; t < P2L_NT; ++t) {
           const R dx = ax[t] - v.x, dy = ay[t] - v.y, dz = az[t] - v.z;
           const R d2 = fma(dx, dx, fma(dy, dy, dz * dz));
-          R gv;
           if constexpr (sizeof(R) == 8)
-            gv = green64<MODE>(d2);
+            part[t] = fma(green64<MODE>(d2), v.w, part[t]);
           else
-            gv = green32<MODE>(d2);
-          part[t] = fma(gv, v.w, part[t]);
+            part[t] = pair32<MODE>(d2, v.w, W2[s], part[t]);
         }
       }
 #pragma unroll
-      for (int t = 0; t < P2L_NT; ++t) acc[t] += (double)part[t];
+      for (int t = 0; t < P2L_NT; ++t) acc[t] += (double)part[t] + (double)tconst;
     }
 #pragma unroll
     for (int t = 0; t < P2L_NT; ++t) {
@@ -194,15 +204,17 @@ constexpr int DT_JT = 8;
 
 template <typename R, int MODE>
 __global__ void __launch_bounds__(DT_THREADS) direct_list_kernel(
-    int pt, int Kstar, const int* __restrict__ rep_p, const int* __restrict__ rep_off,
+    int pt, int Kstar, int pmax, const int* __restrict__ rep_p, const int* __restrict__ rep_off,
     const int64_t* __restrict__ pd_off, const int* __restrict__ pd, const int* __restrict__ pdk,
     const double* __restrict__ centres, const double* __restrict__ zloc, const R* __restrict__ soff,
     const R* __restrict__ rho, double* __restrict__ z) {
   using V4 = typename V4T<R>::type;
   extern __shared__ unsigned char dt_smem[];
   V4* S = reinterpret_cast<V4*>(dt_smem);
+  float* W2 = reinterpret_cast<float*>(S + (size_t)DT_JT * pmax);  // FP32 path: -log(2) rho
   __shared__ double D[DT_JT][3];
   __shared__ int toff[DT_JT + 1], tcol[DT_JT];
+  __shared__ float red32[DT_THREADS / 32];
   const int64_t i = blockIdx.x;
   const double cx = centres[3 * i], cy = centres[3 * i + 1], cz = centres[3 * i + 2];
   double e1[3], e2[3];
@@ -238,6 +250,7 @@ __global__ void __launch_bounds__(DT_THREADS) direct_list_kernel(
     }
     __syncthreads();
     const int ns = toff[nj];
+    float rsum = 0.0f;
     for (int idx = threadIdx.x; idx < ns; idx += DT_THREADS) {
       int jj = 0;
       while (idx >= toff[jj + 1]) ++jj;
@@ -246,9 +259,17 @@ __global__ void __launch_bounds__(DT_THREADS) direct_list_kernel(
       v.x = (R)D[jj][0] + soff[3 * gsrc];
       v.y = (R)D[jj][1] + soff[3 * gsrc + 1];
       v.z = (R)D[jj][2] + soff[3 * gsrc + 2];
-      v.w = rho[gsrc];
+      if constexpr (sizeof(R) == 4) {
+        v.w = 2.0f * rho[gsrc];
+        W2[idx] = -kLn2f * rho[gsrc];
+        rsum += rho[gsrc];
+      } else {
+        v.w = rho[gsrc];
+      }
       S[idx] = v;
     }
+    float tconst = 0.0f;
+    if constexpr (sizeof(R) == 4 && MODE == 1) tconst = kLn4f * block_sum(rsum, red32);
     __syncthreads();
     R part[DT_NT];
 #pragma unroll
@@ -259,16 +280,14 @@ __global__ void __launch_bounds__(DT_THREADS) direct_list_kernel(
       for (int t = 0; t < DT_NT; ++t) {
         const R dx = ax[t] - v.x, dy = ay[t] - v.y, dz = az[t] - v.z;
         const R d2 = fma(dx, dx, fma(dy, dy, dz * dz));
-        R gv;
         if constexpr (sizeof(R) == 8)
-          gv = green64<MODE>(d2);
+          part[t] = fma(green64<MODE>(d2), v.w, part[t]);
         else
-          gv = green32<MODE>(d2);
-        part[t] = fma(gv, v.w, part[t]);
+          part[t] = pair32<MODE>(d2, v.w, W2[s], part[t]);
       }
     }
 #pragma unroll
-    for (int t = 0; t < DT_NT; ++t) acc[t] += (double)part[t];
+    for (int t = 0; t < DT_NT; ++t) acc[t] += (double)part[t] + (double)tconst;
   }
 #pragma unroll
   for (int t = 0; t < DT_NT; ++t)
@@ -354,6 +373,224 @@ __global__ void __launch_bounds__(512) l2p_kernel(int Kstar, const int64_t* __re
       cm = cn;
     }
     acc += (double)val;
+  }
+  if (k < Kstar) z[i * Kstar + k] += acc;
+}
+
+// ---- float-float variants (FP64-accurate on the FP32 pipes) -----------------------
+// Sources are staged as (hi, lo) float4 pairs formed from the FP64 offsets and
+// strengths; tile sums are folded into an FP64 accumulator.
+template <int MODE>
+__global__ void __launch_bounds__(P2L_THREADS) p2l_df_kernel(
+    const int* __restrict__ witem_group, const int* __restrict__ witem_rep, const int* __restrict__ rep_p,
+    const int* __restrict__ rep_off, int pt, const int64_t* __restrict__ witem_lo, const int64_t* __restrict__ witem_hi,
+    const int* __restrict__ isrc, const double* __restrict__ gcen, const int* __restrict__ gshape,
+    const int64_t* __restrict__ goff, const int* __restrict__ shape_nr, const int* __restrict__ shape_nth,
+    const double* __restrict__ gpos, const double* __restrict__ centres, const double* __restrict__ soff,
+    const double* __restrict__ rho, const float4* __restrict__ logtab, double* __restrict__ grid) {
+  extern __shared__ float4 p2d_smem[];
+  __shared__ float4 tab[kLogTable];
+  __shared__ double D[P2L_JT][3];
+  const int item = blockIdx.x;
+  const int g = witem_group[item];
+  const int rk = witem_rep[item];
+  const int p = rep_p[rk], col = rep_off[rk];
+  float4* Sh = p2d_smem;
+  float4* Sl = p2d_smem + P2L_JT * p;
+  for (int t = threadIdx.x; t < kLogTable; t += blockDim.x) tab[t] = logtab[t];
+  const int64_t lo = witem_lo[item], hi = witem_hi[item];
+  const int sh = gshape[g];
+  const int q = shape_nr[sh] * shape_nth[sh];
+  const int64_t off = goff[g];
+  const double gx = gcen[3 * g], gy = gcen[3 * g + 1], gz = gcen[3 * g + 2];
+  constexpr int NT = 2;
+  for (int base = 0; base < q; base += P2L_THREADS * NT) {
+    f2 a[NT][3];
+    double acc[NT];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      const int ap = base + t * P2L_THREADS + threadIdx.x;
+      for (int c = 0; c < 3; ++c) a[t][c] = f2_from_double(ap < q ? gpos[3 * (off + ap) + c] : 0.0);
+      acc[t] = 0.0;
+    }
+    for (int64_t s0 = lo; s0 < hi; s0 += P2L_JT) {
+      const int nj = (int)min((int64_t)P2L_JT, hi - s0);
+      __syncthreads();
+      if (threadIdx.x < nj * 3) {
+        const int jj = threadIdx.x / 3, c = threadIdx.x - 3 * jj;
+        D[jj][c] = centres[3 * isrc[s0 + jj] + c] - (c == 0 ? gx : (c == 1 ? gy : gz));
+      }
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < nj * p; idx += P2L_THREADS) {
+        const int jj = idx / p;
+        const int64_t gs = (int64_t)isrc[s0 + jj] * pt + col + (idx - jj * p);
+        const f2 x = f2_from_double(D[jj][0] + soff[3 * gs]), y = f2_from_double(D[jj][1] + soff[3 * gs + 1]),
+                 z = f2_from_double(D[jj][2] + soff[3 * gs + 2]), r = f2_from_double(rho[gs]);
+        Sh[idx] = make_float4(x.hi, y.hi, z.hi, r.hi);
+        Sl[idx] = make_float4(x.lo, y.lo, z.lo, r.lo);
+      }
+      __syncthreads();
+      const int ns = nj * p;
+      f2 part[NT];
+#pragma unroll
+      for (int t = 0; t < NT; ++t) part[t] = f2{0.0f, 0.0f};
+      for (int s = 0; s < ns; ++s) {
+        const float4 h = Sh[s], l = Sl[s];
+#pragma unroll
+        for (int t = 0; t < NT; ++t) part[t] = f2_add(part[t], pair_f2<MODE>(a[t], h, l, tab));
+      }
+#pragma unroll
+      for (int t = 0; t < NT; ++t) acc[t] += f2_to_double(part[t]);
+    }
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      const int ap = base + t * P2L_THREADS + threadIdx.x;
+      if (ap < q) atomicAdd(&grid[off + ap], acc[t]);
+    }
+  }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(DT_THREADS) direct_list_df_kernel(
+    int pt, int Kstar, const int* __restrict__ rep_p, const int* __restrict__ rep_off,
+    const int64_t* __restrict__ pd_off, const int* __restrict__ pd, const int* __restrict__ pdk,
+    const double* __restrict__ centres, const double* __restrict__ zloc, const double* __restrict__ soff,
+    const double* __restrict__ rho, const float4* __restrict__ logtab, int pmax, double* __restrict__ z) {
+  extern __shared__ float4 dtd_smem[];
+  __shared__ float4 tab[kLogTable];
+  __shared__ double D[DT_JT][3];
+  __shared__ int toff[DT_JT + 1], tcol[DT_JT];
+  float4* Sh = dtd_smem;
+  float4* Sl = dtd_smem + DT_JT * pmax;
+  for (int t = threadIdx.x; t < kLogTable; t += blockDim.x) tab[t] = logtab[t];
+  const int64_t i = blockIdx.x;
+  const double cx = centres[3 * i], cy = centres[3 * i + 1], cz = centres[3 * i + 2];
+  double e1[3], e2[3];
+  patch_frame(cx, cy, cz, e1, e2);
+  f2 a[DT_NT][3];
+  double acc[DT_NT];
+  int kk[DT_NT];
+#pragma unroll
+  for (int t = 0; t < DT_NT; ++t) {
+    kk[t] = (blockIdx.y * DT_NT + t) * DT_THREADS + threadIdx.x;
+    double gq[3] = {0.0, 0.0, 0.0};
+    if (kk[t] < Kstar) frame_apply(e1, e2, cx, cy, cz, zloc[3 * kk[t]], zloc[3 * kk[t] + 1], zloc[3 * kk[t] + 2], gq);
+    for (int c = 0; c < 3; ++c) a[t][c] = f2_from_double(gq[c]);
+    acc[t] = 0.0;
+  }
+  const int64_t lo = pd_off[i], hi = pd_off[i + 1];
+  for (int64_t s0 = lo; s0 < hi; s0 += DT_JT) {
+    const int nj = (int)min((int64_t)DT_JT, hi - s0);
+    __syncthreads();
+    if (threadIdx.x < nj) {
+      const int64_t j = pd[s0 + threadIdx.x];
+      const int k = pdk[s0 + threadIdx.x];
+      for (int c = 0; c < 3; ++c) D[threadIdx.x][c] = centres[3 * j + c] - centres[3 * i + c];
+      toff[threadIdx.x + 1] = rep_p[k];
+      tcol[threadIdx.x] = rep_off[k];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      toff[0] = 0;
+      for (int jj = 0; jj < nj; ++jj) toff[jj + 1] += toff[jj];
+    }
+    __syncthreads();
+    const int ns = toff[nj];
+    for (int idx = threadIdx.x; idx < ns; idx += DT_THREADS) {
+      int jj = 0;
+      while (idx >= toff[jj + 1]) ++jj;
+      const int64_t gs = (int64_t)pd[s0 + jj] * pt + tcol[jj] + (idx - toff[jj]);
+      const f2 x = f2_from_double(D[jj][0] + soff[3 * gs]), y = f2_from_double(D[jj][1] + soff[3 * gs + 1]),
+               zz = f2_from_double(D[jj][2] + soff[3 * gs + 2]), r = f2_from_double(rho[gs]);
+      Sh[idx] = make_float4(x.hi, y.hi, zz.hi, r.hi);
+      Sl[idx] = make_float4(x.lo, y.lo, zz.lo, r.lo);
+    }
+    __syncthreads();
+    f2 part[DT_NT];
+#pragma unroll
+    for (int t = 0; t < DT_NT; ++t) part[t] = f2{0.0f, 0.0f};
+    for (int s = 0; s < ns; ++s) {
+      const float4 h = Sh[s], l = Sl[s];
+#pragma unroll
+      for (int t = 0; t < DT_NT; ++t) part[t] = f2_add(part[t], pair_f2<MODE>(a[t], h, l, tab));
+    }
+#pragma unroll
+    for (int t = 0; t < DT_NT; ++t) acc[t] += f2_to_double(part[t]);
+  }
+#pragma unroll
+  for (int t = 0; t < DT_NT; ++t)
+    if (kk[t] < Kstar) z[i * Kstar + kk[t]] = acc[t];
+}
+
+// L2P in float-float: node position in the group's polar coordinates from FP64,
+// coefficients as (hi, lo), Clenshaw and the angle recurrence in float-float.
+__global__ void __launch_bounds__(512) l2p_df_kernel(int Kstar, const int64_t* __restrict__ pg_off,
+                                                     const int* __restrict__ pg, const double* __restrict__ gcen,
+                                                     const double* __restrict__ gR, const int* __restrict__ gshape,
+                                                     const int64_t* __restrict__ goff, const int* __restrict__ shape_nr,
+                                                     const int* __restrict__ shape_nth, const double* __restrict__ coef,
+                                                     const double* __restrict__ centres, const double* __restrict__ zloc,
+                                                     double* __restrict__ z) {
+  extern __shared__ float2 lpd_smem[];
+  const int64_t i = blockIdx.x;
+  const int k = threadIdx.x;
+  const double cx = centres[3 * i], cy = centres[3 * i + 1], cz = centres[3 * i + 2];
+  double e1[3], e2[3], zo[3] = {0.0, 0.0, 0.0};
+  patch_frame(cx, cy, cz, e1, e2);
+  if (k < Kstar) frame_apply(e1, e2, cx, cy, cz, zloc[3 * k], zloc[3 * k + 1], zloc[3 * k + 2], zo);
+  double acc = 0.0;
+  for (int64_t s = pg_off[i]; s < pg_off[i + 1]; ++s) {
+    const int g = pg[s];
+    const int sh = gshape[g];
+    const int nr = shape_nr[sh], nth = shape_nth[sh], q = nr * nth, mh = nth / 2;
+    const int64_t off = goff[g];
+    __syncthreads();
+    for (int t = threadIdx.x; t < q; t += blockDim.x) {
+      const f2 v = f2_from_double(coef[off + t]);
+      lpd_smem[t] = make_float2(v.hi, v.lo);
+    }
+    __syncthreads();
+    if (k >= Kstar) continue;
+    const double gx = gcen[3 * g], gy = gcen[3 * g + 1], gz = gcen[3 * g + 2];
+    double f1[3], f2v[3];
+    patch_frame(gx, gy, gz, f1, f2v);
+    const double dx = (cx - gx) + zo[0], dy = (cy - gy) + zo[1], dz = (cz - gz) + zo[2];
+    const double u1 = dx * f1[0] + dy * f1[1] + dz * f1[2];
+    const double u2 = dx * f2v[0] + dy * f2v[1] + dz * f2v[2];
+    const double u3 = dx * gx + dy * gy + dz * gz;
+    const double sr = sqrt(u1 * u1 + u2 * u2);
+    const double rr = atan2(sr, 1.0 + u3) / gR[g];
+    const f2 rho = f2_from_double(rr);
+    const f2 ct = f2_from_double(sr > 0.0 ? u1 / sr : 1.0), st = f2_from_double(sr > 0.0 ? u2 / sr : 0.0);
+    const f2 y = f2_add(f2_mul(f2{2.0f * rho.hi, 2.0f * rho.lo}, rho), f2{-1.0f, 0.0f});
+    const f2 y2 = f2{2.0f * y.hi, 2.0f * y.lo};
+    f2 cm = {1.0f, 0.0f}, sm = {0.0f, 0.0f}, val = {0.0f, 0.0f};
+    for (int m = 0; m < mh; ++m) {
+      const float2* A = lpd_smem + m * nr;
+      const float2* B = lpd_smem + mh * nr + m * nr;
+      f2 ba1 = {0.f, 0.f}, ba2 = {0.f, 0.f}, bb1 = {0.f, 0.f}, bb2 = {0.f, 0.f};
+      for (int j = nr - 1; j >= 0; --j) {
+        const f2 ta = f2_add(f2_mul(y2, ba1), f2_sub(f2{A[j].x, A[j].y}, ba2));
+        const f2 tb = f2_add(f2_mul(y2, bb1), f2_sub(f2{B[j].x, B[j].y}, bb2));
+        ba2 = ba1;
+        ba1 = ta;
+        bb2 = bb1;
+        bb1 = tb;
+      }
+      f2 sa, sb;
+      if ((m & 1) == 0) {
+        sa = f2_sub(ba1, f2_mul(y, ba2));
+        sb = f2_sub(bb1, f2_mul(y, bb2));
+      } else {
+        sa = f2_mul(rho, f2_sub(ba1, ba2));
+        sb = f2_mul(rho, f2_sub(bb1, bb2));
+      }
+      val = f2_add(val, f2_add(f2_mul(cm, sa), f2_mul(sm, sb)));
+      const f2 cn = f2_sub(f2_mul(cm, ct), f2_mul(sm, st));
+      sm = f2_add(f2_mul(sm, ct), f2_mul(cm, st));
+      cm = cn;
+    }
+    acc += f2_to_double(val);
   }
   if (k < Kstar) z[i * Kstar + k] += acc;
 }
@@ -476,7 +713,7 @@ static cudaError_t tree_field_impl(const DeviceData& dd, const TreeDevice& t, cu
   if (t.nitems > 0) {
     e = cudaMemsetAsync(t.grid, 0, t.ngrid * sizeof(double), s);
     if (e != cudaSuccess) return e;
-    const size_t smem = (size_t)P2L_JT * dd.pmax * sizeof(V4);
+    const size_t smem = (size_t)P2L_JT * dd.pmax * (sizeof(V4) + 4);
     if ((e = allow_smem(p2l_kernel<R, MODE>, smem)) != cudaSuccess) return e;
     p2l_kernel<R, MODE><<<t.nitems, P2L_THREADS, smem, s>>>(t.witem_group, t.witem_rep, dd.rep_p, dd.rep_off, dd.p,
                                                              t.witem_lo, t.witem_hi, t.isrc, t.gcen, t.gshape, t.goff,
@@ -493,10 +730,10 @@ static cudaError_t tree_field_impl(const DeviceData& dd, const TreeDevice& t, cu
   }
   if (ev) cudaEventRecord(ev[2], s);
   {
-    const size_t smem = (size_t)DT_JT * dd.pmax * sizeof(V4);
+    const size_t smem = (size_t)DT_JT * dd.pmax * (sizeof(V4) + 4);
     if ((e = allow_smem(direct_list_kernel<R, MODE>, smem)) != cudaSuccess) return e;
     dim3 grid((unsigned)dd.N, (unsigned)((dd.Kstar + DT_THREADS * DT_NT - 1) / (DT_THREADS * DT_NT)));
-    direct_list_kernel<R, MODE><<<grid, DT_THREADS, smem, s>>>(dd.p, dd.Kstar, dd.rep_p, dd.rep_off, t.pd_off, t.pd,
+    direct_list_kernel<R, MODE><<<grid, DT_THREADS, smem, s>>>(dd.p, dd.Kstar, dd.pmax, dd.rep_p, dd.rep_off, t.pd_off, t.pd,
                                                                 t.pdk, dd.centres, dd.zloc, soff, rho, dd.z);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
@@ -513,8 +750,53 @@ static cudaError_t tree_field_impl(const DeviceData& dd, const TreeDevice& t, cu
   return cudaSuccess;
 }
 
+template <int MODE>
+static cudaError_t tree_field_df(const DeviceData& dd, const TreeDevice& t, cudaStream_t s, cudaEvent_t* ev) {
+  cudaError_t e;
+  if (ev) cudaEventRecord(ev[0], s);
+  if (t.nitems > 0) {
+    if ((e = cudaMemsetAsync(t.grid, 0, t.ngrid * sizeof(double), s)) != cudaSuccess) return e;
+    const size_t smem = (size_t)2 * P2L_JT * dd.pmax * sizeof(float4);
+    if ((e = allow_smem(p2l_df_kernel<MODE>, smem)) != cudaSuccess) return e;
+    p2l_df_kernel<MODE><<<t.nitems, P2L_THREADS, smem, s>>>(t.witem_group, t.witem_rep, dd.rep_p, dd.rep_off, dd.p,
+                                                           t.witem_lo, t.witem_hi, t.isrc, t.gcen, t.gshape, t.goff,
+                                                           t.shape_nr, t.shape_nth, t.gpos64, dd.centres, dd.soff64,
+                                                           dd.rho64, dd.logtab, t.grid);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[1], s);
+    const size_t csm = (size_t)t.max_q * sizeof(double) + (size_t)t.max_nth * t.max_nr * sizeof(double);
+    if ((e = allow_smem(coef_kernel<double>, csm)) != cudaSuccess) return e;
+    coef_kernel<double><<<t.ngroups, 256, csm, s>>>(t.gshape, t.goff, t.shape_nr, t.shape_nth, t.grid, t.coef);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  } else if (ev) {
+    cudaEventRecord(ev[1], s);
+  }
+  if (ev) cudaEventRecord(ev[2], s);
+  {
+    const size_t smem = (size_t)2 * DT_JT * dd.pmax * sizeof(float4);
+    if ((e = allow_smem(direct_list_df_kernel<MODE>, smem)) != cudaSuccess) return e;
+    dim3 grid((unsigned)dd.N, (unsigned)((dd.Kstar + DT_THREADS * DT_NT - 1) / (DT_THREADS * DT_NT)));
+    direct_list_df_kernel<MODE><<<grid, DT_THREADS, smem, s>>>(dd.p, dd.Kstar, dd.rep_p, dd.rep_off, t.pd_off, t.pd,
+                                                              t.pdk, dd.centres, dd.zloc, dd.soff64, dd.rho64,
+                                                              dd.logtab, dd.pmax, dd.z);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (ev) cudaEventRecord(ev[3], s);
+  if (t.nitems > 0) {
+    if (dd.Kstar > 512) return cudaErrorInvalidConfiguration;
+    const size_t smem = (size_t)t.max_q * sizeof(float2);
+    if ((e = allow_smem(l2p_df_kernel, smem)) != cudaSuccess) return e;
+    l2p_df_kernel<<<(unsigned)dd.N, 512, smem, s>>>(dd.Kstar, t.pg_off, t.pg, t.gcen, t.gR, t.gshape, t.goff,
+                                                   t.shape_nr, t.shape_nth, t.coef, dd.centres, dd.zloc, dd.z);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (ev) cudaEventRecord(ev[4], s);
+  return cudaSuccess;
+}
+
 cudaError_t launch_tree_field(const DeviceData& d, const TreeDevice& t, int mode, int prec, cudaStream_t s,
                               cudaEvent_t* ev) {
+  if (prec == NCS_DF64) return mode == 0 ? tree_field_df<0>(d, t, s, ev) : tree_field_df<1>(d, t, s, ev);
   if (prec == NCS_FP64)
     return mode == 0 ? tree_field_impl<double, 0>(d, t, s, ev) : tree_field_impl<double, 1>(d, t, s, ev);
   return mode == 0 ? tree_field_impl<float, 0>(d, t, s, ev) : tree_field_impl<float, 1>(d, t, s, ev);

@@ -22,20 +22,21 @@ NCS_E_TIMEOUT = -5
 NCS_E_OOM = -6
 NCS_E_STATE = -7
 EXTERIOR, INTERIOR = 0, 1
-FP64, FP32, MIXED = 0, 1, 2
+FP64, FP32, MIXED, DF64 = 0, 1, 2, 3
 METHOD_AUTO, METHOD_DIRECT, METHOD_TREE = 0, 1, 2
 
 EXPORTS = ["ncs_default_params", "ncs_create", "ncs_create_from_operator", "ncs_info", "ncs_timings",
            "ncs_get_operator", "ncs_get_onepatch", "ncs_set_patches", "ncs_set_method", "ncs_matvec",
            "ncs_matvec_dev", "ncs_field_dev", "ncs_solve", "ncs_eval", "ncs_last_error", "ncs_destroy",
-           "ncs_tree_pairs", "ncs_tree_stats", "ncs_profile_matvec", "ncs_create_from_operators", "ncs_get_reps"]
+           "ncs_tree_pairs", "ncs_tree_stats", "ncs_profile_matvec", "ncs_create_from_operators", "ncs_get_reps",
+           "ncs_tc_gemm_f32", "ncs_batch_solve"]
 
 
 class ncs_params(ctypes.Structure):
     _fields_ = [("npan", ctypes.c_int), ("nord", ctypes.c_int), ("ntheta_fine", ctypes.c_int),
                 ("id_tol", ctypes.c_double), ("threads", ctypes.c_int), ("grid_tol", ctypes.c_double),
                 ("method", ctypes.c_int), ("tree_min_patches", ctypes.c_int), ("gmres_maxit", ctypes.c_int),
-                ("verbose", ctypes.c_int)]
+                ("verbose", ctypes.c_int), ("mixed_residual", ctypes.c_int), ("tensor_cores", ctypes.c_int)]
 
 
 class NcsError(RuntimeError):
@@ -84,6 +85,11 @@ def load(path: str = LIB_PATH):
     lib.ncs_tree_pairs.argtypes = [VP, ctypes.POINTER(ctypes.c_int64), I32, I32, I32, I32]
     lib.ncs_tree_stats.argtypes = [VP, ctypes.POINTER(ctypes.c_int64), ctypes.c_int]
     lib.ncs_profile_matvec.argtypes = [VP, VP, VP, ctypes.c_int, VP, D, ctypes.c_int]
+    lib.ncs_tc_gemm_f32.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_int, VP, VP, VP, VP]
+    lib.ncs_batch_solve.argtypes = [ctypes.c_int, D, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64),
+                                    ctypes.POINTER(D), ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                    ctypes.POINTER(ncs_params), ctypes.c_int, D, D, ctypes.POINTER(ctypes.c_int), D,
+                                    ctypes.POINTER(ctypes.c_int), D]
     lib.ncs_destroy.argtypes = [VP]
     lib.ncs_destroy.restype = None
     for name in EXPORTS:
@@ -102,6 +108,33 @@ def _f64(a, shape=None):
     if shape is not None:
         a = a.reshape(shape)
     return a
+
+
+def tc_gemm_f32(rows, cols, kdim, A_ptr, B_ptr, D_ptr, stream=0):
+    """D = A B^T on the tensor cores (see ncs_tc_gemm_f32); device pointers."""
+    rc = load().ncs_tc_gemm_f32(rows, cols, kdim, VP(A_ptr), VP(B_ptr), VP(D_ptr), VP(stream))
+    if rc != NCS_OK:
+        raise NcsError(rc, "ncs_tc_gemm_f32 failed")
+
+
+def batch_solve(instances, K, tol=1e-8, precision=MIXED, workers=0, **kw):
+    """instances: list of (centres (N x 3), eps, mode). Returns a dict of per-instance
+    arrays and timings (see ncs_batch_solve)."""
+    lib = load()
+    B = len(instances)
+    eps = np.ascontiguousarray([e for _, e, _ in instances], dtype=np.float64)
+    mode = np.ascontiguousarray([m for _, _, m in instances], dtype=np.int32)
+    cs = [_f64(c).reshape(-1, 3) for c, _, _ in instances]
+    N = np.ascontiguousarray([c.shape[0] for c in cs], dtype=np.int64)
+    ptrs = (D * B)(*[c.ctypes.data_as(D) for c in cs])
+    sc, Is, rr, secs = np.zeros(B), np.zeros(B), np.zeros(B), np.zeros(3)
+    it, st = np.zeros(B, dtype=np.int32), np.zeros(B, dtype=np.int32)
+    prm = default_params(**kw)
+    I32 = ctypes.POINTER(ctypes.c_int)
+    rc = lib.ncs_batch_solve(B, _ptr(eps), mode.ctypes.data_as(I32), N.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                             ptrs, K, tol, precision, ctypes.byref(prm), workers, _ptr(sc), _ptr(Is),
+                             it.ctypes.data_as(I32), _ptr(rr), st.ctypes.data_as(I32), _ptr(secs))
+    return dict(rc=rc, scalar=sc, Isigma=Is, iterations=it, relres=rr, status=st, seconds=secs)
 
 
 def default_params(**kw) -> ncs_params:

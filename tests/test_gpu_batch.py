@@ -1,0 +1,35 @@
+"""Batched solve of independent spheres (uneven N and eps, both modes) through the C ABI:
+every instance matches its own single-context solve."""
+import numpy as np
+import pytest
+
+from paper_1906_04209_gb300 import layouts as L, ncs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda(libncs):
+    assert torch.cuda.is_available(), "GPU test without a GPU"
+    torch.cuda.set_device(0)
+
+
+def test_batch_matches_individual():
+    g = L.rng(77)
+    inst = []
+    for b in range(6):
+        N = int(g.integers(20, 300))
+        eps = float(g.uniform(0.01, 0.02))
+        inst.append((L.uniform(N, eps, L.rng(77, b + 1)), eps, b % 2))
+    kw = dict(npan=6, nord=10, ntheta_fine=24, method=ncs.METHOD_DIRECT)
+    out = ncs.batch_solve(inst, 21, tol=1e-10, precision=ncs.MIXED, workers=3, **kw)
+    assert out["rc"] == 0 and (out["status"] == 0).all()
+    assert out["seconds"][2] > 0
+    for b, (c, eps, mode) in enumerate(inst):
+        ctx = ncs.Context(eps, mode, 21, **kw)
+        ctx.set_patches(c)
+        r = ctx.solve(tol=1e-10, precision=ncs.MIXED)
+        assert abs(out["scalar"][b] - r["scalar"]) <= 1e-9 * abs(r["scalar"])
+        assert out["relres"][b] <= 1e-10

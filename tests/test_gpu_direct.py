@@ -45,10 +45,12 @@ def test_field_parity_shared_operator(small_pre, mode, N):
     scale = max(np.abs(ref).max(), 1e-300)
     z64 = _field_gpu(ctx, x, ncs.FP64, N, pre.Kstar)
     z32 = _field_gpu(ctx, x, ncs.FP32, N, pre.Kstar)
+    zdf = _field_gpu(ctx, x, ncs.DF64, N, pre.Kstar)
     if N == 1:
-        assert np.abs(z64).max() == 0.0 and np.abs(z32).max() == 0.0
+        assert np.abs(z64).max() == 0.0 and np.abs(z32).max() == 0.0 and np.abs(zdf).max() == 0.0
         return
     assert np.abs(z64 - ref).max() <= 1e-12 * scale
+    assert np.abs(zdf - ref).max() <= 1e-12 * scale
     assert np.abs(z32 - ref).max() <= 2e-6 * scale
 
 
@@ -103,6 +105,8 @@ def test_solve_vs_oracle(small_pre, mode):
     rm = ctx.solve(tol=1e-10, precision=ncs.MIXED)
     assert rm["relres"] <= 1e-10
     assert np.abs(rm["fhat"] - x_ref).max() <= 1e-8 * np.abs(x_ref).max()
+    rd = ctx.solve(tol=1e-11, precision=ncs.DF64)
+    assert np.abs(rd["fhat"] - x_ref).max() <= 1e-9 * np.abs(x_ref).max()
     r32 = ctx.solve(tol=1e-5, precision=ncs.FP32)
     assert np.abs(r32["fhat"] - x_ref).max() <= 1e-4 * np.abs(x_ref).max()
 

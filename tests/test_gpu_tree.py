@@ -46,10 +46,14 @@ def test_tree_vs_compressed_sums(small_pre, mode):
     patches = np.random.default_rng(12).choice(N, 12, replace=False)
     ref = O.id_field(pre, c, x, patches)
     scale = np.abs(ref).max()
-    z64 = _field(ctx, x, ncs.FP64, N, pre.Kstar)[patches]
+    zf64 = _field(ctx, x, ncs.FP64, N, pre.Kstar)
+    zfdf = _field(ctx, x, ncs.DF64, N, pre.Kstar)
+    z64 = zf64[patches]
     z32 = _field(ctx, x, ncs.FP32, N, pre.Kstar)[patches]
     assert np.abs(z64 - ref).max() <= 1e-8 * scale
     assert np.abs(z32 - ref).max() <= 5e-6 * scale
+    # float-float tree product = FP64 tree product to rounding (same grids, same lists)
+    assert np.abs(zfdf - zf64).max() <= 1e-12 * np.abs(zf64).max()
     # the direct product on the same context agrees as well
     ctx.set_method(ncs.METHOD_DIRECT)
     zd = _field(ctx, x, ncs.FP64, N, pre.Kstar)[patches]
@@ -89,9 +93,9 @@ def test_full_size_sampled(libncs):
     nodes = rng.choice(pre.Kstar, 48)
     ref = native.rows(pre, c, x, patches, nodes)
     scale = np.abs(ref).max()
-    z64 = _field(ctx, x, ncs.FP64, N, pre.Kstar)[patches, nodes]
+    zdf = _field(ctx, x, ncs.DF64, N, pre.Kstar)[patches, nodes]
     z32 = _field(ctx, x, ncs.FP32, N, pre.Kstar)[patches, nodes]
-    assert np.abs(z64 - ref).max() <= 1e-6 * scale
+    assert np.abs(zdf - ref).max() <= 1e-6 * scale
     assert np.abs(z32 - ref).max() <= 1e-5 * scale
 
 

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def test_exports_match_header(libncs):
     hdr = open(os.path.join(ROOT, "include", "ncs.h")).read()
-    names = set(re.findall(r"\b(ncs_[a-z_]+)\s*\(", hdr))
+    names = set(re.findall(r"\b(ncs_[a-z0-9_]+)\s*\(", hdr))
     assert names, "no declarations found"
     for n in names:
         assert hasattr(libncs, n), n
