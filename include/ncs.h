@@ -236,6 +236,16 @@ int ncs_solve(ncs_ctx* ctx, double tol, int precision, double* fhat, double* sca
 int ncs_eval(ncs_ctx* ctx, int64_t M, const double* targets, const double* fhat, double* out);
 
 /*
+ * The projections of one GMRES Arnoldi step (Section 7, Step 3; classical Gram-Schmidt
+ * on the device): out[j] = V_j . w for j < k, V_j = V + j*ld, all device FP64 arrays
+ * (n entries each; out holds k), reduced deterministically in two stages (fixed
+ * chunks, then a per-vector sum). Allocates its k x 64 partial sums with cudaMalloc
+ * for the duration of the call; synchronous on `stream`.
+ * Errors: NCS_E_INPUT, NCS_E_OOM, NCS_E_CUDA.
+ */
+int ncs_block_dots(int64_t n, int k, const double* V, int64_t ld, const double* w, double* out, void* stream);
+
+/*
  * The library's tensor-core GEMM on its own: D = A B^T with A (rows x kdim), B
  * (cols x kdim) and D (rows x cols), all row-major FP32 device arrays, computed with
  * tcgen05 kind::tf32 MMAs on hi/lo TF32 splits (3 products, ~FP32 accuracy) - the

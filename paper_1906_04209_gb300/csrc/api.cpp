@@ -937,6 +937,19 @@ int ncs_eval(ncs_ctx* c, int64_t M, const double* targets, const double* fhat, d
   }
 }
 
+int ncs_block_dots(int64_t n, int k, const double* V, int64_t ld, const double* w, double* out, void* stream) {
+  if (n < 0 || k < 0 || ld < n || (k > 0 && (!V || !w || !out))) return NCS_E_INPUT;
+  if (k == 0) return NCS_OK;
+  double* partial = nullptr;
+  if (cudaMalloc(&partial, (size_t)ncs::kDotChunks * k * sizeof(double)) != cudaSuccess) return NCS_E_OOM;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = NCS_OK;
+  if (ncs::launch_dots(n, k, V, ld, w, partial, out, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+    rc = NCS_E_CUDA;
+  cudaFree(partial);
+  return rc;
+}
+
 int ncs_tc_gemm_f32(int64_t rows, int cols, int kdim, const float* A, const float* B, float* D, void* stream) {
   if (rows < 0 || cols < 0 || kdim < 1 || !A || !B || !D) return NCS_E_INPUT;
   if (rows == 0 || cols == 0) return NCS_OK;

@@ -33,3 +33,17 @@ def test_batch_matches_individual():
         r = ctx.solve(tol=1e-10, precision=ncs.MIXED)
         assert abs(out["scalar"][b] - r["scalar"]) <= 1e-9 * abs(r["scalar"])
         assert out["relres"][b] <= 1e-10
+
+
+def test_block_dots():
+    """The Arnoldi projections V^T w through the C ABI against numpy."""
+    rng = np.random.default_rng(5)
+    n, k = 100_003, 37
+    V = rng.standard_normal((k, n))
+    w = rng.standard_normal(n)
+    Vd = torch.tensor(V, device="cuda")
+    wd = torch.tensor(w, device="cuda")
+    out = torch.empty(k, dtype=torch.float64, device="cuda")
+    ncs.block_dots(n, k, Vd.data_ptr(), n, wd.data_ptr(), out.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    ref = V @ w
+    assert np.abs(out.cpu().numpy() - ref).max() <= 1e-12 * np.abs(V).max() * np.abs(w).max() * np.sqrt(n)
