@@ -191,6 +191,17 @@ def run_ours(args):
         torch.cuda.synchronize()
         fp64 = 1000.0 * args.fp64_steps / e0.elapsed_time(e1)
 
+    df64 = None
+    if args.df64_steps > 0:
+        step(ncs.DF64)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.df64_steps):
+            step(ncs.DF64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        df64 = 1000.0 * args.df64_steps / e0.elapsed_time(e1)
+
     solve = None
     if args.solve:
         solve = {}
@@ -240,6 +251,7 @@ def run_ours(args):
         "clocks": clk,
         "stages_ms": {k: round(v, 3) for k, v in stages32.items()},
         "fp64_matvecs_per_s": round(fp64, 4) if fp64 else None,
+        "df64_matvecs_per_s": round(df64, 4) if df64 else None,
         "pairs_per_step": tstats["p2l_pairs"] + tstats["direct_pairs"],
         "pair_rate_per_s": round((tstats["p2l_pairs"] + tstats["direct_pairs"]) * 1000.0 / ms_step, 1),
         "solve": solve,
@@ -307,6 +319,7 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--grid-tol", type=float, default=1e-8)
     ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--df64-steps", type=int, default=2)
     ap.add_argument("--solve", action="store_true")
     ap.add_argument("--solve-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")

@@ -174,8 +174,9 @@ int ncs_tree_pairs(ncs_ctx* ctx, int64_t* count, int* target, int* source, int* 
 /*
  * Tree statistics into out[0..n): levels, grid groups, grid points, P2L work items,
  * P2L kernel evaluations, direct kernel evaluations, L2P node-grid products,
- * direct (target, source) patch pairs, distinct grid shapes. Builds the host tree if
- * needed (host-only).
+ * direct (target, source) patch pairs, distinct grid shapes, grid-to-grid links of
+ * the downward pass, their point-grid products. Builds the host tree if needed
+ * (host-only).
  */
 int ncs_tree_stats(ncs_ctx* ctx, int64_t* out, int n);
 

@@ -673,10 +673,10 @@ int ncs_tree_stats(ncs_ctx* c, int64_t* out, int n) {
     if (c->centres.empty()) throw Fail{NCS_E_STATE, "no patches: call ncs_set_patches first"};
     ensure_tree_host(c);
     const ncs::TreeHost& t = c->tree;
-    const int64_t v[9] = {t.levels, (int64_t)t.gR.size(), t.total_grid_points, (int64_t)t.witem_group.size(),
-                          t.p2l_pairs, t.direct_pairs, t.l2p_evals, t.pd_off.empty() ? 0 : t.pd_off.back(),
-                          (int64_t)t.shapes.size()};
-    for (int i = 0; i < n && i < 9; ++i) out[i] = v[i];
+    const int64_t v[11] = {t.levels, (int64_t)t.gR.size(), t.total_grid_points, (int64_t)t.witem_group.size(),
+                           t.p2l_pairs, t.direct_pairs, t.l2p_evals, t.pd_off.empty() ? 0 : t.pd_off.back(),
+                           (int64_t)t.shapes.size(), (int64_t)t.l2l_child.size(), t.l2l_evals};
+    for (int i = 0; i < n && i < 11; ++i) out[i] = v[i];
     return NCS_OK;
   } catch (const Fail& f) {
     return finish(c, f);

@@ -35,6 +35,21 @@ __device__ __forceinline__ void frame_apply(const double* e1, const double* e2, 
   g[2] = o0 * e1[2] + o1 * e2[2] + o2 * cz;
 }
 
+// Bare MUFU approximations (PTX rsqrt.approx / lg2.approx with denormals flushed):
+// the arguments here are never denormal, and the IEEE-mode wrappers cost extra
+// instructions per pair.
+__device__ __forceinline__ float rsqrt_mufu(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ float lg2_mufu(float x) {
+  float r;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 // G(d) from d^2, eqs. (Gextonsurface) / (Gintonsurface), one logarithm each:
 //   exterior: G_E = u - log(1 + u),           u = 2/d
 //   interior: G_I = u + log 4 - log(d^2 + 2d)
@@ -49,11 +64,11 @@ __device__ __forceinline__ double green64(double d2) {
 
 template <int MODE>
 __device__ __forceinline__ float green32(float d2) {
-  const float rinv = rsqrtf(d2);
+  const float rinv = rsqrt_mufu(d2);
   const float u = 2.0f * rinv;
-  if (MODE == 0) return u - kLn2f * __log2f(1.0f + u);
+  if (MODE == 0) return u - kLn2f * lg2_mufu(1.0f + u);
   const float d = d2 * rinv;
-  return u + kLn4f - kLn2f * __log2f(fmaf(2.0f, d, d2));
+  return u + kLn4f - kLn2f * lg2_mufu(fmaf(2.0f, d, d2));
 }
 
 // One FP32 pair term with pre-scaled source weights w1 = 2 rho, w2 = -log(2) rho:
@@ -63,9 +78,9 @@ __device__ __forceinline__ float green32(float d2) {
 // the caller). Two MUFU operations (rsqrt, lg2) and ~8 FP32 operations per pair.
 template <int MODE>
 __device__ __forceinline__ float pair32(float d2, float w1, float w2, float acc) {
-  const float r = rsqrtf(d2);
+  const float r = rsqrt_mufu(d2);
   const float t = fmaf(2.0f, r, 1.0f);
-  const float l = __log2f(MODE == 0 ? t : d2 * t);
+  const float l = lg2_mufu(MODE == 0 ? t : d2 * t);
   return fmaf(r, w1, fmaf(l, w2, acc));
 }
 

@@ -7,6 +7,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "device_common.cuh"
+
 namespace ncs {
 
 struct f2 {
@@ -99,7 +101,7 @@ __device__ __forceinline__ f2 f2_log(f2 v, const float4* __restrict__ tab) {
 // 1/d from the FP32 reciprocal square root refined by one Newton step in float-float.
 template <int MODE>
 __device__ __forceinline__ f2 green_f2(f2 d2, const float4* __restrict__ tab) {
-  const float y = rsqrtf(d2.hi);
+  const float y = rsqrt_mufu(d2.hi);
   const f2 yy = two_prod(y, y);
   f2 m = two_prod(d2.hi, yy.hi);
   m.lo = fmaf(d2.hi, yy.lo, fmaf(d2.lo, yy.hi, m.lo));

@@ -336,6 +336,30 @@ void tree_build(const std::vector<double>& centres, const Precomputed& pc, const
     return (int)t.shapes.size() - 1;
   };
   const int CH = 16;  // source patches per P2L work item
+  // Bounding circles (Section 7.3) of every group: smallest enclosing circle of the
+  // members' centres in the gnomonic plane at their mean direction, radius + eps; then,
+  // bottom-up, each radius grows until the disk contains the disks of its children that
+  // may keep a grid, so that grid disks nest along the tree (needed by the downward pass).
+  std::vector<std::vector<double>> gcirc(nl), grad(nl);
+  for (int l = 0; l < nl; ++l) {
+    const Level& L = S.lv[l];
+    gcirc[l].resize(3 * L.keys.size());
+    grad[l].resize(L.keys.size());
+    for (size_t g = 0; g < L.keys.size(); ++g)
+      grad[l][g] = bounding_circle(centres, L.members[g], &gcirc[l][3 * g]) + eps * (1.0 + 1e-9);
+  }
+  for (int l = nl - 1; l >= 1; --l) {
+    const Level& L = S.lv[l];
+    const Level& P = S.lv[l - 1];
+    for (size_t g = 0; g < L.keys.size(); ++g) {
+      // a single-patch group never keeps a grid, and its patch already lies in the
+      // parent's disk (which includes eps around every member centre)
+      if ((int)L.members[g].size() < opt.grid_min_members) continue;
+      const int pg = P.group_of[L.members[g][0]];
+      const double need = geodesic(&gcirc[l - 1][3 * pg], &gcirc[l][3 * g]) + grad[l][g];
+      grad[l - 1][pg] = std::max(grad[l - 1][pg], need * (1.0 + 1e-12));
+    }
+  }
   for (int l = 0; l < nl; ++l) {
     const Level& L = S.lv[l];
     for (size_t g = 0; g < L.keys.size(); ++g) {
@@ -344,10 +368,8 @@ void tree_build(const std::vector<double>& centres, const Precomputed& pc, const
       std::vector<int> srcs;
       for (int h : L.il[g])
         for (int j : L.members[h]) srcs.push_back(j);
-      // bounding circle (Section 7.3): smallest enclosing circle of the members'
-      // centres in the gnomonic plane at their mean direction, radius + eps
-      double c[3];
-      double R = bounding_circle(centres, mem, c) + eps * (1.0 + 1e-9);
+      double c[3] = {gcirc[l][3 * g], gcirc[l][3 * g + 1], gcirc[l][3 * g + 2]};
+      const double R = grad[l][g];
       // sources sorted by distance, so that P2L work items hold similar distances
       std::vector<std::pair<double, int>> sd;
       for (int j : srcs) sd.push_back({geodesic(c, &centres[3 * j]), j});
@@ -405,6 +427,53 @@ void tree_build(const std::vector<double>& centres, const Precomputed& pc, const
       for (int h : L.nbrs[g])
         for (int i : L.members[g])
           for (int j : L.members[h]) direct[i].push_back(j);
+  }
+  // Downward pass (a GB300-side reorganisation of Step 3.4): each grid group receives
+  // the field of its nearest grid ancestor by interpolation at its own grid points when
+  // its whole grid disk lies inside the ancestor's disk; a patch then interpolates only
+  // its deepest grid, plus any ancestor whose link could not be made.
+  const int G = (int)t.gR.size();
+  {
+    std::vector<int> parent(G, -1);
+    std::vector<char> linked(G, 0);
+    for (int i = 0; i < N; ++i)
+      for (size_t a = 1; a < pgroups[i].size(); ++a) parent[pgroups[i][a]] = pgroups[i][a - 1];
+    for (int g = 0; g < G; ++g) {
+      const int a = parent[g];
+      if (a < 0) continue;
+      const double dist = geodesic(&t.gcen[3 * a], &t.gcen[3 * g]);
+      linked[g] = (dist + t.gR[g] <= t.gR[a] * (1.0 - 1e-12)) ? 1 : 0;
+    }
+    t.gl_off.assign(nl + 1, 0);
+    for (int g = 0; g < G; ++g) t.gl_off[t.glevel[g] + 1]++;
+    for (int l = 0; l < nl; ++l) t.gl_off[l + 1] += t.gl_off[l];
+    std::vector<std::vector<std::pair<int, int>>> bylevel(nl);
+    for (int g = 0; g < G; ++g)
+      if (linked[g]) {
+        bylevel[t.glevel[parent[g]]].push_back({g, parent[g]});
+        t.l2l_evals += (int64_t)t.shapes[t.gshape[g]].q() * t.shapes[t.gshape[parent[g]]].q();
+      }
+    t.l2l_off.assign(nl + 1, 0);
+    for (int l = 0; l < nl; ++l) {
+      for (auto& cp : bylevel[l]) {
+        t.l2l_child.push_back(cp.first);
+        t.l2l_parent.push_back(cp.second);
+      }
+      t.l2l_off[l + 1] = (int)t.l2l_child.size();
+    }
+    t.l2p_evals = 0;
+    for (int i = 0; i < N; ++i) {
+      if (pgroups[i].empty()) continue;
+      std::vector<int> keep;
+      int cur = pgroups[i].back();
+      keep.push_back(cur);
+      while (parent[cur] >= 0) {
+        if (!linked[cur]) keep.push_back(parent[cur]);
+        cur = parent[cur];
+      }
+      pgroups[i] = keep;
+      for (int g : keep) t.l2p_evals += (int64_t)pc.Kstar * t.shapes[t.gshape[g]].q();
+    }
   }
   t.pd_off.assign(N + 1, 0);
   t.pg_off.assign(N + 1, 0);

@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <stdexcept>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "device_common.cuh"
@@ -154,11 +155,11 @@ __global__ void __launch_bounds__(P2L_THREADS) p2l_kernel(
 //   A_mj = (2 - delta_d0)/nr sum_a C_m(r_a) T_d(x_a), d = 2j + (m mod 2),
 //   x_a = cos((2a + 1) pi / (4 nr)).
 template <typename R>
-__global__ void __launch_bounds__(256) coef_kernel(const int* __restrict__ gshape, const int64_t* __restrict__ goff,
+__global__ void __launch_bounds__(256) coef_kernel(int g0, const int* __restrict__ gshape, const int64_t* __restrict__ goff,
                                                    const int* __restrict__ shape_nr, const int* __restrict__ shape_nth,
                                                    const double* __restrict__ grid, double* __restrict__ coef) {
   extern __shared__ double cf_smem[];
-  const int g = blockIdx.x;
+  const int g = g0 + blockIdx.x;
   const int sh = gshape[g];
   const int nr = shape_nr[sh], nth = shape_nth[sh], q = nr * nth, mh = nth / 2;
   const int64_t off = goff[g];
@@ -294,7 +295,58 @@ __global__ void __launch_bounds__(DT_THREADS) direct_list_kernel(
     if (kk[t] < Kstar) z[i * Kstar + kk[t]] = acc[t];
 }
 
-// L2P: z_i(k) += interpolant of every grid group of patch i at node k.
+// Value at (rho = r/R, cos th, sin th) of a group expansion with coefficients C
+// (A[m][j] then B[m][j]): Clenshaw in y = T_2(rho) over the even (T_2j) and odd
+// (T_2j+1) radial series, cos/sin(m th) by the angle-addition recurrence.
+template <typename R>
+__device__ __forceinline__ R eval_expansion(const R* C, int nr, int mh, R rho, R ct, R st) {
+  const R y = fma((R)2 * rho, rho, (R)-1);
+  const R y2 = y + y;
+  R cm = 1, sm = 0, val = 0;
+  for (int m = 0; m < mh; ++m) {
+    const R* A = C + m * nr;
+    const R* B = C + mh * nr + m * nr;
+    R ba1 = 0, ba2 = 0, bb1 = 0, bb2 = 0;
+    for (int j = nr - 1; j >= 0; --j) {
+      const R ta = fma(y2, ba1, A[j] - ba2);
+      const R tb = fma(y2, bb1, B[j] - bb2);
+      ba2 = ba1;
+      ba1 = ta;
+      bb2 = bb1;
+      bb1 = tb;
+    }
+    R sa, sb;
+    if ((m & 1) == 0) {  // phi_0 = 1, phi_1 = y: sum = b0 - y b1
+      sa = fma(-y, ba2, ba1);
+      sb = fma(-y, bb2, bb1);
+    } else {  // phi_0 = rho, phi_1 = T_3(rho) = rho (2y - 1): sum = rho (b0 - b1)
+      sa = rho * (ba1 - ba2);
+      sb = rho * (bb1 - bb2);
+    }
+    val = fma(cm, sa, fma(sm, sb, val));
+    const R cn = cm * ct - sm * st;
+    sm = sm * ct + cm * st;
+    cm = cn;
+  }
+  return val;
+}
+
+// Polar coordinates, in the frame of a group centred at g (unit) with radius Rg, of
+// the point g + (dx, dy, dz): rho = geodesic distance / Rg, and the angle's cos/sin.
+__device__ __forceinline__ void group_polar(double dx, double dy, double dz, const double* g, double Rg,
+                                            double* rho, double* ct, double* st) {
+  double f1[3], f2[3];
+  patch_frame(g[0], g[1], g[2], f1, f2);
+  const double u1 = dx * f1[0] + dy * f1[1] + dz * f1[2];
+  const double u2 = dx * f2[0] + dy * f2[1] + dz * f2[2];
+  const double u3 = dx * g[0] + dy * g[1] + dz * g[2];
+  const double sr = sqrt(u1 * u1 + u2 * u2);
+  *rho = atan2(sr, 1.0 + u3) / Rg;
+  *ct = sr > 0.0 ? u1 / sr : 1.0;
+  *st = sr > 0.0 ? u2 / sr : 0.0;
+}
+
+// L2P: z_i(k) += expansion of every listed grid group of patch i at node k.
 template <typename R>
 __global__ void __launch_bounds__(512) l2p_kernel(int Kstar, const int64_t* __restrict__ pg_off,
                                                   const int* __restrict__ pg, const double* __restrict__ gcen,
@@ -315,66 +367,47 @@ __global__ void __launch_bounds__(512) l2p_kernel(int Kstar, const int64_t* __re
   for (int64_t s = pg_off[i]; s < pg_off[i + 1]; ++s) {
     const int g = pg[s];
     const int sh = gshape[g];
-    const int nr = shape_nr[sh], nth = shape_nth[sh], q = nr * nth, mh = nth / 2;
+    const int nr = shape_nr[sh], nth = shape_nth[sh], q = nr * nth;
     const int64_t off = goff[g];
     __syncthreads();
     for (int t = threadIdx.x; t < q; t += blockDim.x) C[t] = (R)coef[off + t];
     __syncthreads();
     if (k >= Kstar) continue;
-    const double gx = gcen[3 * g], gy = gcen[3 * g + 1], gz = gcen[3 * g + 2];
-    double f1[3], f2[3];
-    patch_frame(gx, gy, gz, f1, f2);
-    // offset of the node from the group centre, in the group's frame
-    const R dx = (R)(cx - gx) + (R)zo[0], dy = (R)(cy - gy) + (R)zo[1], dz = (R)(cz - gz) + (R)zo[2];
-    const R u1 = dx * (R)f1[0] + dy * (R)f1[1] + dz * (R)f1[2];
-    const R u2 = dx * (R)f2[0] + dy * (R)f2[1] + dz * (R)f2[2];
-    const R u3 = dx * (R)gx + dy * (R)gy + dz * (R)gz;
-    const R sr = sqrt(u1 * u1 + u2 * u2);
-    const R r = atan2(sr, (R)1 + u3);
-    const R rho = r / (R)gR[g];
-    R ct, st;
-    if (sr > (R)0) {
-      ct = u1 / sr;
-      st = u2 / sr;
-    } else {
-      ct = (R)1;
-      st = (R)0;
-    }
-    // Clenshaw in y = T_2(rho) over the even (T_2j) and odd (T_2j+1) series
-    const R y = fma((R)2 * rho, rho, (R)-1);
-    const R y2 = y + y;
-    R cm = 1, sm = 0;  // cos(m th), sin(m th)
-    R val = 0;
-    for (int m = 0; m < mh; ++m) {
-      const R* A = C + m * nr;
-      const R* B = C + mh * nr + m * nr;
-      R ba1 = 0, ba2 = 0, bb1 = 0, bb2 = 0;
-      for (int j = nr - 1; j >= 0; --j) {
-        const R ta = fma(y2, ba1, A[j] - ba2);
-        const R tb = fma(y2, bb1, B[j] - bb2);
-        ba2 = ba1;
-        ba1 = ta;
-        bb2 = bb1;
-        bb1 = tb;
-      }
-      // sum c_j phi_j = phi_0 (b_0 - 2y b_1) + phi_1 b_1, (phi_0, phi_1) = (1, y) or (rho, rho(2y - 1))
-      R sa, sb;
-      if ((m & 1) == 0) {
-        sa = fma(-y, ba2, ba1);  // phi_0 = 1, phi_1 = y: sum = b0 - y b1
-        sb = fma(-y, bb2, bb1);
-      } else {
-        // phi_0 = rho, phi_1 = T_3(rho) = rho (2y - 1): sum = rho (b0 - b1)
-        sa = rho * (ba1 - ba2);
-        sb = rho * (bb1 - bb2);
-      }
-      val = fma(cm, sa, fma(sm, sb, val));
-      const R cn = cm * ct - sm * st;
-      sm = sm * ct + cm * st;
-      cm = cn;
-    }
-    acc += (double)val;
+    const double* gc = gcen + 3 * g;
+    double rho, ct, st;
+    group_polar((cx - gc[0]) + zo[0], (cy - gc[1]) + zo[1], (cz - gc[2]) + zo[2], gc, gR[g], &rho, &ct, &st);
+    acc += (double)eval_expansion<R>(C, nr, nth / 2, (R)rho, (R)ct, (R)st);
   }
   if (k < Kstar) z[i * Kstar + k] += acc;
+}
+
+// Downward pass: grid values of each linked child group += the parent group's
+// expansion at the child's grid points (one block per link; a child has one link).
+template <typename R>
+__global__ void __launch_bounds__(256) l2l_kernel(int l0, const int* __restrict__ l2l_child,
+                                                  const int* __restrict__ l2l_parent, const double* __restrict__ gcen,
+                                                  const double* __restrict__ gR, const int* __restrict__ gshape,
+                                                  const int64_t* __restrict__ goff, const int* __restrict__ shape_nr,
+                                                  const int* __restrict__ shape_nth, const double* __restrict__ coef,
+                                                  const double* __restrict__ gpos, double* __restrict__ grid) {
+  extern __shared__ unsigned char ll_smem[];
+  R* C = reinterpret_cast<R*>(ll_smem);
+  const int ch = l2l_child[l0 + blockIdx.x], pa = l2l_parent[l0 + blockIdx.x];
+  const int shp = gshape[pa], shc = gshape[ch];
+  const int nrp = shape_nr[shp], nthp = shape_nth[shp], qp = nrp * nthp;
+  const int qc = shape_nr[shc] * shape_nth[shc];
+  const int64_t offp = goff[pa], offc = goff[ch];
+  for (int t = threadIdx.x; t < qp; t += blockDim.x) C[t] = (R)coef[offp + t];
+  __syncthreads();
+  const double* gp = gcen + 3 * pa;
+  const double* gq = gcen + 3 * ch;
+  const double Dx = gq[0] - gp[0], Dy = gq[1] - gp[1], Dz = gq[2] - gp[2];
+  for (int a = threadIdx.x; a < qc; a += blockDim.x) {
+    const double* o = gpos + 3 * (offc + a);
+    double rho, ct, st;
+    group_polar(Dx + o[0], Dy + o[1], Dz + o[2], gp, gR[pa], &rho, &ct, &st);
+    grid[offc + a] += (double)eval_expansion<R>(C, nrp, nthp / 2, (R)rho, (R)ct, (R)st);
+  }
 }
 
 // ---- float-float variants (FP64-accurate on the FP32 pipes) -----------------------
@@ -522,8 +555,41 @@ __global__ void __launch_bounds__(DT_THREADS) direct_list_df_kernel(
     if (kk[t] < Kstar) z[i * Kstar + kk[t]] = acc[t];
 }
 
+// Float-float expansion value (same recurrences as eval_expansion).
+__device__ __forceinline__ f2 eval_expansion_f2(const float2* C, int nr, int mh, f2 rho, f2 ct, f2 st) {
+  const f2 y = f2_add(f2_mul(f2{2.0f * rho.hi, 2.0f * rho.lo}, rho), f2{-1.0f, 0.0f});
+  const f2 y2 = f2{2.0f * y.hi, 2.0f * y.lo};
+  f2 cm = {1.0f, 0.0f}, sm = {0.0f, 0.0f}, val = {0.0f, 0.0f};
+  for (int m = 0; m < mh; ++m) {
+    const float2* A = C + m * nr;
+    const float2* B = C + mh * nr + m * nr;
+    f2 ba1 = {0.f, 0.f}, ba2 = {0.f, 0.f}, bb1 = {0.f, 0.f}, bb2 = {0.f, 0.f};
+    for (int j = nr - 1; j >= 0; --j) {
+      const f2 ta = f2_add(f2_mul(y2, ba1), f2_sub(f2{A[j].x, A[j].y}, ba2));
+      const f2 tb = f2_add(f2_mul(y2, bb1), f2_sub(f2{B[j].x, B[j].y}, bb2));
+      ba2 = ba1;
+      ba1 = ta;
+      bb2 = bb1;
+      bb1 = tb;
+    }
+    f2 sa, sb;
+    if ((m & 1) == 0) {
+      sa = f2_sub(ba1, f2_mul(y, ba2));
+      sb = f2_sub(bb1, f2_mul(y, bb2));
+    } else {
+      sa = f2_mul(rho, f2_sub(ba1, ba2));
+      sb = f2_mul(rho, f2_sub(bb1, bb2));
+    }
+    val = f2_add(val, f2_add(f2_mul(cm, sa), f2_mul(sm, sb)));
+    const f2 cn = f2_sub(f2_mul(cm, ct), f2_mul(sm, st));
+    sm = f2_add(f2_mul(sm, ct), f2_mul(cm, st));
+    cm = cn;
+  }
+  return val;
+}
+
 // L2P in float-float: node position in the group's polar coordinates from FP64,
-// coefficients as (hi, lo), Clenshaw and the angle recurrence in float-float.
+// coefficients as (hi, lo).
 __global__ void __launch_bounds__(512) l2p_df_kernel(int Kstar, const int64_t* __restrict__ pg_off,
                                                      const int* __restrict__ pg, const double* __restrict__ gcen,
                                                      const double* __restrict__ gR, const int* __restrict__ gshape,
@@ -542,7 +608,7 @@ __global__ void __launch_bounds__(512) l2p_df_kernel(int Kstar, const int64_t* _
   for (int64_t s = pg_off[i]; s < pg_off[i + 1]; ++s) {
     const int g = pg[s];
     const int sh = gshape[g];
-    const int nr = shape_nr[sh], nth = shape_nth[sh], q = nr * nth, mh = nth / 2;
+    const int nr = shape_nr[sh], nth = shape_nth[sh], q = nr * nth;
     const int64_t off = goff[g];
     __syncthreads();
     for (int t = threadIdx.x; t < q; t += blockDim.x) {
@@ -551,48 +617,42 @@ __global__ void __launch_bounds__(512) l2p_df_kernel(int Kstar, const int64_t* _
     }
     __syncthreads();
     if (k >= Kstar) continue;
-    const double gx = gcen[3 * g], gy = gcen[3 * g + 1], gz = gcen[3 * g + 2];
-    double f1[3], f2v[3];
-    patch_frame(gx, gy, gz, f1, f2v);
-    const double dx = (cx - gx) + zo[0], dy = (cy - gy) + zo[1], dz = (cz - gz) + zo[2];
-    const double u1 = dx * f1[0] + dy * f1[1] + dz * f1[2];
-    const double u2 = dx * f2v[0] + dy * f2v[1] + dz * f2v[2];
-    const double u3 = dx * gx + dy * gy + dz * gz;
-    const double sr = sqrt(u1 * u1 + u2 * u2);
-    const double rr = atan2(sr, 1.0 + u3) / gR[g];
-    const f2 rho = f2_from_double(rr);
-    const f2 ct = f2_from_double(sr > 0.0 ? u1 / sr : 1.0), st = f2_from_double(sr > 0.0 ? u2 / sr : 0.0);
-    const f2 y = f2_add(f2_mul(f2{2.0f * rho.hi, 2.0f * rho.lo}, rho), f2{-1.0f, 0.0f});
-    const f2 y2 = f2{2.0f * y.hi, 2.0f * y.lo};
-    f2 cm = {1.0f, 0.0f}, sm = {0.0f, 0.0f}, val = {0.0f, 0.0f};
-    for (int m = 0; m < mh; ++m) {
-      const float2* A = lpd_smem + m * nr;
-      const float2* B = lpd_smem + mh * nr + m * nr;
-      f2 ba1 = {0.f, 0.f}, ba2 = {0.f, 0.f}, bb1 = {0.f, 0.f}, bb2 = {0.f, 0.f};
-      for (int j = nr - 1; j >= 0; --j) {
-        const f2 ta = f2_add(f2_mul(y2, ba1), f2_sub(f2{A[j].x, A[j].y}, ba2));
-        const f2 tb = f2_add(f2_mul(y2, bb1), f2_sub(f2{B[j].x, B[j].y}, bb2));
-        ba2 = ba1;
-        ba1 = ta;
-        bb2 = bb1;
-        bb1 = tb;
-      }
-      f2 sa, sb;
-      if ((m & 1) == 0) {
-        sa = f2_sub(ba1, f2_mul(y, ba2));
-        sb = f2_sub(bb1, f2_mul(y, bb2));
-      } else {
-        sa = f2_mul(rho, f2_sub(ba1, ba2));
-        sb = f2_mul(rho, f2_sub(bb1, bb2));
-      }
-      val = f2_add(val, f2_add(f2_mul(cm, sa), f2_mul(sm, sb)));
-      const f2 cn = f2_sub(f2_mul(cm, ct), f2_mul(sm, st));
-      sm = f2_add(f2_mul(sm, ct), f2_mul(cm, st));
-      cm = cn;
-    }
-    acc += f2_to_double(val);
+    const double* gc = gcen + 3 * g;
+    double rho, ct, st;
+    group_polar((cx - gc[0]) + zo[0], (cy - gc[1]) + zo[1], (cz - gc[2]) + zo[2], gc, gR[g], &rho, &ct, &st);
+    acc += f2_to_double(eval_expansion_f2(lpd_smem, nr, nth / 2, f2_from_double(rho), f2_from_double(ct),
+                                          f2_from_double(st)));
   }
   if (k < Kstar) z[i * Kstar + k] += acc;
+}
+
+__global__ void __launch_bounds__(256) l2l_df_kernel(int l0, const int* __restrict__ l2l_child,
+                                                     const int* __restrict__ l2l_parent, const double* __restrict__ gcen,
+                                                     const double* __restrict__ gR, const int* __restrict__ gshape,
+                                                     const int64_t* __restrict__ goff, const int* __restrict__ shape_nr,
+                                                     const int* __restrict__ shape_nth, const double* __restrict__ coef,
+                                                     const double* __restrict__ gpos, double* __restrict__ grid) {
+  extern __shared__ float2 lld_smem[];
+  const int ch = l2l_child[l0 + blockIdx.x], pa = l2l_parent[l0 + blockIdx.x];
+  const int shp = gshape[pa], shc = gshape[ch];
+  const int nrp = shape_nr[shp], nthp = shape_nth[shp], qp = nrp * nthp;
+  const int qc = shape_nr[shc] * shape_nth[shc];
+  const int64_t offp = goff[pa], offc = goff[ch];
+  for (int t = threadIdx.x; t < qp; t += blockDim.x) {
+    const f2 v = f2_from_double(coef[offp + t]);
+    lld_smem[t] = make_float2(v.hi, v.lo);
+  }
+  __syncthreads();
+  const double* gp = gcen + 3 * pa;
+  const double* gq = gcen + 3 * ch;
+  const double Dx = gq[0] - gp[0], Dy = gq[1] - gp[1], Dz = gq[2] - gp[2];
+  for (int a = threadIdx.x; a < qc; a += blockDim.x) {
+    const double* o = gpos + 3 * (offc + a);
+    double rho, ct, st;
+    group_polar(Dx + o[0], Dy + o[1], Dz + o[2], gp, gR[pa], &rho, &ct, &st);
+    grid[offc + a] += f2_to_double(eval_expansion_f2(lld_smem, nrp, nthp / 2, f2_from_double(rho),
+                                                     f2_from_double(ct), f2_from_double(st)));
+  }
 }
 
 }  // namespace
@@ -666,6 +726,10 @@ void tree_upload(const TreeHost& t, const Precomputed& pc, TreeDevice& d) {
   chk(up(&d.pd, t.pd));
   chk(up(&d.pdk, t.pdk));
   chk(up(&d.gpos64, gp64));
+  chk(up(&d.l2l_child, t.l2l_child));
+  chk(up(&d.l2l_parent, t.l2l_parent));
+  d.gl_off = t.gl_off;
+  d.l2l_off = t.l2l_off;
   chk(up(&d.gpos32, gp32));
   chk(cudaMalloc(&d.grid, std::max<int64_t>(1, d.ngrid) * sizeof(double)));
   chk(cudaMalloc(&d.coef, std::max<int64_t>(1, d.ngrid) * sizeof(double)));
@@ -689,6 +753,10 @@ void tree_free(TreeDevice& d) {
   fr(d.pd);
   fr(d.pdk);
   fr(d.gpos64);
+  fr(d.l2l_child);
+  fr(d.l2l_parent);
+  d.gl_off.clear();
+  d.l2l_off.clear();
   fr(d.gpos32);
   fr(d.grid);
   fr(d.coef);
@@ -700,6 +768,41 @@ template <typename K>
 static cudaError_t allow_smem(K kernel, size_t bytes) {
   if (bytes <= 48 * 1024) return cudaSuccess;
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// Top-down over levels: coefficients of the level's grid groups (their grids now hold
+// their own P2L sums plus everything passed down), then the grid-to-grid transfer into
+// the nearest grid descendants whose parent is at this level.
+template <typename R>
+static cudaError_t downward(const TreeDevice& t, cudaStream_t s) {
+  cudaError_t e;
+  using CR = typename std::conditional<std::is_same<R, f2>::value, double, R>::type;
+  const size_t csm = (size_t)t.max_q * sizeof(double) + (size_t)t.max_nth * t.max_nr * sizeof(double);
+  if ((e = allow_smem(coef_kernel<CR>, csm)) != cudaSuccess) return e;
+  const int nl = (int)t.gl_off.size() - 1;
+  for (int l = 0; l < nl; ++l) {
+    const int g0 = t.gl_off[l], ng = t.gl_off[l + 1] - g0;
+    if (ng > 0) {
+      coef_kernel<CR><<<ng, 256, csm, s>>>(g0, t.gshape, t.goff, t.shape_nr, t.shape_nth, t.grid, t.coef);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    const int l0 = t.l2l_off[l], nlk = t.l2l_off[l + 1] - l0;
+    if (nlk > 0) {
+      if constexpr (std::is_same<R, f2>::value) {
+        const size_t sm = (size_t)t.max_q * sizeof(float2);
+        if ((e = allow_smem(l2l_df_kernel, sm)) != cudaSuccess) return e;
+        l2l_df_kernel<<<nlk, 256, sm, s>>>(l0, t.l2l_child, t.l2l_parent, t.gcen, t.gR, t.gshape, t.goff, t.shape_nr,
+                                           t.shape_nth, t.coef, t.gpos64, t.grid);
+      } else {
+        const size_t sm = (size_t)t.max_q * sizeof(R);
+        if ((e = allow_smem(l2l_kernel<R>, sm)) != cudaSuccess) return e;
+        l2l_kernel<R><<<nlk, 256, sm, s>>>(l0, t.l2l_child, t.l2l_parent, t.gcen, t.gR, t.gshape, t.goff,
+                                           t.shape_nr, t.shape_nth, t.coef, t.gpos64, t.grid);
+      }
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
 }
 
 template <typename R, int MODE>
@@ -721,10 +824,7 @@ static cudaError_t tree_field_impl(const DeviceData& dd, const TreeDevice& t, cu
                                                              t.grid);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], s);
-    const size_t csm = (size_t)t.max_q * sizeof(double) + (size_t)t.max_nth * t.max_nr * sizeof(double);
-    if ((e = allow_smem(coef_kernel<R>, csm)) != cudaSuccess) return e;
-    coef_kernel<R><<<t.ngroups, 256, csm, s>>>(t.gshape, t.goff, t.shape_nr, t.shape_nth, t.grid, t.coef);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = downward<R>(t, s)) != cudaSuccess) return e;
   } else if (ev) {
     cudaEventRecord(ev[1], s);
   }
@@ -764,10 +864,7 @@ static cudaError_t tree_field_df(const DeviceData& dd, const TreeDevice& t, cuda
                                                            dd.rho64, dd.logtab, t.grid);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], s);
-    const size_t csm = (size_t)t.max_q * sizeof(double) + (size_t)t.max_nth * t.max_nr * sizeof(double);
-    if ((e = allow_smem(coef_kernel<double>, csm)) != cudaSuccess) return e;
-    coef_kernel<double><<<t.ngroups, 256, csm, s>>>(t.gshape, t.goff, t.shape_nr, t.shape_nth, t.grid, t.coef);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = downward<f2>(t, s)) != cudaSuccess) return e;
   } else if (ev) {
     cudaEventRecord(ev[1], s);
   }

@@ -46,6 +46,11 @@ struct TreeHost {
   std::vector<int64_t> pd_off;
   std::vector<int> pd;
   std::vector<int> pdk;          // representation per direct entry
+  // downward pass (grid-to-grid interpolation into the nearest grid descendants)
+  std::vector<int> gl_off;       // levels+1: grid groups of level l are [gl_off[l], gl_off[l+1])
+  std::vector<int> l2l_child, l2l_parent;  // links, grouped by the parent's level
+  std::vector<int> l2l_off;      // levels+1
+  int64_t l2l_evals = 0;         // child grid points x parent grid size
   // statistics
   int64_t total_grid_points = 0;
   int64_t pairs_per_matvec = 0;  // kernel evaluations (P2L + direct)
@@ -77,6 +82,9 @@ struct TreeDevice {
   int* pdk = nullptr;
   double* gpos64 = nullptr;      // 3*ngrid grid-point offsets from the group centre
   float* gpos32 = nullptr;
+  int* l2l_child = nullptr;
+  int* l2l_parent = nullptr;
+  std::vector<int> gl_off, l2l_off;  // host copies of the per-level ranges
   double* grid = nullptr;        // ngrid values (FP64 accumulation for both precisions)
   double* coef = nullptr;        // ngrid coefficients
   int max_q = 0, max_nr = 0, max_nth = 0;

@@ -255,10 +255,10 @@ class Context:
         return tuple(arrs)
 
     def tree_stats(self) -> dict:
-        out = (ctypes.c_int64 * 9)()
-        self._check(load().ncs_tree_stats(self.h, out, 9))
+        out = (ctypes.c_int64 * 11)()
+        self._check(load().ncs_tree_stats(self.h, out, 11))
         keys = ["levels", "grid_groups", "grid_points", "p2l_items", "p2l_pairs", "direct_pairs", "l2p_evals",
-                "direct_patch_pairs", "shapes"]
+                "direct_patch_pairs", "shapes", "l2l_links", "l2l_evals"]
         return dict(zip(keys, [int(v) for v in out]))
 
     def set_method(self, method):
