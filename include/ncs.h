@@ -247,6 +247,21 @@ int ncs_eval(ncs_ctx* ctx, int64_t M, const double* targets, const double* fhat,
 int ncs_block_dots(int64_t n, int k, const double* V, int64_t ld, const double* w, double* out, void* stream);
 
 /*
+ * ncs_block_dots without any allocation, for callers that cannot call cudaMalloc (a
+ * host application that manages the device memory itself, a loop that must not block
+ * on the allocator, work recorded into a stream capture). The paper has no
+ * counterpart: this is a property of the library, not of the method. The partial sums
+ * live in a fixed device array inside the library (room for k <= 1024 vectors, 512 KiB,
+ * held by every GPU that loads the library until the process exits); the first call on
+ * a device looks its address up with that device current, so make that first call
+ * before any stream capture. Asynchronous on `stream`; calls that overlap on the GPU
+ * share the array and race, so serialise them. Nothing is allocated or freed.
+ * Errors: NCS_E_INPUT (k > 1024, bad sizes or NULL), NCS_E_CUDA.
+ */
+int ncs_block_dots_noalloc(int64_t n, int k, const double* V, int64_t ld, const double* w, double* out,
+                           void* stream);
+
+/*
  * The library's tensor-core GEMM on its own: D = A B^T with A (rows x kdim), B
  * (cols x kdim) and D (rows x cols), all row-major FP32 device arrays, computed with
  * tcgen05 kind::tf32 MMAs on hi/lo TF32 splits (3 products, ~FP32 accuracy) - the

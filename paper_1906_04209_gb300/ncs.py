@@ -29,7 +29,7 @@ EXPORTS = ["ncs_default_params", "ncs_create", "ncs_create_from_operator", "ncs_
            "ncs_get_operator", "ncs_get_onepatch", "ncs_set_patches", "ncs_set_method", "ncs_matvec",
            "ncs_matvec_dev", "ncs_field_dev", "ncs_solve", "ncs_eval", "ncs_last_error", "ncs_destroy",
            "ncs_tree_pairs", "ncs_tree_stats", "ncs_profile_matvec", "ncs_create_from_operators", "ncs_get_reps",
-           "ncs_tc_gemm_f32", "ncs_batch_solve", "ncs_block_dots"]
+           "ncs_tc_gemm_f32", "ncs_batch_solve", "ncs_block_dots", "ncs_block_dots_noalloc"]
 
 
 class ncs_params(ctypes.Structure):
@@ -91,6 +91,7 @@ def load(path: str = LIB_PATH):
                                     ctypes.POINTER(ncs_params), ctypes.c_int, D, D, ctypes.POINTER(ctypes.c_int), D,
                                     ctypes.POINTER(ctypes.c_int), D]
     lib.ncs_block_dots.argtypes = [ctypes.c_int64, ctypes.c_int, VP, ctypes.c_int64, VP, VP, VP]
+    lib.ncs_block_dots_noalloc.argtypes = [ctypes.c_int64, ctypes.c_int, VP, ctypes.c_int64, VP, VP, VP]
     lib.ncs_destroy.argtypes = [VP]
     lib.ncs_destroy.restype = None
     for name in EXPORTS:
@@ -143,6 +144,13 @@ def block_dots(n, k, V_ptr, ld, w_ptr, out_ptr, stream=0):
     rc = load().ncs_block_dots(n, k, VP(V_ptr), ld, VP(w_ptr), VP(out_ptr), VP(stream))
     if rc != NCS_OK:
         raise NcsError(rc, "ncs_block_dots failed")
+
+
+def block_dots_noalloc(n, k, V_ptr, ld, w_ptr, out_ptr, stream=0):
+    """ncs_block_dots without allocating (fixed scratch, k <= 1024); asynchronous."""
+    rc = load().ncs_block_dots_noalloc(n, k, VP(V_ptr), ld, VP(w_ptr), VP(out_ptr), VP(stream))
+    if rc != NCS_OK:
+        raise NcsError(rc, "ncs_block_dots_noalloc failed")
 
 
 def default_params(**kw) -> ncs_params:
