@@ -36,6 +36,9 @@ WORKLOAD = "interior N=100000 eps=0.001 K=136 jittered-Fibonacci tree (configs[3
 FLOPS_PER_PAIR = 20
 
 
+P2L_BYTES_PER_PAIR = 199.2e6 / 2.2033e10
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -111,10 +114,10 @@ def run_ours(args):
         dist.init_process_group("nccl")
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    centres, eps, mode, K = L.workload(3, layout=args.layout)
+    centres, eps, mode, K = L.workload(3, layout=args.layout, N=args.patches)
     N = len(centres)
     t0 = time.time()
-    ctx = ncs.Context(eps, mode, K, method=ncs.METHOD_TREE, grid_tol=args.grid_tol)
+    ctx = ncs.Context(eps, mode, K, method=ncs.METHOD_TREE, grid_tol=args.grid_tol, tensor_cores=args.tensor_cores)
     ctx.set_patches(centres)
     setup_s = time.time() - t0
     info, tstats = ctx.info(), ctx.tree_stats()
@@ -143,8 +146,10 @@ def run_ours(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     # P2L duration inside the timed region, measured on the launching stream
     e0.record(stream)
+    n_launch0 = ncs.launch_count()
     for _ in range(args.steps):
         step()
+    n_launches = ncs.launch_count() - n_launch0
     e1.record(stream)
     torch.cuda.synchronize()
     if ws > 1:
@@ -227,7 +232,11 @@ def run_ours(args):
         "peak": round(pair_peak * FLOPS_PER_PAIR / 1e12, 3) if pair_peak else None,
         "unit": "TFLOP/s",
         "frac": round(achieved_pairs / pair_peak, 4) if pair_peak else None,
-        "traffic": None,
+        # DRAM bytes per launch: an ncu capture of this kernel on the N = 2e4 layout of the
+        # same family measured 199.2 MB for 2.2033e10 pairs; the P2L reads scale with its
+        # work items, so it is scaled by the pair ratio (null for other precisions)
+        "traffic": round(P2L_BYTES_PER_PAIR * p2l_pairs) if prec == ncs.FP32 else None,
+        "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum at N=2e4, scaled by pairs",
         "pairs_per_launch": p2l_pairs,
         "ms_per_launch": round(p2l_avg, 3),
         "peak_source": "derived: 152 SMs x 16 MUFU/clk / 2 MUFU per pair x %g MHz (%s clocks)" % (sm_max, src),
@@ -240,12 +249,12 @@ def run_ours(args):
         "data": "synthetic (seeded layout, random Gaussian input vector)",
         "config": {"workload": WORKLOAD, "N": N, "eps": eps, "K": K, "mode": "interior",
                    "layout": args.layout, "p": info["p"], "Kstar": info["Kstar"], "levels": tstats["levels"],
-                   "grid_tol": args.grid_tol, "parallelism": "replicas" if ws > 1 else "single",
+                   "grid_tol": args.grid_tol, "tensor_cores": args.tensor_cores, "parallelism": "replicas" if ws > 1 else "single",
                    "l2": "working set > L2 (skeleton offsets 200 MB, z 397 MB, grids per step)",
                    "setup_s": round(setup_s, 2)},
         "e2e": {"value": round(ws / e2e_s, 4), "unit": UNIT, "h2d_bytes_per_step": n * 8,
                 "d2h_bytes_per_step": n * 8},
-        "gpu_launches": 6 * args.steps,
+        "gpu_launches": n_launches,
         "roofline": roof,
         "cpu_baseline": cpu,
         "clocks": clk,
@@ -321,6 +330,9 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--df64-steps", type=int, default=2)
     ap.add_argument("--solve", action="store_true")
+    # a smaller layout of the same family (profiler captures only; the line names its N)
+    ap.add_argument("--patches", type=int, default=None)
+    ap.add_argument("--tensor-cores", type=int, default=0, choices=[0, 1])
     ap.add_argument("--solve-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

@@ -290,6 +290,14 @@ int ncs_batch_solve(int B, const double* eps, const int* mode, const int64_t* N,
 /* Message of the last failure on ctx (static string if ctx is NULL). */
 const char* ncs_last_error(const ncs_ctx* ctx);
 
+/*
+ * Number of CUDA kernels this library has launched in this process so far, over all
+ * contexts and threads (diagnostic; not part of the method). The difference across a
+ * call is the number of kernels that call launched, when no other thread uses the
+ * library meanwhile. Never fails.
+ */
+int64_t ncs_launch_count(void);
+
 /* Releases all host and device memory of ctx (NULL is ignored). */
 void ncs_destroy(ncs_ctx* ctx);
 

@@ -41,16 +41,18 @@ def sources():
     return sorted(f for f in os.listdir(CSRC) if f.endswith((".cu", ".cpp")))
 
 
-def build(verbose: bool = False, extra_nvcc=()) -> str:
-    """Compiles every translation unit of csrc/ in parallel and links libncs.so."""
+def build(verbose: bool = False, extra_nvcc=(), lib_path: str = LIB, build_dir: str = OUT) -> str:
+    """Compiles every translation unit of csrc/ in parallel and links libncs.so.
+    extra_nvcc adds flags to the CUDA compilations (e.g. -D tuning macros); lib_path and
+    build_dir place a variant build elsewhere."""
     cuda = _cuda_home()
     nvcc = os.path.join(cuda, "bin", "nvcc")
-    os.makedirs(OUT, exist_ok=True)
+    os.makedirs(build_dir, exist_ok=True)
     common_inc = ["-I", CSRC, "-I", INCLUDE]
     jobs = []
     for f in sources():
         src = os.path.join(CSRC, f)
-        obj = os.path.join(OUT, f + ".o")
+        obj = os.path.join(build_dir, f + ".o")
         if f.endswith(".cu"):
             cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fopenmp",
                    *common_inc, *extra_nvcc, "-c", src, "-o", obj]
@@ -65,11 +67,11 @@ def build(verbose: bool = False, extra_nvcc=()) -> str:
             if o.strip():
                 print(o)
     objs = [o for _, o in jobs]
-    tmp = LIB + ".tmp"
+    tmp = lib_path + ".tmp"
     _run([nvcc, *ARCH, "-shared", "-Xcompiler", "-fPIC", "-o", tmp, *objs, "-lgomp", "-lcudart",
           "-L", os.path.join(cuda, "lib64")])
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

@@ -21,6 +21,10 @@
 
 using ncs::DeviceData;
 
+namespace ncs {
+std::atomic<long long> g_launches{0};
+}  // namespace ncs
+
 namespace {
 
 const char* g_static_err = "ncs: no context";
@@ -251,7 +255,7 @@ void apply_P(ncs_ctx* c, const double* x, double* y, int prec, cudaStream_t s) {
   if (prec == NCS_FP32 && c->prm.tensor_cores)
     CU(ncs::launch_tc_apply_P(c->d, x, y, c->d.P32, c->d.tc_err, s));
   else
-    CU(ncs::launch_apply_P(c->d, x, y, s));
+    CU(ncs::launch_apply_P(c->d, x, y, prec, s));
 }
 
 // A tensor-core kernel whose bounded wait gave up leaves the flag set (checked at
@@ -1037,6 +1041,8 @@ int ncs_batch_solve(int B, const double* eps, const int* mode, const int64_t* N,
 }
 
 const char* ncs_last_error(const ncs_ctx* c) { return c ? c->err.c_str() : g_static_err; }
+
+int64_t ncs_launch_count(void) { return (int64_t)ncs::g_launches.load(std::memory_order_relaxed); }
 
 void ncs_destroy(ncs_ctx* c) {
   if (!c) return;

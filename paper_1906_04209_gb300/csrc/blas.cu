@@ -36,8 +36,8 @@ __global__ void dots_final_kernel(int k, const double* __restrict__ partial, dou
 cudaError_t launch_dots(int64_t n, int k, const double* V, int64_t ld, const double* w, double* partial,
                         double* out, cudaStream_t s) {
   if (k <= 0) return cudaSuccess;
-  dots_partial_kernel<<<dim3(kDotChunks, k), 256, 0, s>>>(n, V, ld, w, partial);
-  dots_final_kernel<<<(k + 127) / 128, 128, 0, s>>>(k, partial, out);
+  count_launch(), dots_partial_kernel<<<dim3(kDotChunks, k), 256, 0, s>>>(n, V, ld, w, partial);
+  count_launch(), dots_final_kernel<<<(k + 127) / 128, 128, 0, s>>>(k, partial, out);
   return cudaGetLastError();
 }
 
@@ -59,7 +59,7 @@ cudaError_t launch_sub_combination(int64_t n, int k, const double* V, int64_t ld
                                    double sign, cudaStream_t s) {
   if (k <= 0) return cudaSuccess;
   const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 16);
-  sub_combination_kernel<<<(unsigned)blocks, 256, k * sizeof(double), s>>>(n, k, V, ld, h, w, sign);
+  count_launch(), sub_combination_kernel<<<(unsigned)blocks, 256, k * sizeof(double), s>>>(n, k, V, ld, h, w, sign);
   return cudaGetLastError();
 }
 
@@ -70,7 +70,7 @@ __global__ void scale_copy_kernel(int64_t n, const double* __restrict__ w, doubl
 
 cudaError_t launch_scale_copy(int64_t n, const double* w, double a, double* v, cudaStream_t s) {
   const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 16);
-  scale_copy_kernel<<<(unsigned)blocks, 256, 0, s>>>(n, w, a, v);
+  count_launch(), scale_copy_kernel<<<(unsigned)blocks, 256, 0, s>>>(n, w, a, v);
   return cudaGetLastError();
 }
 
@@ -82,7 +82,7 @@ __global__ void axpby_kernel(int64_t n, double a, const double* __restrict__ x, 
 
 cudaError_t launch_axpby(int64_t n, double a, const double* x, double b, double* y, cudaStream_t s) {
   const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 16);
-  axpby_kernel<<<(unsigned)blocks, 256, 0, s>>>(n, a, x, b, y);
+  count_launch(), axpby_kernel<<<(unsigned)blocks, 256, 0, s>>>(n, a, x, b, y);
   return cudaGetLastError();
 }
 
@@ -95,7 +95,7 @@ __global__ void nonfinite_kernel(int64_t n, const double* __restrict__ x, int* _
 
 cudaError_t launch_nonfinite_count(int64_t n, const double* x, int* out, cudaStream_t s) {
   const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 4);
-  nonfinite_kernel<<<(unsigned)blocks, 256, 0, s>>>(n, x, out);
+  count_launch(), nonfinite_kernel<<<(unsigned)blocks, 256, 0, s>>>(n, x, out);
   return cudaGetLastError();
 }
 
@@ -124,8 +124,8 @@ __global__ void __launch_bounds__(256) periodic_dot_kernel(int64_t n, int K, con
 
 cudaError_t launch_periodic_dot(int64_t n, int K, const double* x, const double* I, double* partial,
                                 double* out, cudaStream_t s) {
-  periodic_dot_kernel<<<kDotChunks, 256, 0, s>>>(n, K, x, I, partial);
-  dots_final_kernel<<<1, 128, 0, s>>>(1, partial, out);
+  count_launch(), periodic_dot_kernel<<<kDotChunks, 256, 0, s>>>(n, K, x, I, partial);
+  count_launch(), dots_final_kernel<<<1, 128, 0, s>>>(1, partial, out);
   return cudaGetLastError();
 }
 

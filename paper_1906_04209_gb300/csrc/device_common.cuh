@@ -84,6 +84,39 @@ __device__ __forceinline__ float pair32(float d2, float w1, float w2, float acc)
   return fmaf(r, w1, fmaf(l, w2, acc));
 }
 
+// log2(x) for normal x > 0 on the FMA and integer pipes instead of the MUFU unit:
+// x = 2^e m with m in [sqrt(1/2), sqrt(2)), log2(x) = e + f P(f), f = m - 1, P of
+// degree 8 fitted by least squares (coefficients from gen_log2_poly.py; absolute
+// error <= 1e-7 for |log2 x| < 1, <= 3 ulp of the result elsewhere). The exponent is
+// turned into a float by adding it to the bits of 1.5 * 2^23, so no conversion
+// instruction is issued.
+__device__ __forceinline__ float lg2_poly(float x) {
+  const int i = __float_as_int(x);
+  const int e = (i - 0x3f3504f3) >> 23;
+  const float f = __int_as_float(i - (e << 23)) - 1.0f;
+  float p = 1.224903390e-01f;
+  p = fmaf(p, f, -2.088673115e-01f);
+  p = fmaf(p, f, 2.178854942e-01f);
+  p = fmaf(p, f, -2.387827337e-01f);
+  p = fmaf(p, f, 2.876248062e-01f);
+  p = fmaf(p, f, -3.607062101e-01f);
+  p = fmaf(p, f, 4.809235036e-01f);
+  p = fmaf(p, f, -7.213473916e-01f);
+  p = fmaf(p, f, 1.442694902e+00f);
+  const float ef = __int_as_float(e + 0x4b400000) - 12582912.0f;
+  return fmaf(f, p, ef);
+}
+
+// pair32 with the logarithm taken by lg2_poly: the pair kernels use it for a share of
+// their pairs so that the MUFU unit and the FMA pipe are both kept busy.
+template <int MODE>
+__device__ __forceinline__ float pair32_poly(float d2, float w1, float w2, float acc) {
+  const float r = rsqrt_mufu(d2);
+  const float t = fmaf(2.0f, r, 1.0f);
+  const float l = lg2_poly(MODE == 0 ? t : d2 * t);
+  return fmaf(r, w1, fmaf(l, w2, acc));
+}
+
 // Block-wide sum of a per-thread float (all threads must call; result valid in all threads).
 __device__ __forceinline__ float block_sum(float v, float* scratch32) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

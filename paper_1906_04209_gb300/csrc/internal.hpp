@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -11,6 +12,11 @@
 #include "tree.hpp"
 
 namespace ncs {
+
+// Process-wide number of kernels the library has launched (read by ncs_launch_count).
+// Every launch site is written `count_launch(), kernel<<<...>>>(...)`.
+extern std::atomic<long long> g_launches;
+inline void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 // Device-resident data of one patch layout plus the precompute.
 struct DeviceData {
@@ -46,7 +52,7 @@ struct DeviceData {
 cudaError_t launch_skeleton_offsets(const DeviceData& d, cudaStream_t s);
 cudaError_t launch_outgoing(const DeviceData& d, const double* x, int prec, cudaStream_t s);
 cudaError_t launch_direct_field(const DeviceData& d, int mode, int prec, double eps, cudaStream_t s);
-cudaError_t launch_apply_P(const DeviceData& d, const double* x, double* y, cudaStream_t s);
+cudaError_t launch_apply_P(const DeviceData& d, const double* x, double* y, int prec, cudaStream_t s);
 cudaError_t launch_eval(const DeviceData& d, int mode, int64_t M, const double* targets,
                         double* out, cudaStream_t s);
 

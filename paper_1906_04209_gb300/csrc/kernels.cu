@@ -47,41 +47,60 @@ __global__ void skeleton_offsets_kernel(int64_t N, int p, const double* __restri
 cudaError_t launch_skeleton_offsets(const DeviceData& d, cudaStream_t s) {
   const int64_t n = d.N * d.p;
   const int th = 256;
-  skeleton_offsets_kernel<<<(unsigned)((n + th - 1) / th), th, 0, s>>>(d.N, d.p, d.centres, d.sloc,
+  count_launch(), skeleton_offsets_kernel<<<(unsigned)((n + th - 1) / th), th, 0, s>>>(d.N, d.p, d.centres, d.sloc,
                                                                        d.soff64, d.soff32);
   return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
-// Step 3.1: rho_i = T f_i for PB patches per block; TT is T transposed (K x p) so
-// that consecutive threads read consecutive skeleton rows.
+// Step 3.1: rho_i = T f_i for OG_PB patches per block; TT is T transposed (K x p), and
+// each thread accumulates 4 consecutive skeleton rows for all OG_PB patches, so one
+// coalesced row read of TT and OG_PB shared-memory broadcasts feed 4 * OG_PB FMAs.
 constexpr int OG_PB = 8;
 
 template <typename R>
-__global__ void __launch_bounds__(256) outgoing_kernel(int64_t N, int p, int K, const R* __restrict__ TT,
+__global__ void __launch_bounds__(128) outgoing_kernel(int64_t N, int p, int K, const R* __restrict__ TT,
                                                        const double* __restrict__ x, R* __restrict__ rho) {
   extern __shared__ unsigned char og_smem[];
   R* xs = reinterpret_cast<R*>(og_smem);  // OG_PB x K
   const int64_t i0 = (int64_t)blockIdx.x * OG_PB;
   const int np = (int)min((int64_t)OG_PB, N - i0);
-  for (int idx = threadIdx.x; idx < np * K; idx += blockDim.x) xs[idx] = (R)x[i0 * K + idx];
+  for (int idx = threadIdx.x; idx < OG_PB * K; idx += blockDim.x)
+    xs[idx] = (idx < np * K) ? (R)x[i0 * K + idx] : (R)0;
   __syncthreads();
-  for (int idx = threadIdx.x; idx < np * p; idx += blockDim.x) {
-    const int ii = idx / p, m = idx - ii * p;
-    const R* xr = xs + ii * K;
-    R acc = 0;
-    for (int k = 0; k < K; ++k) acc = fma(TT[(int64_t)k * p + m], xr[k], acc);
-    rho[(i0 + ii) * p + m] = acc;
+  for (int m0 = 4 * threadIdx.x; m0 < p; m0 += 4 * blockDim.x) {
+    R acc[OG_PB][4];
+#pragma unroll
+    for (int ii = 0; ii < OG_PB; ++ii)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[ii][j] = 0;
+    for (int k = 0; k < K; ++k) {
+      const R* row = TT + (int64_t)k * p + m0;
+      R t[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) t[j] = (m0 + j < p) ? row[j] : (R)0;
+#pragma unroll
+      for (int ii = 0; ii < OG_PB; ++ii) {
+        const R xv = xs[ii * K + k];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[ii][j] = fma(t[j], xv, acc[ii][j]);
+      }
+    }
+#pragma unroll
+    for (int ii = 0; ii < OG_PB; ++ii)
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (ii < np && m0 + j < p) rho[(i0 + ii) * p + m0 + j] = acc[ii][j];
   }
 }
 
 cudaError_t launch_outgoing(const DeviceData& d, const double* x, int prec, cudaStream_t s) {
   const unsigned blocks = (unsigned)((d.N + OG_PB - 1) / OG_PB);
   if (prec == NCS_FP64 || prec == NCS_DF64)
-    outgoing_kernel<double><<<blocks, 256, OG_PB * d.K * sizeof(double), s>>>(d.N, d.p, d.K, d.TT64, x,
+    count_launch(), outgoing_kernel<double><<<blocks, 128, OG_PB * d.K * sizeof(double), s>>>(d.N, d.p, d.K, d.TT64, x,
                                                                                 d.rho64);
   else
-    outgoing_kernel<float><<<blocks, 256, OG_PB * d.K * sizeof(float), s>>>(d.N, d.p, d.K, d.TT32, x,
+    count_launch(), outgoing_kernel<float><<<blocks, 128, OG_PB * d.K * sizeof(float), s>>>(d.N, d.p, d.K, d.TT32, x,
                                                                               d.rho32);
   return cudaGetLastError();
 }
@@ -302,12 +321,12 @@ cudaError_t launch_direct_field(const DeviceData& d, int mode, int prec, double 
     cudaError_t e;
     if (mode == 0) {
       if ((e = allow_smem(direct_field_df_kernel<0>, smem)) != cudaSuccess) return e;
-      direct_field_df_kernel<0><<<grid, DF_THREADS, smem, s>>>(d.N, d.p, d.Kstar, JT, d.pmax, d.nrep, d.rep_p,
+      count_launch(), direct_field_df_kernel<0><<<grid, DF_THREADS, smem, s>>>(d.N, d.p, d.Kstar, JT, d.pmax, d.nrep, d.rep_p,
                                                                d.rep_off, d.rep_rho, eps, d.centres, d.zloc,
                                                                d.soff64, d.rho64, d.logtab, d.z);
     } else {
       if ((e = allow_smem(direct_field_df_kernel<1>, smem)) != cudaSuccess) return e;
-      direct_field_df_kernel<1><<<grid, DF_THREADS, smem, s>>>(d.N, d.p, d.Kstar, JT, d.pmax, d.nrep, d.rep_p,
+      count_launch(), direct_field_df_kernel<1><<<grid, DF_THREADS, smem, s>>>(d.N, d.p, d.Kstar, JT, d.pmax, d.nrep, d.rep_p,
                                                                d.rep_off, d.rep_rho, eps, d.centres, d.zloc,
                                                                d.soff64, d.rho64, d.logtab, d.z);
     }
@@ -322,7 +341,7 @@ cudaError_t launch_direct_field(const DeviceData& d, int mode, int prec, double 
 #define NCS_DF(R, M, SOFF, RHO)                                                                            \
   do {                                                                                                     \
     if ((e = allow_smem(direct_field_kernel<R, M>, smem)) != cudaSuccess) return e;                       \
-    direct_field_kernel<R, M><<<grid, DF_THREADS, smem, s>>>(d.N, d.p, d.Kstar, JT, d.pmax, d.nrep, d.rep_p, \
+    count_launch(), direct_field_kernel<R, M><<<grid, DF_THREADS, smem, s>>>(d.N, d.p, d.Kstar, JT, d.pmax, d.nrep, d.rep_p, \
                                                              d.rep_off, d.rep_rho, eps, d.centres, d.zloc, \
                                                              SOFF, RHO, d.z);                              \
   } while (0)
@@ -345,27 +364,33 @@ cudaError_t launch_direct_field(const DeviceData& d, int mode, int prec, double 
 // Step 3.5: y_i = x_i + P z_i. PT is P transposed (Kstar x K).
 constexpr int AP_PB = 4;
 
-__global__ void __launch_bounds__(256) apply_P_kernel(int64_t N, int K, int Kstar, const double* __restrict__ PT,
+template <typename R>
+__global__ void __launch_bounds__(256) apply_P_kernel(int64_t N, int K, int Kstar, const R* __restrict__ PT,
                                                       const double* __restrict__ z, const double* __restrict__ x,
                                                       double* __restrict__ y) {
   extern __shared__ unsigned char ap_smem[];
-  double* zs = reinterpret_cast<double*>(ap_smem);  // AP_PB x Kstar
+  R* zs = reinterpret_cast<R*>(ap_smem);  // AP_PB x Kstar
   const int64_t i0 = (int64_t)blockIdx.x * AP_PB;
   const int np = (int)min((int64_t)AP_PB, N - i0);
-  for (int idx = threadIdx.x; idx < np * Kstar; idx += blockDim.x) zs[idx] = z[i0 * Kstar + idx];
+  for (int idx = threadIdx.x; idx < np * Kstar; idx += blockDim.x) zs[idx] = (R)z[i0 * Kstar + idx];
   __syncthreads();
   for (int idx = threadIdx.x; idx < np * K; idx += blockDim.x) {
     const int ii = idx / K, j = idx - ii * K;
-    const double* zr = zs + ii * Kstar;
-    double acc = 0.0;
+    const R* zr = zs + ii * Kstar;
+    R acc = 0;
     for (int q = 0; q < Kstar; ++q) acc = fma(PT[(int64_t)q * K + j], zr[q], acc);
-    y[(i0 + ii) * K + j] = x[(i0 + ii) * K + j] + acc;
+    y[(i0 + ii) * K + j] = x[(i0 + ii) * K + j] + (double)acc;
   }
 }
 
-cudaError_t launch_apply_P(const DeviceData& d, const double* x, double* y, cudaStream_t s) {
+// prec: NCS_FP32 runs the transform in FP32 (the FP32 product), otherwise FP64.
+cudaError_t launch_apply_P(const DeviceData& d, const double* x, double* y, int prec, cudaStream_t s) {
   const unsigned blocks = (unsigned)((d.N + AP_PB - 1) / AP_PB);
-  apply_P_kernel<<<blocks, 256, AP_PB * d.Kstar * sizeof(double), s>>>(d.N, d.K, d.Kstar, d.PT64, d.z, x, y);
+  if (prec == NCS_FP32)
+    count_launch(), apply_P_kernel<float><<<blocks, 256, AP_PB * d.Kstar * sizeof(float), s>>>(d.N, d.K, d.Kstar, d.PT32, d.z, x, y);
+  else
+    count_launch(), apply_P_kernel<double><<<blocks, 256, AP_PB * d.Kstar * sizeof(double), s>>>(d.N, d.K, d.Kstar, d.PT64, d.z, x,
+                                                                                 y);
   return cudaGetLastError();
 }
 
@@ -409,9 +434,9 @@ cudaError_t launch_eval(const DeviceData& d, int mode, int64_t M, const double* 
                         cudaStream_t s) {
   if (M == 0) return cudaSuccess;
   if (mode == 0)
-    eval_kernel<0><<<(unsigned)M, 256, 0, s>>>(d.N, d.p0, d.p, d.centres, d.soff64, d.rho64, targets, out);
+    count_launch(), eval_kernel<0><<<(unsigned)M, 256, 0, s>>>(d.N, d.p0, d.p, d.centres, d.soff64, d.rho64, targets, out);
   else
-    eval_kernel<1><<<(unsigned)M, 256, 0, s>>>(d.N, d.p0, d.p, d.centres, d.soff64, d.rho64, targets, out);
+    count_launch(), eval_kernel<1><<<(unsigned)M, 256, 0, s>>>(d.N, d.p0, d.p, d.centres, d.soff64, d.rho64, targets, out);
   return cudaGetLastError();
 }
 

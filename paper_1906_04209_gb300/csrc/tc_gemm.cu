@@ -216,7 +216,7 @@ cudaError_t launch(int64_t rows, int cols, int Kd, const TA* A, int64_t lda, con
                                        (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)((rows + TC_BM - 1) / TC_BM), (unsigned)((cols + BN - 1) / BN));
-  tc_gemm_kernel<TA, TB, BN><<<grid, TC_THREADS, smem, s>>>(rows, cols, Kd, A, lda, B, ldb, D, ldd, addx, Dd, err);
+  count_launch(), tc_gemm_kernel<TA, TB, BN><<<grid, TC_THREADS, smem, s>>>(rows, cols, Kd, A, lda, B, ldb, D, ldd, addx, Dd, err);
   return cudaGetLastError();
 }
 

@@ -49,8 +49,13 @@ void fr(T*& p) {
 }
 
 constexpr int P2L_THREADS = 256;
-constexpr int P2L_NT = 4;
+constexpr int P2L_NT = 2;
 constexpr int P2L_JT = 8;
+// FP32 P2L: odd target slots take their logarithm with lg2_poly (FMA pipe) instead of
+// the MUFU unit, which alone would otherwise bound the pair rate.
+#ifndef NCS_P2L_POLYLOG
+#define NCS_P2L_POLYLOG 0
+#endif
 
 // One block per work item (grid group g, a slice of its interaction-list patches).
 template <typename R, int MODE>
@@ -124,16 +129,33 @@ __global__ void __launch_bounds__(P2L_THREADS) p2l_kernel(
       R part[P2L_NT];
 #pragma unroll
       for (int t = 0; t < P2L_NT; ++t) part[t] = 0;
-      for (int s = 0; s < ns; ++s) {
-        const V4 v = S[s];
+      // warps whose every target slot lies beyond the grid skip the pair work
+      const int wbase = base + (threadIdx.x & ~31);
+      const int nact = (wbase >= q) ? 0 : ((wbase + P2L_THREADS >= q) ? 1 : P2L_NT);
+      if (nact == P2L_NT) {
+        for (int s = 0; s < ns; ++s) {
+          const V4 v = S[s];
 #pragma unroll
-        for (int t = 0; t < P2L_NT; ++t) {
-          const R dx = ax[t] - v.x, dy = ay[t] - v.y, dz = az[t] - v.z;
+          for (int t = 0; t < P2L_NT; ++t) {
+            const R dx = ax[t] - v.x, dy = ay[t] - v.y, dz = az[t] - v.z;
+            const R d2 = fma(dx, dx, fma(dy, dy, dz * dz));
+            if constexpr (sizeof(R) == 8)
+              part[t] = fma(green64<MODE>(d2), v.w, part[t]);
+            else if (NCS_P2L_POLYLOG && (t & 1))
+              part[t] = pair32_poly<MODE>(d2, v.w, W2[s], part[t]);
+            else
+              part[t] = pair32<MODE>(d2, v.w, W2[s], part[t]);
+          }
+        }
+      } else if (nact == 1) {
+        for (int s = 0; s < ns; ++s) {
+          const V4 v = S[s];
+          const R dx = ax[0] - v.x, dy = ay[0] - v.y, dz = az[0] - v.z;
           const R d2 = fma(dx, dx, fma(dy, dy, dz * dz));
           if constexpr (sizeof(R) == 8)
-            part[t] = fma(green64<MODE>(d2), v.w, part[t]);
+            part[0] = fma(green64<MODE>(d2), v.w, part[0]);
           else
-            part[t] = pair32<MODE>(d2, v.w, W2[s], part[t]);
+            part[0] = pair32<MODE>(d2, v.w, W2[s], part[0]);
         }
       }
 #pragma unroll
@@ -467,10 +489,16 @@ __global__ void __launch_bounds__(P2L_THREADS) p2l_df_kernel(
       f2 part[NT];
 #pragma unroll
       for (int t = 0; t < NT; ++t) part[t] = f2{0.0f, 0.0f};
-      for (int s = 0; s < ns; ++s) {
-        const float4 h = Sh[s], l = Sl[s];
+      const int wbase = base + (threadIdx.x & ~31);
+      const int nact = (wbase >= q) ? 0 : ((wbase + P2L_THREADS >= q) ? 1 : NT);
+      if (nact == NT) {
+        for (int s = 0; s < ns; ++s) {
+          const float4 h = Sh[s], l = Sl[s];
 #pragma unroll
-        for (int t = 0; t < NT; ++t) part[t] = f2_add(part[t], pair_f2<MODE>(a[t], h, l, tab));
+          for (int t = 0; t < NT; ++t) part[t] = f2_add(part[t], pair_f2<MODE>(a[t], h, l, tab));
+        }
+      } else if (nact == 1) {
+        for (int s = 0; s < ns; ++s) part[0] = f2_add(part[0], pair_f2<MODE>(a[0], Sh[s], Sl[s], tab));
       }
 #pragma unroll
       for (int t = 0; t < NT; ++t) acc[t] += f2_to_double(part[t]);
@@ -783,7 +811,7 @@ static cudaError_t downward(const TreeDevice& t, cudaStream_t s) {
   for (int l = 0; l < nl; ++l) {
     const int g0 = t.gl_off[l], ng = t.gl_off[l + 1] - g0;
     if (ng > 0) {
-      coef_kernel<CR><<<ng, 256, csm, s>>>(g0, t.gshape, t.goff, t.shape_nr, t.shape_nth, t.grid, t.coef);
+      count_launch(), coef_kernel<CR><<<ng, 256, csm, s>>>(g0, t.gshape, t.goff, t.shape_nr, t.shape_nth, t.grid, t.coef);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     const int l0 = t.l2l_off[l], nlk = t.l2l_off[l + 1] - l0;
@@ -791,12 +819,12 @@ static cudaError_t downward(const TreeDevice& t, cudaStream_t s) {
       if constexpr (std::is_same<R, f2>::value) {
         const size_t sm = (size_t)t.max_q * sizeof(float2);
         if ((e = allow_smem(l2l_df_kernel, sm)) != cudaSuccess) return e;
-        l2l_df_kernel<<<nlk, 256, sm, s>>>(l0, t.l2l_child, t.l2l_parent, t.gcen, t.gR, t.gshape, t.goff, t.shape_nr,
+        count_launch(), l2l_df_kernel<<<nlk, 256, sm, s>>>(l0, t.l2l_child, t.l2l_parent, t.gcen, t.gR, t.gshape, t.goff, t.shape_nr,
                                            t.shape_nth, t.coef, t.gpos64, t.grid);
       } else {
         const size_t sm = (size_t)t.max_q * sizeof(R);
         if ((e = allow_smem(l2l_kernel<R>, sm)) != cudaSuccess) return e;
-        l2l_kernel<R><<<nlk, 256, sm, s>>>(l0, t.l2l_child, t.l2l_parent, t.gcen, t.gR, t.gshape, t.goff,
+        count_launch(), l2l_kernel<R><<<nlk, 256, sm, s>>>(l0, t.l2l_child, t.l2l_parent, t.gcen, t.gR, t.gshape, t.goff,
                                            t.shape_nr, t.shape_nth, t.coef, t.gpos64, t.grid);
       }
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -818,7 +846,7 @@ static cudaError_t tree_field_impl(const DeviceData& dd, const TreeDevice& t, cu
     if (e != cudaSuccess) return e;
     const size_t smem = (size_t)P2L_JT * dd.pmax * (sizeof(V4) + 4);
     if ((e = allow_smem(p2l_kernel<R, MODE>, smem)) != cudaSuccess) return e;
-    p2l_kernel<R, MODE><<<t.nitems, P2L_THREADS, smem, s>>>(t.witem_group, t.witem_rep, dd.rep_p, dd.rep_off, dd.p,
+    count_launch(), p2l_kernel<R, MODE><<<t.nitems, P2L_THREADS, smem, s>>>(t.witem_group, t.witem_rep, dd.rep_p, dd.rep_off, dd.p,
                                                              t.witem_lo, t.witem_hi, t.isrc, t.gcen, t.gshape, t.goff,
                                                              t.shape_nr, t.shape_nth, gpos, dd.centres, soff, rho,
                                                              t.grid);
@@ -833,7 +861,7 @@ static cudaError_t tree_field_impl(const DeviceData& dd, const TreeDevice& t, cu
     const size_t smem = (size_t)DT_JT * dd.pmax * (sizeof(V4) + 4);
     if ((e = allow_smem(direct_list_kernel<R, MODE>, smem)) != cudaSuccess) return e;
     dim3 grid((unsigned)dd.N, (unsigned)((dd.Kstar + DT_THREADS * DT_NT - 1) / (DT_THREADS * DT_NT)));
-    direct_list_kernel<R, MODE><<<grid, DT_THREADS, smem, s>>>(dd.p, dd.Kstar, dd.pmax, dd.rep_p, dd.rep_off, t.pd_off, t.pd,
+    count_launch(), direct_list_kernel<R, MODE><<<grid, DT_THREADS, smem, s>>>(dd.p, dd.Kstar, dd.pmax, dd.rep_p, dd.rep_off, t.pd_off, t.pd,
                                                                 t.pdk, dd.centres, dd.zloc, soff, rho, dd.z);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
@@ -842,7 +870,7 @@ static cudaError_t tree_field_impl(const DeviceData& dd, const TreeDevice& t, cu
     if (dd.Kstar > 512) return cudaErrorInvalidConfiguration;
     const size_t smem = (size_t)t.max_q * sizeof(R);
     if ((e = allow_smem(l2p_kernel<R>, smem)) != cudaSuccess) return e;
-    l2p_kernel<R><<<(unsigned)dd.N, 512, smem, s>>>(dd.Kstar, t.pg_off, t.pg, t.gcen, t.gR, t.gshape, t.goff,
+    count_launch(), l2p_kernel<R><<<(unsigned)dd.N, 512, smem, s>>>(dd.Kstar, t.pg_off, t.pg, t.gcen, t.gR, t.gshape, t.goff,
                                                     t.shape_nr, t.shape_nth, t.coef, dd.centres, dd.zloc, dd.z);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
@@ -858,7 +886,7 @@ static cudaError_t tree_field_df(const DeviceData& dd, const TreeDevice& t, cuda
     if ((e = cudaMemsetAsync(t.grid, 0, t.ngrid * sizeof(double), s)) != cudaSuccess) return e;
     const size_t smem = (size_t)2 * P2L_JT * dd.pmax * sizeof(float4);
     if ((e = allow_smem(p2l_df_kernel<MODE>, smem)) != cudaSuccess) return e;
-    p2l_df_kernel<MODE><<<t.nitems, P2L_THREADS, smem, s>>>(t.witem_group, t.witem_rep, dd.rep_p, dd.rep_off, dd.p,
+    count_launch(), p2l_df_kernel<MODE><<<t.nitems, P2L_THREADS, smem, s>>>(t.witem_group, t.witem_rep, dd.rep_p, dd.rep_off, dd.p,
                                                            t.witem_lo, t.witem_hi, t.isrc, t.gcen, t.gshape, t.goff,
                                                            t.shape_nr, t.shape_nth, t.gpos64, dd.centres, dd.soff64,
                                                            dd.rho64, dd.logtab, t.grid);
@@ -873,7 +901,7 @@ static cudaError_t tree_field_df(const DeviceData& dd, const TreeDevice& t, cuda
     const size_t smem = (size_t)2 * DT_JT * dd.pmax * sizeof(float4);
     if ((e = allow_smem(direct_list_df_kernel<MODE>, smem)) != cudaSuccess) return e;
     dim3 grid((unsigned)dd.N, (unsigned)((dd.Kstar + DT_THREADS * DT_NT - 1) / (DT_THREADS * DT_NT)));
-    direct_list_df_kernel<MODE><<<grid, DT_THREADS, smem, s>>>(dd.p, dd.Kstar, dd.rep_p, dd.rep_off, t.pd_off, t.pd,
+    count_launch(), direct_list_df_kernel<MODE><<<grid, DT_THREADS, smem, s>>>(dd.p, dd.Kstar, dd.rep_p, dd.rep_off, t.pd_off, t.pd,
                                                               t.pdk, dd.centres, dd.zloc, dd.soff64, dd.rho64,
                                                               dd.logtab, dd.pmax, dd.z);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -883,7 +911,7 @@ static cudaError_t tree_field_df(const DeviceData& dd, const TreeDevice& t, cuda
     if (dd.Kstar > 512) return cudaErrorInvalidConfiguration;
     const size_t smem = (size_t)t.max_q * sizeof(float2);
     if ((e = allow_smem(l2p_df_kernel, smem)) != cudaSuccess) return e;
-    l2p_df_kernel<<<(unsigned)dd.N, 512, smem, s>>>(dd.Kstar, t.pg_off, t.pg, t.gcen, t.gR, t.gshape, t.goff,
+    count_launch(), l2p_df_kernel<<<(unsigned)dd.N, 512, smem, s>>>(dd.Kstar, t.pg_off, t.pg, t.gcen, t.gR, t.gshape, t.goff,
                                                    t.shape_nr, t.shape_nth, t.coef, dd.centres, dd.zloc, dd.z);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }

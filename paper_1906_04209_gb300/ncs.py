@@ -29,7 +29,8 @@ EXPORTS = ["ncs_default_params", "ncs_create", "ncs_create_from_operator", "ncs_
            "ncs_get_operator", "ncs_get_onepatch", "ncs_set_patches", "ncs_set_method", "ncs_matvec",
            "ncs_matvec_dev", "ncs_field_dev", "ncs_solve", "ncs_eval", "ncs_last_error", "ncs_destroy",
            "ncs_tree_pairs", "ncs_tree_stats", "ncs_profile_matvec", "ncs_create_from_operators", "ncs_get_reps",
-           "ncs_tc_gemm_f32", "ncs_batch_solve", "ncs_block_dots", "ncs_block_dots_noalloc"]
+           "ncs_tc_gemm_f32", "ncs_batch_solve", "ncs_block_dots", "ncs_block_dots_noalloc",
+           "ncs_launch_count"]
 
 
 class ncs_params(ctypes.Structure):
@@ -92,10 +93,12 @@ def load(path: str = LIB_PATH):
                                     ctypes.POINTER(ctypes.c_int), D]
     lib.ncs_block_dots.argtypes = [ctypes.c_int64, ctypes.c_int, VP, ctypes.c_int64, VP, VP, VP]
     lib.ncs_block_dots_noalloc.argtypes = [ctypes.c_int64, ctypes.c_int, VP, ctypes.c_int64, VP, VP, VP]
+    lib.ncs_launch_count.argtypes = []
+    lib.ncs_launch_count.restype = ctypes.c_int64
     lib.ncs_destroy.argtypes = [VP]
     lib.ncs_destroy.restype = None
     for name in EXPORTS:
-        if name not in ("ncs_default_params", "ncs_last_error", "ncs_destroy"):
+        if name not in ("ncs_default_params", "ncs_last_error", "ncs_destroy", "ncs_launch_count"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -144,6 +147,11 @@ def block_dots(n, k, V_ptr, ld, w_ptr, out_ptr, stream=0):
     rc = load().ncs_block_dots(n, k, VP(V_ptr), ld, VP(w_ptr), VP(out_ptr), VP(stream))
     if rc != NCS_OK:
         raise NcsError(rc, "ncs_block_dots failed")
+
+
+def launch_count():
+    """Kernels launched by the library so far in this process."""
+    return int(load().ncs_launch_count())
 
 
 def block_dots_noalloc(n, k, V_ptr, ld, w_ptr, out_ptr, stream=0):

@@ -49,7 +49,13 @@ def test_tree_vs_compressed_sums(small_pre, mode):
     zf64 = _field(ctx, x, ncs.FP64, N, pre.Kstar)
     zfdf = _field(ctx, x, ncs.DF64, N, pre.Kstar)
     z64 = zf64[patches]
+    n0 = ncs.launch_count()
     z32 = _field(ctx, x, ncs.FP32, N, pre.Kstar)[patches]
+    n1 = ncs.launch_count()
+    _field(ctx, x, ncs.FP32, N, pre.Kstar)
+    # outgoing, P2L, direct lists, L2P, plus one coefficient and at most one L2L launch per level
+    assert n1 - n0 == ncs.launch_count() - n1
+    assert 4 + 1 <= n1 - n0 <= 4 + 2 * st["levels"]
     assert np.abs(z64 - ref).max() <= 1e-8 * scale
     assert np.abs(z32 - ref).max() <= 5e-6 * scale
     # float-float tree product = FP64 tree product to rounding (same grids, same lists)
@@ -68,9 +74,10 @@ def test_tree_solve_matches_direct(small_pre, mode):
     c = L.jittered_fibonacci(N, eps, L.rng(97))
     ctx = _ctx(pre, method=ncs.METHOD_DIRECT)
     ctx.set_patches(c)
-    rd = ctx.solve(tol=1e-10, precision=ncs.FP64)
+    # float-float products: FP64-accurate at a fraction of the FP64-pipe time
+    rd = ctx.solve(tol=1e-10, precision=ncs.DF64)
     ctx.set_method(ncs.METHOD_TREE)
-    rt = ctx.solve(tol=1e-10, precision=ncs.FP64)
+    rt = ctx.solve(tol=1e-10, precision=ncs.DF64)
     rm = ctx.solve(tol=1e-8, precision=ncs.MIXED)
     assert abs(rt["scalar"] - rd["scalar"]) <= 1e-8 * abs(rd["scalar"])
     assert np.abs(rt["fhat"] - rd["fhat"]).max() <= 1e-7 * np.abs(rd["fhat"]).max()

@@ -76,3 +76,8 @@ def test_set_patches_validation(libncs):
     with pytest.raises(ncs.NcsError) as e:  # arguments are checked before any device work
         c.solve(tol=0)
     assert e.value.code == ncs.NCS_E_INPUT
+
+
+def test_launch_count_without_gpu(libncs):
+    # no kernel has been launched by the CPU-only tests; the counter is readable anyway
+    assert ncs.launch_count() >= 0
