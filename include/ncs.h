@@ -81,6 +81,10 @@ typedef struct ncs_params {
   int tensor_cores;    /* 1: the FP32 product runs its dense contractions
                           (rho = T x, y = x + P z) on the tcgen05 tensor cores (3xTF32);
                           0 (default): FP32 SIMT kernels */
+  int residual_update; /* NCS_MIXED: 1 (default) forms the refinement residual as
+                          r - A corr with an FP32 product once |r| <= 1e-4 |b| (its error,
+                          ~1e-6 |r|, is then below 1e-10 |b|); 0 always recomputes
+                          b - A x at mixed_residual precision */
 } ncs_params;
 
 /* Fills *p with the defaults listed above. */
@@ -214,12 +218,13 @@ int ncs_field_dev(ncs_ctx* ctx, const double* x, double* z, int precision, void*
  * Solves the system by GMRES (Section 7, Step 3; x0 = 0, relative residual tol).
  * precision: NCS_FP64 (all FP64), NCS_DF64 (float-float products, FP64 Arnoldi),
  * NCS_FP32 (FP32 products, FP64 Arnoldi) or NCS_MIXED (FP32 inner GMRES wrapped in
- * iterative refinement whose residuals use NCS_DF64 products).
+ * iterative refinement whose residuals use NCS_DF64 products, or, once the residual
+ * is below 1e-4 |b|, the FP32 residual update of ncs_params.residual_update).
  * Outputs (each may be NULL): fhat (N*K host doubles, the densities in the b_n
  * basis, Remark sigrep), scalar = mean first passage time mu = 1/(3 I_sigma) - 3/5
  * (interior, eq. mufromsigma2) or capacitance C = 4 pi I_sigma (exterior, |J|
  * of Section 2.2), I_sigma (eq. getI), iterations (total products by A), and the
- * final true relative residual. Errors: NCS_E_NOCONV (cap reached; outputs hold
+ * final relative residual (recomputed as b - A x, or updated as above). Errors: NCS_E_NOCONV (cap reached; outputs hold
  * the last iterate), NCS_E_NUMERIC, NCS_E_STATE, NCS_E_CUDA.
  */
 int ncs_solve(ncs_ctx* ctx, double tol, int precision, double* fhat, double* scalar,

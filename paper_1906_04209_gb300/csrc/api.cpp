@@ -456,6 +456,7 @@ void ncs_default_params(ncs_params* p) {
   p->verbose = 0;
   p->mixed_residual = NCS_DF64;
   p->tensor_cores = 0;
+  p->residual_update = 1;
 }
 
 int ncs_create(double eps, int mode, int K, const ncs_params* params, ncs_ctx** out) {
@@ -840,7 +841,11 @@ int ncs_solve(ncs_ctx* c, double tol, int precision, double* fhat, double* scala
       ++total;
       converged = est <= tol;
     } else {
-      // iterative refinement: FP32 inner GMRES, FP64 residuals
+      // iterative refinement: FP32 inner GMRES, FP64-accurate residuals. Once the
+      // residual is small, the correction is small as well and the new residual is
+      // updated as r - A corr with the FP32 product: its error (about 1e-6 |A corr|,
+      // |A corr| ~ |r|) is then below kUpdateRel * 1e-6 of |b|, far under the tolerance.
+      constexpr double kUpdateRel = 1e-4;
       double* corr = c->work + 4 * n;
       CU(cudaMemsetAsync(x, 0, n * sizeof(double), s));
       CU(cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -851,8 +856,14 @@ int ncs_solve(ncs_ctx* c, double tol, int precision, double* fhat, double* scala
         double inner_est = 1.0;
         total += gmres(c, r, corr, std::min(inner_tol, 0.5), NCS_FP32, maxit, &inner_est, s);
         CU(ncs::launch_axpby(n, 1.0, corr, 1.0, x, s));
-        matvec(c, x, r, c->prm.mixed_residual, s);
-        CU(ncs::launch_axpby(n, 1.0, b, -1.0, r, s));
+        if (rel <= kUpdateRel && c->prm.residual_update) {
+          double* Ac = c->work + 3 * n;
+          matvec(c, corr, Ac, NCS_FP32, s);
+          CU(ncs::launch_axpby(n, -1.0, Ac, 1.0, r, s));
+        } else {
+          matvec(c, x, r, c->prm.mixed_residual, s);
+          CU(ncs::launch_axpby(n, 1.0, b, -1.0, r, s));
+        }
         ++total;
         const double newrel = std::sqrt(dev_dot(c, r, r, s)) / bnorm;
         if (log_level() > 0) std::fprintf(stderr, "ncs: refinement %d relres %.3e\n", outer, newrel);

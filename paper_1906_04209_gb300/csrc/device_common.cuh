@@ -7,7 +7,6 @@ namespace ncs {
 
 constexpr double kLn4 = 1.3862943611198906188;
 constexpr float kLn2f = 0.69314718055994530942f;
-constexpr float kLn4f = 1.3862943611198906188f;
 
 // Patch frame for unit centre c: e1 = (z x c)/|z x c| (x-axis at the poles), e2 = c x e1.
 __device__ __forceinline__ void patch_frame(double cx, double cy, double cz, double* e1, double* e2) {
@@ -62,26 +61,17 @@ __device__ __forceinline__ double green64(double d2) {
   return u + kLn4 - log(fma(2.0, d, d2));
 }
 
+// One FP32 pair from half-scaled offsets: every coordinate is multiplied by 1/2, so
+// d2h = d^2 / 4 and rh = 1/sqrt(d2h) = 2/d = u. Then
+//   exterior: G_E = u - log(1 + u)                                  = rh - log(1 + rh)
+//   interior: G_I = u + log 4 - log(d^2 + 2d) = u - log((d^2 + 2d) / 4) = rh - log(d2h + d2h rh)
+// Two MUFU operations (rsqrt, lg2) and four FP32 operations per pair besides the squared
+// distance; returns acc + G rho.
 template <int MODE>
-__device__ __forceinline__ float green32(float d2) {
-  const float rinv = rsqrt_mufu(d2);
-  const float u = 2.0f * rinv;
-  if (MODE == 0) return u - kLn2f * lg2_mufu(1.0f + u);
-  const float d = d2 * rinv;
-  return u + kLn4f - kLn2f * lg2_mufu(fmaf(2.0f, d, d2));
-}
-
-// One FP32 pair term with pre-scaled source weights w1 = 2 rho, w2 = -log(2) rho:
-//   exterior: G rho = r w1 + log2(1 + 2r) w2                   (r = 1/d)
-//   interior: G rho = r w1 + log2(d^2 (1 + 2r)) w2 + log(4) rho
-// (the constant log(4) rho of the interior kernel is added once per source tile by
-// the caller). Two MUFU operations (rsqrt, lg2) and ~8 FP32 operations per pair.
-template <int MODE>
-__device__ __forceinline__ float pair32(float d2, float w1, float w2, float acc) {
-  const float r = rsqrt_mufu(d2);
-  const float t = fmaf(2.0f, r, 1.0f);
-  const float l = lg2_mufu(MODE == 0 ? t : d2 * t);
-  return fmaf(r, w1, fmaf(l, w2, acc));
+__device__ __forceinline__ float pair32(float d2h, float rho, float acc) {
+  const float rh = rsqrt_mufu(d2h);
+  const float l = lg2_mufu(MODE == 0 ? 1.0f + rh : fmaf(d2h, rh, d2h));
+  return fmaf(fmaf(l, -kLn2f, rh), rho, acc);
 }
 
 // log2(x) for normal x > 0 on the FMA and integer pipes instead of the MUFU unit:
@@ -107,26 +97,13 @@ __device__ __forceinline__ float lg2_poly(float x) {
   return fmaf(f, p, ef);
 }
 
-// pair32 with the logarithm taken by lg2_poly: the pair kernels use it for a share of
-// their pairs so that the MUFU unit and the FMA pipe are both kept busy.
+// pair32 with the logarithm taken by lg2_poly: the pair kernels may use it for a share
+// of their pairs so that the MUFU unit and the FMA pipe are both kept busy.
 template <int MODE>
-__device__ __forceinline__ float pair32_poly(float d2, float w1, float w2, float acc) {
-  const float r = rsqrt_mufu(d2);
-  const float t = fmaf(2.0f, r, 1.0f);
-  const float l = lg2_poly(MODE == 0 ? t : d2 * t);
-  return fmaf(r, w1, fmaf(l, w2, acc));
-}
-
-// Block-wide sum of a per-thread float (all threads must call; result valid in all threads).
-__device__ __forceinline__ float block_sum(float v, float* scratch32) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) scratch32[w] = v;
-  __syncthreads();
-  float s = 0.0f;
-  for (int i = 0; i < nw; ++i) s += scratch32[i];
-  return s;
+__device__ __forceinline__ float pair32_poly(float d2h, float rho, float acc) {
+  const float rh = rsqrt_mufu(d2h);
+  const float l = lg2_poly(MODE == 0 ? 1.0f + rh : fmaf(d2h, rh, d2h));
+  return fmaf(fmaf(l, -kLn2f, rh), rho, acc);
 }
 
 }  // namespace ncs

@@ -66,38 +66,55 @@ __device__ __forceinline__ f2 f2_sqr(f2 a) {
   return fast_two_sum(p.hi, p.lo);
 }
 
+// a + b in any order: TwoSum on the high words, the low words added once (the
+// "sloppy" float-float addition: accurate to ~2^-47 of max(|a|, |b|)).
+__device__ __forceinline__ f2 f2_add_sloppy(f2 a, f2 b) {
+  const f2 s = two_sum(a.hi, b.hi);
+  return fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
+
 // Table for log: entries i = 0..63 hold c_i = 1 + (i + 0.5)/64 as (log c_i hi, lo, 1/c_i hi, lo).
 constexpr int kLogTable = 64;
 
-// log(v) for v > 0 given as float-float: v = 2^e m, m in [1, 2); m = c_i (1 + delta)
-// with |delta| <= 1/129; log v = e log 2 + log c_i + log(1 + delta), the last by its
-// Taylor series through delta^6 (the delta and delta^2 terms in float-float).
-__device__ __forceinline__ f2 f2_log(f2 v, const float4* __restrict__ tab) {
+// log(v / 2^k) for v > 0 given as float-float (v.hi normal, |v.lo| <= ulp(v.hi)).
+// v = 2^e m, m in [1, 2); the top six bits of m pick c_i, m = c_i (1 + delta) with
+// |delta| <= 1/128, and log v = e log 2 + log c_i + log(1 + delta), the last by its
+// Taylor series through delta^6 (delta and delta^2 carried in float-float). The sums
+// are ordered so that only two TwoSums and one final renormalisation are needed.
+__device__ __forceinline__ f2 f2_log_pow2(f2 v, int k, const float4* __restrict__ tab) {
   const int ib = __float_as_int(v.hi);
-  const int e = ((ib >> 23) & 0xff) - 127;
+  const int e = (ib >> 23) - 127;
   const float m = __int_as_float((ib & 0x007fffff) | 0x3f800000);
-  const float vl = ldexpf(v.lo, -e);  // exact scaling of the low word
-  const int i = min(kLogTable - 1, (int)((m - 1.0f) * (float)kLogTable));
-  const float ci = 1.0f + ((float)i + 0.5f) / (float)kLogTable;
+  const float vl = v.lo * __int_as_float((127 - e) << 23);  // v.lo / 2^e, exact
+  const int i = (ib >> 17) & (kLogTable - 1);
+  const float ci = __int_as_float(0x3f800000 | (i << 17) | (1 << 16));
   const float4 t = tab[i];
-  // delta = (m - c_i + vl) / c_i
-  const f2 num = two_sum(m - ci, vl);  // m - c_i is exact (both in [1, 2), within 1/64)
-  const f2 d = f2_mul(num, f2{t.z, t.w});
+  // delta = (m - c_i + vl) / c_i; m - c_i is exact (both in [1, 2), 1/128 apart at most)
+  const float nh = m - ci;
+  const float dh = nh * t.z;
+  const f2 d = fast_two_sum(dh, fmaf(nh, t.w, fmaf(vl, t.z, fmaf(nh, t.z, -dh))));
   // log(1 + d) = d - d^2/2 + d^3 (1/3 - d/4 + d^2/5 - d^3/6)
-  const f2 d2 = f2_sqr(d);
-  const float dh = d.hi;
-  const float tail = dh * dh * dh * (0.333333333f + dh * (-0.25f + dh * (0.2f + dh * (-0.166666667f))));
-  f2 r = f2_add(d, f2{-0.5f * d2.hi, -0.5f * d2.lo});
-  r = f2_add(r, f2{tail, 0.0f});
+  const float q = d.hi * d.hi;
+  const float ql = fmaf(d.hi, d.hi, -q) + 2.0f * d.hi * d.lo;
+  const float tail =
+      q * d.hi * fmaf(d.hi, fmaf(d.hi, fmaf(d.hi, -0.166666667f, 0.2f), -0.25f), 0.333333333f);
+  const float rs = fmaf(-0.5f, q, d.hi);               // |d| > |d^2 / 2|: Fast2Sum
+  const float re = (-0.5f * q) - (rs - d.hi);
+  const float rl = re + d.lo + fmaf(-0.5f, ql, tail);
   // + log c_i
-  r = f2_add(r, f2{t.x, t.y});
-  // + e log 2, with log 2 as a float-float constant
-  const f2 ln2 = {0.693147182464599609375f, -1.904654323148236e-09f};
-  return f2_add(r, f2_mul_f(ln2, (float)e));
+  const f2 s1 = two_sum(t.x, rs);
+  const float l1 = s1.lo + (rl + t.y);
+  // + (e - k) log 2, log 2 as a float-float constant
+  const float ef = (float)(e - k);
+  const float Eh = ef * 0.693147182464599609375f;
+  const float El = fmaf(ef, 0.693147182464599609375f, -Eh) + ef * -1.904654323148236e-09f;
+  const f2 s2 = two_sum(Eh, s1.hi);
+  return fast_two_sum(s2.hi, s2.lo + (l1 + El));
 }
 
 // G from the float-float squared distance (eqs. Gextonsurface / Gintonsurface):
-//   exterior: u - log(1 + u), interior: u + log 4 - log(d^2 + 2d), u = 2/d.
+//   exterior: G_E = u - log(1 + u),
+//   interior: G_I = u + log 4 - log(d^2 + 2d) = u - log((d^2 + 2d) / 4),   u = 2/d.
 // 1/d from the FP32 reciprocal square root refined by one Newton step in float-float.
 template <int MODE>
 __device__ __forceinline__ f2 green_f2(f2 d2, const float4* __restrict__ tab) {
@@ -108,28 +125,37 @@ __device__ __forceinline__ f2 green_f2(f2 d2, const float4* __restrict__ tab) {
   const float r = (1.0f - m.hi) - m.lo;  // 1 - d^2 y^2, ~1e-7
   // 1/d = y (1 + r/2 + 3 r^2 / 8): u = 2/d
   const f2 u = fast_two_sum(2.0f * y, y * (r + 0.75f * r * r));
+  f2 v;
   if (MODE == 0) {
-    const f2 v = f2_add(f2{1.0f, 0.0f}, u);
-    return f2_sub(u, f2_log(v, tab));
+    v = two_sum(u.hi, 1.0f);
+    v = fast_two_sum(v.hi, v.lo + u.lo);
+  } else {
+    v = f2_add_sloppy(f2_mul(d2, u), d2);  // 2d = d^2 u
   }
-  const f2 d = f2_mul(d2, f2{0.5f * u.hi, 0.5f * u.lo});  // d = d^2 (u/2)
-  const f2 v = f2_add(d2, f2{2.0f * d.hi, 2.0f * d.lo});
-  const f2 ln4 = {1.38629436492919921875f, -3.809308646296472e-09f};
-  return f2_sub(f2_add(u, ln4), f2_log(v, tab));
+  const f2 L = f2_log_pow2(v, MODE == 0 ? 0 : 2, tab);
+  return f2_add_sloppy(u, f2{-L.hi, -L.lo});
 }
 
-// One pair term in float-float: target offset a (3 float-float words), source
-// (hi, lo) quadruples (offset, strength); returns G * rho.
+// acc += G * rho for one pair in float-float: target offset a (3 float-float words),
+// source (hi, lo) quadruples (offset, strength).
 template <int MODE>
-__device__ __forceinline__ f2 pair_f2(const f2* a, float4 sh, float4 sl, const float4* __restrict__ tab) {
-  f2 dx = two_sum(a[0].hi, -sh.x);
-  dx = fast_two_sum(dx.hi, dx.lo + (a[0].lo - sl.x));
-  f2 dy = two_sum(a[1].hi, -sh.y);
-  dy = fast_two_sum(dy.hi, dy.lo + (a[1].lo - sl.y));
-  f2 dz = two_sum(a[2].hi, -sh.z);
-  dz = fast_two_sum(dz.hi, dz.lo + (a[2].lo - sl.z));
-  const f2 d2 = f2_add(f2_add(f2_sqr(dx), f2_sqr(dy)), f2_sqr(dz));
-  return f2_mul(green_f2<MODE>(d2, tab), f2{sh.w, sl.w});
+__device__ __forceinline__ void pair_f2_acc(const f2* a, float4 sh, float4 sl, const float4* __restrict__ tab,
+                                            f2& acc) {
+  // offset differences as unnormalised (hi, lo) pairs, |lo| a few ulp of |hi|
+  f2 dx = two_sum(a[0].hi, -sh.x), dy = two_sum(a[1].hi, -sh.y), dz = two_sum(a[2].hi, -sh.z);
+  dx.lo += a[0].lo - sl.x;
+  dy.lo += a[1].lo - sl.y;
+  dz.lo += a[2].lo - sl.z;
+  // d^2 = sum hi^2 (exact products, two TwoSums) + sum (2 hi lo + lo^2)
+  const float px = dx.hi * dx.hi, py = dy.hi * dy.hi, pz = dz.hi * dz.hi;
+  const f2 s1 = two_sum(px, py);
+  const f2 s2 = two_sum(s1.hi, pz);
+  float lo = (s1.lo + s2.lo) + (fmaf(dx.hi, dx.hi, -px) + fmaf(dy.hi, dy.hi, -py) + fmaf(dz.hi, dz.hi, -pz));
+  lo = fmaf(fmaf(2.0f, dx.hi, dx.lo), dx.lo, lo);
+  lo = fmaf(fmaf(2.0f, dy.hi, dy.lo), dy.lo, lo);
+  lo = fmaf(fmaf(2.0f, dz.hi, dz.lo), dz.lo, lo);
+  const f2 d2 = fast_two_sum(s2.hi, lo);
+  acc = f2_add_sloppy(acc, f2_mul(green_f2<MODE>(d2, tab), f2{sh.w, sl.w}));
 }
 
 }  // namespace ncs

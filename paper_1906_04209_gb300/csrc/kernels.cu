@@ -134,10 +134,8 @@ __global__ void __launch_bounds__(DF_THREADS) direct_field_kernel(
   using V4 = typename Vec4<R>::type;
   extern __shared__ unsigned char df_smem[];
   V4* S = reinterpret_cast<V4*>(df_smem);  // JT * pmax
-  float* W2 = reinterpret_cast<float*>(S + (size_t)JT * pmax);  // FP32 path: -log(2) rho
   __shared__ double D[DF_JTMAX][3];
   __shared__ int toff[DF_JTMAX + 1], tcol[DF_JTMAX];
-  __shared__ float red32[DF_THREADS / 32];
   const int64_t i = blockIdx.x;
   const double cx = centres[3 * i], cy = centres[3 * i + 1], cz = centres[3 * i + 2];
   double e1[3], e2[3];
@@ -150,9 +148,10 @@ __global__ void __launch_bounds__(DF_THREADS) direct_field_kernel(
     kk[t] = (blockIdx.y * DF_NT + t) * DF_THREADS + threadIdx.x;
     double g[3] = {0.0, 0.0, 0.0};
     if (kk[t] < Kstar) frame_apply(e1, e2, cx, cy, cz, zloc[3 * kk[t]], zloc[3 * kk[t] + 1], zloc[3 * kk[t] + 2], g);
-    ax[t] = (R)g[0];
-    ay[t] = (R)g[1];
-    az[t] = (R)g[2];
+    const double sc = (sizeof(R) == 4) ? 0.5 : 1.0;  // FP32: half-scaled offsets
+    ax[t] = (R)(sc * g[0]);
+    ay[t] = (R)(sc * g[1]);
+    az[t] = (R)(sc * g[2]);
     acc[t] = 0.0;
   }
   for (int64_t j0 = 0; j0 < N; j0 += JT) {
@@ -181,7 +180,6 @@ __global__ void __launch_bounds__(DF_THREADS) direct_field_kernel(
     }
     __syncthreads();
     const int ns = toff[nj];
-    float rsum = 0.0f;
     for (int idx = threadIdx.x; idx < ns; idx += DF_THREADS) {
       int jj = 0;
       while (idx >= toff[jj + 1]) ++jj;
@@ -190,17 +188,14 @@ __global__ void __launch_bounds__(DF_THREADS) direct_field_kernel(
       v.x = (R)D[jj][0] + soff[3 * g];
       v.y = (R)D[jj][1] + soff[3 * g + 1];
       v.z = (R)D[jj][2] + soff[3 * g + 2];
-      if constexpr (sizeof(R) == 4) {
-        v.w = 2.0f * rho[g];
-        W2[idx] = -kLn2f * rho[g];
-        rsum += rho[g];
-      } else {
-        v.w = rho[g];
+      v.w = rho[g];
+      if constexpr (sizeof(R) == 4) {  // the FP32 pairs take half-scaled offsets
+        v.x *= 0.5f;
+        v.y *= 0.5f;
+        v.z *= 0.5f;
       }
       S[idx] = v;
     }
-    float tconst = 0.0f;
-    if constexpr (sizeof(R) == 4 && MODE == 1) tconst = kLn4f * block_sum(rsum, red32);
     __syncthreads();
     R part[DF_NT];
 #pragma unroll
@@ -214,11 +209,11 @@ __global__ void __launch_bounds__(DF_THREADS) direct_field_kernel(
         if constexpr (sizeof(R) == 8)
           part[t] = fma(green64<MODE>(d2), v.w, part[t]);
         else
-          part[t] = pair32<MODE>(d2, v.w, W2[s], part[t]);
+          part[t] = pair32<MODE>(d2, v.w, part[t]);
       }
     }
 #pragma unroll
-    for (int t = 0; t < DF_NT; ++t) acc[t] += (double)part[t] + (double)tconst;
+    for (int t = 0; t < DF_NT; ++t) acc[t] += (double)part[t];
   }
 #pragma unroll
   for (int t = 0; t < DF_NT; ++t)
@@ -296,7 +291,7 @@ __global__ void __launch_bounds__(DF_THREADS) direct_field_df_kernel(
     for (int s = 0; s < ns; ++s) {
       const float4 h = Sh[s], l = Sl[s];
 #pragma unroll
-      for (int t = 0; t < DF_NT; ++t) part[t] = f2_add(part[t], pair_f2<MODE>(a[t], h, l, tab));
+      for (int t = 0; t < DF_NT; ++t) pair_f2_acc<MODE>(a[t], h, l, tab, part[t]);
     }
 #pragma unroll
     for (int t = 0; t < DF_NT; ++t) acc[t] += f2_to_double(part[t]);
@@ -333,9 +328,9 @@ cudaError_t launch_direct_field(const DeviceData& d, int mode, int prec, double 
     return cudaGetLastError();
   }
   const size_t v4 = (prec == NCS_FP64) ? sizeof(double4) : sizeof(float4);
-  int JT = (int)std::min<size_t>(DF_JTMAX, (40 * 1024) / ((v4 + 4) * (size_t)d.pmax));
+  int JT = (int)std::min<size_t>(DF_JTMAX, (40 * 1024) / (v4 * (size_t)d.pmax));
   if (JT < 1) JT = 1;
-  const size_t smem = (size_t)JT * d.pmax * (v4 + 4);
+  const size_t smem = (size_t)JT * d.pmax * v4;
   dim3 grid((unsigned)d.N, (unsigned)((d.Kstar + DF_THREADS * DF_NT - 1) / (DF_THREADS * DF_NT)));
   cudaError_t e;
 #define NCS_DF(R, M, SOFF, RHO)                                                                            \
@@ -362,35 +357,82 @@ cudaError_t launch_direct_field(const DeviceData& d, int mode, int prec, double 
 
 // ---------------------------------------------------------------------------
 // Step 3.5: y_i = x_i + P z_i. PT is P transposed (Kstar x K).
-constexpr int AP_PB = 4;
+// A block takes BP patches; their z rows are staged transposed in shared memory
+// (zT[q][i], row stride BP + 1 so that the staging stores spread over the banks), and
+// each thread accumulates a 4-patch x 4-output register tile over all Kstar nodes: per
+// node four shared loads of z and four loads of PT (L1/L2 resident, 270 KB in FP32)
+// feed 16 FMAs.
+constexpr int AP_THREADS = 288;
 
-template <typename R>
-__global__ void __launch_bounds__(256) apply_P_kernel(int64_t N, int K, int Kstar, const R* __restrict__ PT,
-                                                      const double* __restrict__ z, const double* __restrict__ x,
-                                                      double* __restrict__ y) {
-  extern __shared__ unsigned char ap_smem[];
-  R* zs = reinterpret_cast<R*>(ap_smem);  // AP_PB x Kstar
-  const int64_t i0 = (int64_t)blockIdx.x * AP_PB;
-  const int np = (int)min((int64_t)AP_PB, N - i0);
-  for (int idx = threadIdx.x; idx < np * Kstar; idx += blockDim.x) zs[idx] = (R)z[i0 * Kstar + idx];
+template <typename R, int BP>
+__global__ void __launch_bounds__(AP_THREADS) apply_P_kernel(int64_t N, int K, int Kstar, const R* __restrict__ PT,
+                                                             const double* __restrict__ z,
+                                                             const double* __restrict__ x, double* __restrict__ y) {
+  extern __shared__ __align__(16) unsigned char ap_smem[];
+  constexpr int SB = BP + 1;
+  R* zT = reinterpret_cast<R*>(ap_smem);  // Kstar x SB
+  const int64_t i0 = (int64_t)blockIdx.x * BP;
+  const int np = (int)min((int64_t)BP, N - i0);
+  for (int idx = threadIdx.x; idx < BP * Kstar; idx += blockDim.x) {
+    const int ii = idx / Kstar, q = idx - ii * Kstar;
+    zT[q * SB + ii] = (ii < np) ? (R)z[(i0 + ii) * Kstar + q] : (R)0;
+  }
   __syncthreads();
-  for (int idx = threadIdx.x; idx < np * K; idx += blockDim.x) {
-    const int ii = idx / K, j = idx - ii * K;
-    const R* zr = zs + ii * Kstar;
-    R acc = 0;
-    for (int q = 0; q < Kstar; ++q) acc = fma(PT[(int64_t)q * K + j], zr[q], acc);
-    y[(i0 + ii) * K + j] = x[(i0 + ii) * K + j] + (double)acc;
+  const int nJ = (K + 3) / 4, nW = nJ * (BP / 4);
+  for (int w = threadIdx.x; w < nW; w += blockDim.x) {
+    const int j0 = 4 * (w % nJ), a0 = 4 * (w / nJ);
+    R acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[a][c] = 0;
+    for (int q = 0; q < Kstar; ++q) {
+      const R* pr = PT + (int64_t)q * K + j0;
+      R pv[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) pv[c] = (j0 + c < K) ? __ldg(pr + c) : (R)0;
+      const R* zr = zT + q * SB + a0;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const R zv = zr[a];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[a][c] = fma(pv[c], zv, acc[a][c]);
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (a0 + a < np && j0 + c < K) {
+          const int64_t o = (i0 + a0 + a) * K + j0 + c;
+          y[o] = x[o] + (double)acc[a][c];
+        }
   }
 }
 
 // prec: NCS_FP32 runs the transform in FP32 (the FP32 product), otherwise FP64.
 cudaError_t launch_apply_P(const DeviceData& d, const double* x, double* y, int prec, cudaStream_t s) {
-  const unsigned blocks = (unsigned)((d.N + AP_PB - 1) / AP_PB);
-  if (prec == NCS_FP32)
-    count_launch(), apply_P_kernel<float><<<blocks, 256, AP_PB * d.Kstar * sizeof(float), s>>>(d.N, d.K, d.Kstar, d.PT32, d.z, x, y);
-  else
-    count_launch(), apply_P_kernel<double><<<blocks, 256, AP_PB * d.Kstar * sizeof(double), s>>>(d.N, d.K, d.Kstar, d.PT64, d.z, x,
-                                                                                 y);
+  if (prec == NCS_FP32) {
+    constexpr int BP = 32;
+    const size_t smem = (size_t)(BP + 1) * d.Kstar * sizeof(float);
+    if (smem > 48 * 1024) {
+      const cudaError_t e = cudaFuncSetAttribute(apply_P_kernel<float, BP>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    const unsigned blocks = (unsigned)((d.N + BP - 1) / BP);
+    count_launch(), apply_P_kernel<float, BP><<<blocks, AP_THREADS, smem, s>>>(d.N, d.K, d.Kstar, d.PT32, d.z, x, y);
+  } else {
+    constexpr int BP = 16;
+    const size_t smem = (size_t)(BP + 1) * d.Kstar * sizeof(double);
+    if (smem > 48 * 1024) {
+      const cudaError_t e = cudaFuncSetAttribute(apply_P_kernel<double, BP>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    const unsigned blocks = (unsigned)((d.N + BP - 1) / BP);
+    count_launch(), apply_P_kernel<double, BP><<<blocks, AP_THREADS, smem, s>>>(d.N, d.K, d.Kstar, d.PT64, d.z, x, y);
+  }
   return cudaGetLastError();
 }
 

@@ -51,8 +51,8 @@ void fr(T*& p) {
 constexpr int P2L_THREADS = 256;
 constexpr int P2L_NT = 2;
 constexpr int P2L_JT = 8;
-// FP32 P2L: odd target slots take their logarithm with lg2_poly (FMA pipe) instead of
-// the MUFU unit, which alone would otherwise bound the pair rate.
+// FP32 P2L: NCS_P2L_POLYLOG of every 16 pairs (0, 1 or 2) take their logarithm with
+// lg2_poly on the FMA pipe instead of the MUFU unit, which otherwise bounds the pair rate.
 #ifndef NCS_P2L_POLYLOG
 #define NCS_P2L_POLYLOG 0
 #endif
@@ -69,13 +69,11 @@ __global__ void __launch_bounds__(P2L_THREADS) p2l_kernel(
   using V4 = typename V4T<R>::type;
   extern __shared__ unsigned char p2l_smem[];
   __shared__ double D[P2L_JT][3];
-  __shared__ float red32[P2L_THREADS / 32];
   const int item = blockIdx.x;
   const int g = witem_group[item];
   const int rk = witem_rep[item];
   const int p = rep_p[rk], col = rep_off[rk];
   V4* S = reinterpret_cast<V4*>(p2l_smem);
-  float* W2 = reinterpret_cast<float*>(S + (size_t)P2L_JT * p);  // FP32 path: -log(2) rho
   const int64_t lo = witem_lo[item], hi = witem_hi[item];
   const int sh = gshape[g];
   const int q = shape_nr[sh] * shape_nth[sh];
@@ -87,10 +85,11 @@ __global__ void __launch_bounds__(P2L_THREADS) p2l_kernel(
 #pragma unroll
     for (int t = 0; t < P2L_NT; ++t) {
       const int a = base + t * P2L_THREADS + threadIdx.x;
+      const R sc = (sizeof(R) == 4) ? (R)0.5 : (R)1;  // FP32: half-scaled offsets
       if (a < q) {
-        ax[t] = gpos[3 * (off + a)];
-        ay[t] = gpos[3 * (off + a) + 1];
-        az[t] = gpos[3 * (off + a) + 2];
+        ax[t] = sc * gpos[3 * (off + a)];
+        ay[t] = sc * gpos[3 * (off + a) + 1];
+        az[t] = sc * gpos[3 * (off + a) + 2];
       } else {
         ax[t] = ay[t] = az[t] = (R)0;
       }
@@ -105,7 +104,6 @@ __global__ void __launch_bounds__(P2L_THREADS) p2l_kernel(
         D[jj][c] = centres[3 * j + c] - (c == 0 ? gx : (c == 1 ? gy : gz));
       }
       __syncthreads();
-      float rsum = 0.0f;
       for (int idx = threadIdx.x; idx < nj * p; idx += P2L_THREADS) {
         const int jj = idx / p;
         const int64_t gsrc = (int64_t)isrc[s0 + jj] * pt + col + (idx - jj * p);
@@ -113,17 +111,14 @@ __global__ void __launch_bounds__(P2L_THREADS) p2l_kernel(
         v.x = (R)D[jj][0] + soff[3 * gsrc];
         v.y = (R)D[jj][1] + soff[3 * gsrc + 1];
         v.z = (R)D[jj][2] + soff[3 * gsrc + 2];
-        if constexpr (sizeof(R) == 4) {
-          v.w = 2.0f * rho[gsrc];
-          W2[idx] = -kLn2f * rho[gsrc];
-          rsum += rho[gsrc];
-        } else {
-          v.w = rho[gsrc];
+        v.w = rho[gsrc];
+        if constexpr (sizeof(R) == 4) {  // the FP32 pairs take half-scaled offsets
+          v.x *= 0.5f;
+          v.y *= 0.5f;
+          v.z *= 0.5f;
         }
         S[idx] = v;
       }
-      float tconst = 0.0f;
-      if constexpr (sizeof(R) == 4 && MODE == 1) tconst = kLn4f * block_sum(rsum, red32);
       __syncthreads();
       const int ns = nj * p;
       R part[P2L_NT];
@@ -133,7 +128,27 @@ __global__ void __launch_bounds__(P2L_THREADS) p2l_kernel(
       const int wbase = base + (threadIdx.x & ~31);
       const int nact = (wbase >= q) ? 0 : ((wbase + P2L_THREADS >= q) ? 1 : P2L_NT);
       if (nact == P2L_NT) {
-        for (int s = 0; s < ns; ++s) {
+        int s = 0;
+        if constexpr (sizeof(R) == 4 && NCS_P2L_POLYLOG > 0) {
+          // sources in groups of 8: the last source of a group takes lg2_poly for its
+          // first NCS_P2L_POLYLOG target slots (1 or 2 of the group's 16 pairs)
+          for (; s + 8 <= ns; s += 8) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const V4 v = S[s + u];
+#pragma unroll
+              for (int t = 0; t < P2L_NT; ++t) {
+                const R dx = ax[t] - v.x, dy = ay[t] - v.y, dz = az[t] - v.z;
+                const R d2 = fma(dx, dx, fma(dy, dy, dz * dz));
+                if (u == 7 && t < NCS_P2L_POLYLOG)
+                  part[t] = pair32_poly<MODE>(d2, v.w, part[t]);
+                else
+                  part[t] = pair32<MODE>(d2, v.w, part[t]);
+              }
+            }
+          }
+        }
+        for (; s < ns; ++s) {
           const V4 v = S[s];
 #pragma unroll
           for (int t = 0; t < P2L_NT; ++t) {
@@ -141,10 +156,8 @@ __global__ void __launch_bounds__(P2L_THREADS) p2l_kernel(
             const R d2 = fma(dx, dx, fma(dy, dy, dz * dz));
             if constexpr (sizeof(R) == 8)
               part[t] = fma(green64<MODE>(d2), v.w, part[t]);
-            else if (NCS_P2L_POLYLOG && (t & 1))
-              part[t] = pair32_poly<MODE>(d2, v.w, W2[s], part[t]);
             else
-              part[t] = pair32<MODE>(d2, v.w, W2[s], part[t]);
+              part[t] = pair32<MODE>(d2, v.w, part[t]);
           }
         }
       } else if (nact == 1) {
@@ -155,11 +168,11 @@ __global__ void __launch_bounds__(P2L_THREADS) p2l_kernel(
           if constexpr (sizeof(R) == 8)
             part[0] = fma(green64<MODE>(d2), v.w, part[0]);
           else
-            part[0] = pair32<MODE>(d2, v.w, W2[s], part[0]);
+            part[0] = pair32<MODE>(d2, v.w, part[0]);
         }
       }
 #pragma unroll
-      for (int t = 0; t < P2L_NT; ++t) acc[t] += (double)part[t] + (double)tconst;
+      for (int t = 0; t < P2L_NT; ++t) acc[t] += (double)part[t];
     }
 #pragma unroll
     for (int t = 0; t < P2L_NT; ++t) {
@@ -234,10 +247,8 @@ __global__ void __launch_bounds__(DT_THREADS) direct_list_kernel(
   using V4 = typename V4T<R>::type;
   extern __shared__ unsigned char dt_smem[];
   V4* S = reinterpret_cast<V4*>(dt_smem);
-  float* W2 = reinterpret_cast<float*>(S + (size_t)DT_JT * pmax);  // FP32 path: -log(2) rho
   __shared__ double D[DT_JT][3];
   __shared__ int toff[DT_JT + 1], tcol[DT_JT];
-  __shared__ float red32[DT_THREADS / 32];
   const int64_t i = blockIdx.x;
   const double cx = centres[3 * i], cy = centres[3 * i + 1], cz = centres[3 * i + 2];
   double e1[3], e2[3];
@@ -250,9 +261,10 @@ __global__ void __launch_bounds__(DT_THREADS) direct_list_kernel(
     kk[t] = (blockIdx.y * DT_NT + t) * DT_THREADS + threadIdx.x;
     double gq[3] = {0.0, 0.0, 0.0};
     if (kk[t] < Kstar) frame_apply(e1, e2, cx, cy, cz, zloc[3 * kk[t]], zloc[3 * kk[t] + 1], zloc[3 * kk[t] + 2], gq);
-    ax[t] = (R)gq[0];
-    ay[t] = (R)gq[1];
-    az[t] = (R)gq[2];
+    const double sc = (sizeof(R) == 4) ? 0.5 : 1.0;  // FP32: half-scaled offsets
+    ax[t] = (R)(sc * gq[0]);
+    ay[t] = (R)(sc * gq[1]);
+    az[t] = (R)(sc * gq[2]);
     acc[t] = 0.0;
   }
   const int64_t lo = pd_off[i], hi = pd_off[i + 1];
@@ -273,7 +285,6 @@ __global__ void __launch_bounds__(DT_THREADS) direct_list_kernel(
     }
     __syncthreads();
     const int ns = toff[nj];
-    float rsum = 0.0f;
     for (int idx = threadIdx.x; idx < ns; idx += DT_THREADS) {
       int jj = 0;
       while (idx >= toff[jj + 1]) ++jj;
@@ -282,17 +293,14 @@ __global__ void __launch_bounds__(DT_THREADS) direct_list_kernel(
       v.x = (R)D[jj][0] + soff[3 * gsrc];
       v.y = (R)D[jj][1] + soff[3 * gsrc + 1];
       v.z = (R)D[jj][2] + soff[3 * gsrc + 2];
-      if constexpr (sizeof(R) == 4) {
-        v.w = 2.0f * rho[gsrc];
-        W2[idx] = -kLn2f * rho[gsrc];
-        rsum += rho[gsrc];
-      } else {
-        v.w = rho[gsrc];
+      v.w = rho[gsrc];
+      if constexpr (sizeof(R) == 4) {  // the FP32 pairs take half-scaled offsets
+        v.x *= 0.5f;
+        v.y *= 0.5f;
+        v.z *= 0.5f;
       }
       S[idx] = v;
     }
-    float tconst = 0.0f;
-    if constexpr (sizeof(R) == 4 && MODE == 1) tconst = kLn4f * block_sum(rsum, red32);
     __syncthreads();
     R part[DT_NT];
 #pragma unroll
@@ -306,11 +314,11 @@ __global__ void __launch_bounds__(DT_THREADS) direct_list_kernel(
         if constexpr (sizeof(R) == 8)
           part[t] = fma(green64<MODE>(d2), v.w, part[t]);
         else
-          part[t] = pair32<MODE>(d2, v.w, W2[s], part[t]);
+          part[t] = pair32<MODE>(d2, v.w, part[t]);
       }
     }
 #pragma unroll
-    for (int t = 0; t < DT_NT; ++t) acc[t] += (double)part[t] + (double)tconst;
+    for (int t = 0; t < DT_NT; ++t) acc[t] += (double)part[t];
   }
 #pragma unroll
   for (int t = 0; t < DT_NT; ++t)
@@ -432,6 +440,211 @@ __global__ void __launch_bounds__(256) l2l_kernel(int l0, const int* __restrict_
   }
 }
 
+// ---- FP32 L2P / L2L ----------------------------------------------------------------
+// The FP32 product evaluates the expansions with polar coordinates formed in FP32: per
+// (patch or child, group) threads 0..11 build the rotation M from the evaluation points'
+// local frame into the group frame (uploaded per group) and the offset of their origin,
+// and every point then needs 9 FMAs, a square root and an atan2 on the FP32 pipes. Each
+// thread evaluates two points, so every coefficient load from shared memory serves both.
+
+// Clenshaw as eval_expansion for two points at once, the A and B coefficients of each
+// (m, j) interleaved.
+__device__ __forceinline__ void eval_expansion_ab2(const float2* C, int nr, int mh, const float* rho,
+                                                   const float* ct, const float* st, float* out) {
+  float y[2], y2[2], cm[2], sm[2], val[2];
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    y[t] = fmaf(2.0f * rho[t], rho[t], -1.0f);
+    y2[t] = y[t] + y[t];
+    cm[t] = 1.0f;
+    sm[t] = 0.0f;
+    val[t] = 0.0f;
+  }
+  for (int m = 0; m < mh; ++m) {
+    const float2* c = C + m * nr;
+    float ba1[2] = {0.0f, 0.0f}, ba2[2] = {0.0f, 0.0f}, bb1[2] = {0.0f, 0.0f}, bb2[2] = {0.0f, 0.0f};
+    for (int j = nr - 1; j >= 0; --j) {
+      const float2 ab = c[j];
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        const float ta = fmaf(y2[t], ba1[t], ab.x - ba2[t]);
+        const float tb = fmaf(y2[t], bb1[t], ab.y - bb2[t]);
+        ba2[t] = ba1[t];
+        ba1[t] = ta;
+        bb2[t] = bb1[t];
+        bb1[t] = tb;
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      float sa, sb;
+      if ((m & 1) == 0) {
+        sa = fmaf(-y[t], ba2[t], ba1[t]);
+        sb = fmaf(-y[t], bb2[t], bb1[t]);
+      } else {
+        sa = rho[t] * (ba1[t] - ba2[t]);
+        sb = rho[t] * (bb1[t] - bb2[t]);
+      }
+      val[t] = fmaf(cm[t], sa, fmaf(sm[t], sb, val[t]));
+      const float cn = cm[t] * ct[t] - sm[t] * st[t];
+      sm[t] = fmaf(sm[t], ct[t], cm[t] * st[t]);
+      cm[t] = cn;
+    }
+  }
+  out[0] = val[0];
+  out[1] = val[1];
+}
+
+// Stages group coefficients (FP64, A block then B block) as interleaved FP32 pairs.
+__device__ __forceinline__ void stage_ab(const double* __restrict__ coef, int nr, int mh, float2* C) {
+  const int h = mh * nr;
+  for (int t = threadIdx.x; t < h; t += blockDim.x) C[t] = make_float2((float)coef[t], (float)coef[h + t]);
+}
+
+// FP32 patch frame (same rule as patch_frame).
+__device__ __forceinline__ void patch_frame32(float cx, float cy, float cz, float* e1, float* e2) {
+  const float ax = -cy, ay = cx, na2 = fmaf(ax, ax, ay * ay);
+  if (na2 >= 1e-24f) {
+    const float inv = rsqrtf(na2);
+    e1[0] = ax * inv;
+    e1[1] = ay * inv;
+  } else {
+    e1[0] = 1.0f;
+    e1[1] = 0.0f;
+  }
+  e1[2] = 0.0f;
+  e2[0] = cy * e1[2] - cz * e1[1];
+  e2[1] = cz * e1[0] - cx * e1[2];
+  e2[2] = cx * e1[1] - cy * e1[0];
+}
+
+// Threads 0..11 fill M (caller synchronises): M[3r + c] = F_r . a_c for the group frame
+// rows F_r and the local frame columns a_c, M[9 + r] = F_r . (o - g) for the local
+// origin o and group centre g. Thread t < 9 passes in acol the column a_(t mod 3)
+// (ignored when identity is set: the local frame is then the global one).
+__device__ __forceinline__ void group_transform32(const float* __restrict__ F, const double* __restrict__ g,
+                                                  const float* acol, bool identity, double ox, double oy,
+                                                  double oz, float* M) {
+  const int t = threadIdx.x;
+  if (t < 9) {
+    const int r = t / 3, c = t - 3 * (t / 3);
+    const float* f = F + 3 * r;
+    M[t] = identity ? f[c] : fmaf(f[0], acol[0], fmaf(f[1], acol[1], f[2] * acol[2]));
+  } else if (t < 12) {
+    const float* f = F + 3 * (t - 9);
+    M[t] = fmaf(f[0], (float)(ox - g[0]), fmaf(f[1], (float)(oy - g[1]), f[2] * (float)(oz - g[2])));
+  }
+}
+
+// Polar coordinates in the group frame of the local point v, given M from group_transform32.
+__device__ __forceinline__ void polar32(const float* M, float v0, float v1, float v2, float invR, float* rho,
+                                        float* ct, float* st) {
+  const float u1 = fmaf(M[0], v0, fmaf(M[1], v1, fmaf(M[2], v2, M[9])));
+  const float u2 = fmaf(M[3], v0, fmaf(M[4], v1, fmaf(M[5], v2, M[10])));
+  const float u3 = fmaf(M[6], v0, fmaf(M[7], v1, fmaf(M[8], v2, M[11])));
+  const float sr2 = fmaf(u1, u1, u2 * u2);
+  if (sr2 > 0.0f) {
+    const float ir = rsqrtf(sr2);
+    const float sr = sr2 * ir;
+    *rho = atan2f(sr, 1.0f + u3) * invR;
+    *ct = u1 * ir;
+    *st = u2 * ir;
+  } else {
+    *rho = 0.0f;
+    *ct = 1.0f;
+    *st = 0.0f;
+  }
+}
+
+constexpr int L2P32_THREADS = 256;  // two Zernike nodes per thread (K* <= 512)
+
+// L2P, FP32 product: z_i(k) += expansion of every listed grid group of patch i at node k.
+__global__ void __launch_bounds__(L2P32_THREADS) l2p_f32_kernel(
+    int Kstar, const int64_t* __restrict__ pg_off, const int* __restrict__ pg, const double* __restrict__ gcen,
+    const double* __restrict__ gR, const float* __restrict__ gframe, const int* __restrict__ gshape,
+    const int64_t* __restrict__ goff, const int* __restrict__ shape_nr, const int* __restrict__ shape_nth,
+    const double* __restrict__ coef, const double* __restrict__ centres, const double* __restrict__ zloc,
+    double* __restrict__ z) {
+  extern __shared__ unsigned char lp32_smem[];
+  float2* C = reinterpret_cast<float2*>(lp32_smem);
+  __shared__ float M[12];
+  const int64_t i = blockIdx.x;
+  const int k[2] = {(int)threadIdx.x, (int)threadIdx.x + L2P32_THREADS};
+  float v[2][3];
+#pragma unroll
+  for (int t = 0; t < 2; ++t)
+    for (int c = 0; c < 3; ++c) v[t][c] = (k[t] < Kstar) ? (float)zloc[3 * k[t] + c] : 0.0f;
+  const double cx = centres[3 * i], cy = centres[3 * i + 1], cz = centres[3 * i + 2];
+  float acol[3] = {0.0f, 0.0f, 0.0f};  // column (threadIdx mod 3) of the patch frame (e1, e2, c)
+  if (threadIdx.x < 9) {
+    float e1[3], e2[3];
+    patch_frame32((float)cx, (float)cy, (float)cz, e1, e2);
+    const int c = threadIdx.x % 3;
+    const float cc[3] = {(float)cx, (float)cy, (float)cz};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) acol[k] = c == 0 ? e1[k] : (c == 1 ? e2[k] : cc[k]);
+  }
+  double acc[2] = {0.0, 0.0};
+  for (int64_t s = pg_off[i]; s < pg_off[i + 1]; ++s) {
+    const int g = pg[s];
+    const int sh = gshape[g];
+    const int nr = shape_nr[sh], mh = shape_nth[sh] / 2;
+    __syncthreads();
+    stage_ab(coef + goff[g], nr, mh, C);
+    group_transform32(gframe + 9 * (size_t)g, gcen + 3 * g, acol, false, cx, cy, cz, M);
+    __syncthreads();
+    const float invR = (float)(1.0 / gR[g]);
+    float rho[2], ct[2], st[2], out[2];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) polar32(M, v[t][0], v[t][1], v[t][2], invR, &rho[t], &ct[t], &st[t]);
+    eval_expansion_ab2(C, nr, mh, rho, ct, st, out);
+    acc[0] += (double)out[0];
+    acc[1] += (double)out[1];
+  }
+#pragma unroll
+  for (int t = 0; t < 2; ++t)
+    if (k[t] < Kstar) z[i * Kstar + k[t]] += acc[t];
+}
+
+constexpr int L2L32_THREADS = 256;
+
+// Downward pass, FP32 product: the child's grid points are given by their FP32 offsets
+// from the child centre in the global frame (local frame = identity); two points per
+// thread per round.
+__global__ void __launch_bounds__(L2L32_THREADS) l2l_f32_kernel(
+    int l0, const int* __restrict__ l2l_child, const int* __restrict__ l2l_parent, const double* __restrict__ gcen,
+    const double* __restrict__ gR, const float* __restrict__ gframe, const int* __restrict__ gshape,
+    const int64_t* __restrict__ goff, const int* __restrict__ shape_nr, const int* __restrict__ shape_nth,
+    const double* __restrict__ coef, const float* __restrict__ gpos, double* __restrict__ grid) {
+  extern __shared__ unsigned char ll32_smem[];
+  float2* C = reinterpret_cast<float2*>(ll32_smem);
+  __shared__ float M[12];
+  const int ch = l2l_child[l0 + blockIdx.x], pa = l2l_parent[l0 + blockIdx.x];
+  const int shp = gshape[pa], shc = gshape[ch];
+  const int nrp = shape_nr[shp], mhp = shape_nth[shp] / 2;
+  const int qc = shape_nr[shc] * shape_nth[shc];
+  const int64_t offc = goff[ch];
+  stage_ab(coef + goff[pa], nrp, mhp, C);
+  const double* q = gcen + 3 * ch;
+  group_transform32(gframe + 9 * (size_t)pa, gcen + 3 * pa, nullptr, true, q[0], q[1], q[2], M);
+  __syncthreads();
+  const float invR = (float)(1.0 / gR[pa]);
+  for (int a0 = threadIdx.x; a0 < qc; a0 += 2 * L2L32_THREADS) {
+    const int a[2] = {a0, a0 + L2L32_THREADS};
+    float rho[2], ct[2], st[2], out[2];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const int aa = a[t] < qc ? a[t] : a0;
+      const float* o = gpos + 3 * (offc + aa);
+      polar32(M, o[0], o[1], o[2], invR, &rho[t], &ct[t], &st[t]);
+    }
+    eval_expansion_ab2(C, nrp, mhp, rho, ct, st, out);
+#pragma unroll
+    for (int t = 0; t < 2; ++t)
+      if (a[t] < qc) grid[offc + a[t]] += (double)out[t];
+  }
+}
+
 // ---- float-float variants (FP64-accurate on the FP32 pipes) -----------------------
 // Sources are staged as (hi, lo) float4 pairs formed from the FP64 offsets and
 // strengths; tile sums are folded into an FP64 accumulator.
@@ -495,10 +708,10 @@ __global__ void __launch_bounds__(P2L_THREADS) p2l_df_kernel(
         for (int s = 0; s < ns; ++s) {
           const float4 h = Sh[s], l = Sl[s];
 #pragma unroll
-          for (int t = 0; t < NT; ++t) part[t] = f2_add(part[t], pair_f2<MODE>(a[t], h, l, tab));
+          for (int t = 0; t < NT; ++t) pair_f2_acc<MODE>(a[t], h, l, tab, part[t]);
         }
       } else if (nact == 1) {
-        for (int s = 0; s < ns; ++s) part[0] = f2_add(part[0], pair_f2<MODE>(a[0], Sh[s], Sl[s], tab));
+        for (int s = 0; s < ns; ++s) pair_f2_acc<MODE>(a[0], Sh[s], Sl[s], tab, part[0]);
       }
 #pragma unroll
       for (int t = 0; t < NT; ++t) acc[t] += f2_to_double(part[t]);
@@ -573,7 +786,7 @@ __global__ void __launch_bounds__(DT_THREADS) direct_list_df_kernel(
     for (int s = 0; s < ns; ++s) {
       const float4 h = Sh[s], l = Sl[s];
 #pragma unroll
-      for (int t = 0; t < DT_NT; ++t) part[t] = f2_add(part[t], pair_f2<MODE>(a[t], h, l, tab));
+      for (int t = 0; t < DT_NT; ++t) pair_f2_acc<MODE>(a[t], h, l, tab, part[t]);
     }
 #pragma unroll
     for (int t = 0; t < DT_NT; ++t) acc[t] += f2_to_double(part[t]);
@@ -704,6 +917,7 @@ void tree_upload(const TreeHost& t, const Precomputed& pc, TreeDevice& d) {
   }
   // grid-point offsets from the group centre in the global frame (FP64 and FP32)
   std::vector<double> gp64(3 * (size_t)d.ngrid);
+  std::vector<float> gf(9 * (size_t)d.ngroups);
   for (int g = 0; g < d.ngroups; ++g) {
     const GridShape& s = t.shapes[t.gshape[g]];
     const double* c = &t.gcen[3 * g];
@@ -722,6 +936,11 @@ void tree_upload(const TreeHost& t, const Precomputed& pc, TreeDevice& d) {
     e2[0] = c[1] * e1[2] - c[2] * e1[1];
     e2[1] = c[2] * e1[0] - c[0] * e1[2];
     e2[2] = c[0] * e1[1] - c[1] * e1[0];
+    for (int k = 0; k < 3; ++k) {
+      gf[9 * (size_t)g + k] = (float)e1[k];
+      gf[9 * (size_t)g + 3 + k] = (float)e2[k];
+      gf[9 * (size_t)g + 6 + k] = (float)c[k];
+    }
     for (int a = 0; a < s.nr; ++a) {
       const double r = t.gR[g] * std::cos((2.0 * a + 1.0) * kPi / (4.0 * s.nr));
       for (int b = 0; b < s.nth; ++b) {
@@ -759,6 +978,7 @@ void tree_upload(const TreeHost& t, const Precomputed& pc, TreeDevice& d) {
   d.gl_off = t.gl_off;
   d.l2l_off = t.l2l_off;
   chk(up(&d.gpos32, gp32));
+  chk(up(&d.gframe, gf));
   chk(cudaMalloc(&d.grid, std::max<int64_t>(1, d.ngrid) * sizeof(double)));
   chk(cudaMalloc(&d.coef, std::max<int64_t>(1, d.ngrid) * sizeof(double)));
 }
@@ -786,6 +1006,7 @@ void tree_free(TreeDevice& d) {
   d.gl_off.clear();
   d.l2l_off.clear();
   fr(d.gpos32);
+  fr(d.gframe);
   fr(d.grid);
   fr(d.coef);
   d.ngroups = d.nitems = 0;
@@ -821,6 +1042,12 @@ static cudaError_t downward(const TreeDevice& t, cudaStream_t s) {
         if ((e = allow_smem(l2l_df_kernel, sm)) != cudaSuccess) return e;
         count_launch(), l2l_df_kernel<<<nlk, 256, sm, s>>>(l0, t.l2l_child, t.l2l_parent, t.gcen, t.gR, t.gshape, t.goff, t.shape_nr,
                                            t.shape_nth, t.coef, t.gpos64, t.grid);
+      } else if constexpr (std::is_same<R, float>::value) {
+        const size_t sm = (size_t)t.max_q * sizeof(float);
+        if ((e = allow_smem(l2l_f32_kernel, sm)) != cudaSuccess) return e;
+        count_launch(), l2l_f32_kernel<<<nlk, L2L32_THREADS, sm, s>>>(l0, t.l2l_child, t.l2l_parent, t.gcen, t.gR,
+                                                                      t.gframe, t.gshape, t.goff, t.shape_nr,
+                                                                      t.shape_nth, t.coef, t.gpos32, t.grid);
       } else {
         const size_t sm = (size_t)t.max_q * sizeof(R);
         if ((e = allow_smem(l2l_kernel<R>, sm)) != cudaSuccess) return e;
@@ -844,7 +1071,7 @@ static cudaError_t tree_field_impl(const DeviceData& dd, const TreeDevice& t, cu
   if (t.nitems > 0) {
     e = cudaMemsetAsync(t.grid, 0, t.ngrid * sizeof(double), s);
     if (e != cudaSuccess) return e;
-    const size_t smem = (size_t)P2L_JT * dd.pmax * (sizeof(V4) + 4);
+    const size_t smem = (size_t)P2L_JT * dd.pmax * sizeof(V4);
     if ((e = allow_smem(p2l_kernel<R, MODE>, smem)) != cudaSuccess) return e;
     count_launch(), p2l_kernel<R, MODE><<<t.nitems, P2L_THREADS, smem, s>>>(t.witem_group, t.witem_rep, dd.rep_p, dd.rep_off, dd.p,
                                                              t.witem_lo, t.witem_hi, t.isrc, t.gcen, t.gshape, t.goff,
@@ -858,7 +1085,7 @@ static cudaError_t tree_field_impl(const DeviceData& dd, const TreeDevice& t, cu
   }
   if (ev) cudaEventRecord(ev[2], s);
   {
-    const size_t smem = (size_t)DT_JT * dd.pmax * (sizeof(V4) + 4);
+    const size_t smem = (size_t)DT_JT * dd.pmax * sizeof(V4);
     if ((e = allow_smem(direct_list_kernel<R, MODE>, smem)) != cudaSuccess) return e;
     dim3 grid((unsigned)dd.N, (unsigned)((dd.Kstar + DT_THREADS * DT_NT - 1) / (DT_THREADS * DT_NT)));
     count_launch(), direct_list_kernel<R, MODE><<<grid, DT_THREADS, smem, s>>>(dd.p, dd.Kstar, dd.pmax, dd.rep_p, dd.rep_off, t.pd_off, t.pd,
@@ -869,9 +1096,17 @@ static cudaError_t tree_field_impl(const DeviceData& dd, const TreeDevice& t, cu
   if (t.nitems > 0) {
     if (dd.Kstar > 512) return cudaErrorInvalidConfiguration;
     const size_t smem = (size_t)t.max_q * sizeof(R);
-    if ((e = allow_smem(l2p_kernel<R>, smem)) != cudaSuccess) return e;
-    count_launch(), l2p_kernel<R><<<(unsigned)dd.N, 512, smem, s>>>(dd.Kstar, t.pg_off, t.pg, t.gcen, t.gR, t.gshape, t.goff,
-                                                    t.shape_nr, t.shape_nth, t.coef, dd.centres, dd.zloc, dd.z);
+    if constexpr (std::is_same<R, float>::value) {
+      if ((e = allow_smem(l2p_f32_kernel, smem)) != cudaSuccess) return e;
+      count_launch(), l2p_f32_kernel<<<(unsigned)dd.N, L2P32_THREADS, smem, s>>>(
+          dd.Kstar, t.pg_off, t.pg, t.gcen, t.gR, t.gframe, t.gshape, t.goff, t.shape_nr, t.shape_nth, t.coef,
+          dd.centres, dd.zloc, dd.z);
+    } else {
+      if ((e = allow_smem(l2p_kernel<R>, smem)) != cudaSuccess) return e;
+      count_launch(), l2p_kernel<R><<<(unsigned)dd.N, 512, smem, s>>>(dd.Kstar, t.pg_off, t.pg, t.gcen, t.gR, t.gshape,
+                                                                     t.goff, t.shape_nr, t.shape_nth, t.coef,
+                                                                     dd.centres, dd.zloc, dd.z);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (ev) cudaEventRecord(ev[4], s);

@@ -82,6 +82,7 @@ struct TreeDevice {
   int* pdk = nullptr;
   double* gpos64 = nullptr;      // 3*ngrid grid-point offsets from the group centre
   float* gpos32 = nullptr;
+  float* gframe = nullptr;       // 9*G: rows f1, f2, g of each group's frame (FP32)
   int* l2l_child = nullptr;
   int* l2l_parent = nullptr;
   std::vector<int> gl_off, l2l_off;  // host copies of the per-level ranges

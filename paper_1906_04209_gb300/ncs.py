@@ -37,7 +37,8 @@ class ncs_params(ctypes.Structure):
     _fields_ = [("npan", ctypes.c_int), ("nord", ctypes.c_int), ("ntheta_fine", ctypes.c_int),
                 ("id_tol", ctypes.c_double), ("threads", ctypes.c_int), ("grid_tol", ctypes.c_double),
                 ("method", ctypes.c_int), ("tree_min_patches", ctypes.c_int), ("gmres_maxit", ctypes.c_int),
-                ("verbose", ctypes.c_int), ("mixed_residual", ctypes.c_int), ("tensor_cores", ctypes.c_int)]
+                ("verbose", ctypes.c_int), ("mixed_residual", ctypes.c_int), ("tensor_cores", ctypes.c_int),
+                ("residual_update", ctypes.c_int)]
 
 
 class NcsError(RuntimeError):

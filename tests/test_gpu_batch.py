@@ -3,6 +3,7 @@ every instance matches its own single-context solve."""
 import numpy as np
 import pytest
 
+from oracle import operator as O, solve as S
 from paper_1906_04209_gb300 import layouts as L, ncs
 
 pytestmark = pytest.mark.gpu
@@ -33,6 +34,26 @@ def test_batch_matches_individual():
         r = ctx.solve(tol=1e-10, precision=ncs.MIXED)
         assert abs(out["scalar"][b] - r["scalar"]) <= 1e-9 * abs(r["scalar"])
         assert out["relres"][b] <= 1e-10
+
+
+def test_batch_vs_oracle():
+    """Batched mixed-precision solves of uneven spheres (both modes, distinct eps)
+    against the oracle's dense solve of the uncompressed system (eq. opinteqnsdisc)."""
+    g = L.rng(78)
+    inst = []
+    for b, N in enumerate((8, 15, 24, 40)):
+        eps = float(g.uniform(0.03, 0.06))
+        inst.append((L.uniform(N, eps, L.rng(78, b + 1)), eps, b % 2))
+    K, kw = 21, dict(npan=6, nord=10, ntheta_fine=24, method=ncs.METHOD_DIRECT)
+    out = ncs.batch_solve(inst, K, tol=1e-10, precision=ncs.MIXED, workers=2, **kw)
+    assert out["rc"] == 0 and (out["status"] == 0).all()
+    for b, (c, eps, mode) in enumerate(inst):
+        pre = O.make_precompute(eps, mode, K, npan=6, nord=10, ntheta=24, with_id=False)
+        N = len(c)
+        fhat = S.dense_solve(O.dense_operator(pre, c), O.rhs(pre, N))
+        Is, val = S.outputs(pre.op.I, fhat, N, mode)
+        assert abs(out["scalar"][b] - val) <= 1e-8 * abs(val)
+        assert abs(out["Isigma"][b] - Is) <= 1e-8 * abs(Is)
 
 
 def test_block_dots():

@@ -85,6 +85,30 @@ def test_tree_solve_matches_direct(small_pre, mode):
     assert np.abs(rm["fhat"] - rt["fhat"]).max() <= 1e-6 * np.abs(rt["fhat"]).max()
 
 
+@pytest.mark.parametrize("update", [0, 1])
+def test_mixed_solve_true_residual(small_pre, update):
+    """The mixed solve's reported residual is the true one: b - A x recomputed with
+    float-float products after the solve stays within the tolerance, with and without
+    the FP32 residual update of the refinement."""
+    eps = 0.01
+    pre = small_pre(INTERIOR, eps=eps)
+    N = 2500
+    c = L.uniform(N, eps, L.rng(98))
+    ctx = _ctx(pre, method=ncs.METHOD_TREE, grid_tol=1e-10, residual_update=update)
+    ctx.set_patches(c)
+    tol = 1e-9
+    rm = ctx.solve(tol=tol, precision=ncs.MIXED)
+    assert rm["relres"] <= tol
+    b = np.tile(pre.P.sum(axis=1), N)
+    xd = torch.tensor(rm["fhat"], dtype=torch.float64, device="cuda")
+    yd = torch.empty_like(xd)
+    ctx.matvec_dev(xd.data_ptr(), yd.data_ptr(), ncs.DF64, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    true_rel = np.linalg.norm(b - yd.cpu().numpy()) / np.linalg.norm(b)
+    assert true_rel <= 1.05 * tol
+    assert abs(true_rel - rm["relres"]) <= 0.05 * tol
+
+
 def test_full_size_sampled(libncs):
     """The 100 000-patch workload (eps = 0.001, K = 136, jittered Fibonacci, interior):
     tree product in the launch configuration the benchmark times, checked at 48
