@@ -37,6 +37,9 @@ FLOPS_PER_PAIR = 20
 
 
 P2L_BYTES_PER_PAIR = 199.2e6 / 2.2033e10
+# MUFU operations per FP32 pair in the P2L kernel: rsqrt always, log2 on the MUFU unit for
+# 15 pairs in 16 (the 16th takes a polynomial log2 on the FMA pipe)
+MUFU_PER_PAIR = 2.0 - 1.0 / 16.0
 
 
 def _dist():
@@ -235,9 +238,10 @@ def run_ours(args):
 
     peaks, src = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    # ALU roofline of the pair kernel: per pair the FP32 path issues 2 MUFU ops (rsqrt,
-    # log2) and ~10 FP32-pipe ops; 152 SMs x 16 MUFU/clk caps it at 8 pairs/clk/SM.
-    pair_peak = 152 * 8 * sm_max * 1e6 if prec == ncs.FP32 else None
+    # ALU roofline of the pair kernel: per pair the FP32 path issues MUFU_PER_PAIR MUFU
+    # ops (rsqrt, and log2 for all but one pair in 16) and ~11 other instructions;
+    # 152 SMs x 16 MUFU/clk cap it at 16 / MUFU_PER_PAIR pairs/clk/SM.
+    pair_peak = 152 * (16.0 / MUFU_PER_PAIR) * sm_max * 1e6 if prec == ncs.FP32 else None
     p2l_pairs = tstats["p2l_pairs"]
     achieved_pairs = p2l_pairs / (p2l_avg / 1000.0)
     roof = {
@@ -254,7 +258,8 @@ def run_ours(args):
         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum at N=2e4, scaled by pairs",
         "pairs_per_launch": p2l_pairs,
         "ms_per_launch": round(p2l_avg, 3),
-        "peak_source": "derived: 152 SMs x 16 MUFU/clk / 2 MUFU per pair x %g MHz (%s clocks)" % (sm_max, src),
+        "peak_source": "derived: 152 SMs x 16 MUFU/clk / %g MUFU per pair x %g MHz (%s clocks)" % (
+            MUFU_PER_PAIR, sm_max, src),
     }
     cpu = cpu_baseline(args, centres, eps, mode, K) if (rank == 0 and args.cpu_baseline) else None
     line = {

@@ -105,8 +105,8 @@ void free_all(ncs_ctx* c) {
   dev_free(d.rep_off);
   dev_free(d.rep_rho);
   dev_free(d.logtab);
-  dev_free(d.T32);
-  dev_free(d.P32);
+  dev_free(d.Tpack);
+  dev_free(d.Ppack);
   dev_free(d.tc_err);
   if (c->stream) cudaStreamDestroy(c->stream);
   c->stream = nullptr;
@@ -148,8 +148,18 @@ void upload_operator(ncs_ctx* c) {
     for (int m = 0; m < rp[r]; ++m)
       for (int k = 0; k < pc.K; ++k) T32[(size_t)(ro[r] + m) * pc.K + k] = (float)pc.reps[r].T[(size_t)m * pc.K + k];
   std::vector<float> P32(pc.P.begin(), pc.P.end());
-  d.T32 = dev_upload(T32);
-  d.P32 = dev_upload(P32);
+  {
+    // tensor-core operands: TF32 hi/lo blocks packed once on the device
+    float* T32d = dev_upload(T32);
+    float* P32d = dev_upload(P32);
+    d.Tpack = dev_alloc<uint32_t>((size_t)ncs::tc_pack_words(pt, pc.K));
+    d.Ppack = dev_alloc<uint32_t>((size_t)ncs::tc_pack_words(pc.K, pc.Kstar));
+    CU(ncs::launch_tc_pack(T32d, pt, pc.K, d.Tpack, 0));
+    CU(ncs::launch_tc_pack(P32d, pc.K, pc.Kstar, d.Ppack, 0));
+    CU(cudaDeviceSynchronize());
+    dev_free(T32d);
+    dev_free(P32d);
+  }
   d.tc_err = dev_alloc<int>(1);
   CU(cudaMemset(d.tc_err, 0, sizeof(int)));
   d.TT64 = dev_upload(TT);
@@ -246,14 +256,14 @@ void ensure_tree(ncs_ctx* c) {
 
 void outgoing(ncs_ctx* c, const double* x, int prec, cudaStream_t s) {
   if (prec == NCS_FP32 && c->prm.tensor_cores)
-    CU(ncs::launch_tc_outgoing(c->d, x, c->d.T32, c->d.tc_err, s));
+    CU(ncs::launch_tc_outgoing(c->d, x, c->d.tc_err, s));
   else
     CU(ncs::launch_outgoing(c->d, x, prec, s));
 }
 
 void apply_P(ncs_ctx* c, const double* x, double* y, int prec, cudaStream_t s) {
   if (prec == NCS_FP32 && c->prm.tensor_cores)
-    CU(ncs::launch_tc_apply_P(c->d, x, y, c->d.P32, c->d.tc_err, s));
+    CU(ncs::launch_tc_apply_P(c->d, x, y, c->d.tc_err, s));
   else
     CU(ncs::launch_apply_P(c->d, x, y, prec, s));
 }
@@ -969,11 +979,17 @@ int ncs_tc_gemm_f32(int64_t rows, int cols, int kdim, const float* A, const floa
   if (rows < 0 || cols < 0 || kdim < 1 || !A || !B || !D) return NCS_E_INPUT;
   if (rows == 0 || cols == 0) return NCS_OK;
   int* err = nullptr;
+  uint32_t* pack = nullptr;
   if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) return NCS_E_OOM;
+  if (cudaMalloc(&pack, (size_t)ncs::tc_pack_words(cols, kdim) * sizeof(uint32_t)) != cudaSuccess) {
+    cudaFree(err);
+    return NCS_E_OOM;
+  }
   int rc = NCS_OK;
   cudaStream_t s = (cudaStream_t)stream;
   if (cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess ||
-      ncs::launch_tc_gemm_f32(rows, cols, kdim, A, B, D, err, s) != cudaSuccess ||
+      ncs::launch_tc_pack(B, cols, kdim, pack, s) != cudaSuccess ||
+      ncs::launch_tc_gemm_f32(rows, cols, kdim, A, pack, D, err, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess) {
     rc = NCS_E_CUDA;
   } else {
@@ -981,6 +997,7 @@ int ncs_tc_gemm_f32(int64_t rows, int cols, int kdim, const float* A, const floa
     if (cudaMemcpy(&f, err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) rc = NCS_E_CUDA;
     else if (f) rc = NCS_E_TIMEOUT;
   }
+  cudaFree(pack);
   cudaFree(err);
   return rc;
 }

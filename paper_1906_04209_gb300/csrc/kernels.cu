@@ -200,16 +200,16 @@ __global__ void __launch_bounds__(DF_THREADS) direct_field_kernel(
     R part[DF_NT];
 #pragma unroll
     for (int t = 0; t < DF_NT; ++t) part[t] = 0;
-    for (int s = 0; s < ns; ++s) {
-      const V4 v = S[s];
+    if constexpr (sizeof(R) == 4) {
+      pair_loop32<MODE, DF_NT>(S, ns, ax, ay, az, part);
+    } else {
+      for (int s = 0; s < ns; ++s) {
+        const V4 v = S[s];
 #pragma unroll
-      for (int t = 0; t < DF_NT; ++t) {
-        const R dx = ax[t] - v.x, dy = ay[t] - v.y, dz = az[t] - v.z;
-        const R d2 = fma(dx, dx, fma(dy, dy, dz * dz));
-        if constexpr (sizeof(R) == 8)
-          part[t] = fma(green64<MODE>(d2), v.w, part[t]);
-        else
-          part[t] = pair32<MODE>(d2, v.w, part[t]);
+        for (int t = 0; t < DF_NT; ++t) {
+          const R dx = ax[t] - v.x, dy = ay[t] - v.y, dz = az[t] - v.z;
+          part[t] = fma(green64<MODE>(fma(dx, dx, fma(dy, dy, dz * dz))), v.w, part[t]);
+        }
       }
     }
 #pragma unroll

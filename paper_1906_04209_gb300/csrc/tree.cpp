@@ -298,17 +298,18 @@ void build_structure(const std::vector<double>& centres, const TreeOptions& opt,
 }
 
 // Incoming-grid size for a group of radius R whose nearest source is at geodesic
-// distance D from the centre: Fourier modes decay like (R/D)^m and the radial
-// parity-restricted Chebyshev series converges like rho_B^-k with
-// rho_B = rho + sqrt(rho^2 - 1), rho = D/R.
+// distance D from the centre: the angular Fourier coefficients of a point source there
+// decay like (R/D)^m and its radial parity-restricted Chebyshev coefficients like
+// rho_B^-k with rho_B = rho + sqrt(rho^2 - 1), rho = D/R. The grid keeps the modes and
+// degrees up to the first trailing coefficient below tol (Section 7.3).
 GridShape grid_size(double R, double D, double tol) {
   const double rho = D / R;
-  const double lt = std::log(1.0 / (0.1 * tol));
-  int m = (int)std::ceil(lt / std::log(rho)) + 2;
+  const double lt = std::log(1.0 / tol);
+  const int m = (int)std::ceil(lt / std::log(rho));
   int nth = 2 * m + 2;
   nth = (nth + 3) / 4 * 4;
   const double rb = rho + std::sqrt(rho * rho - 1.0);
-  const int d = (int)std::ceil(lt / std::log(rb)) + 2;
+  const int d = (int)std::ceil(lt / std::log(rb));
   int nr = (d + 2) / 2;
   GridShape s;
   s.nr = std::min(64, std::max(2, nr));

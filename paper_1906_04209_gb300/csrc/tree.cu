@@ -51,11 +51,6 @@ void fr(T*& p) {
 constexpr int P2L_THREADS = 256;
 constexpr int P2L_NT = 2;
 constexpr int P2L_JT = 8;
-// FP32 P2L: NCS_P2L_POLYLOG of every 16 pairs (0, 1 or 2) take their logarithm with
-// lg2_poly on the FMA pipe instead of the MUFU unit, which otherwise bounds the pair rate.
-#ifndef NCS_P2L_POLYLOG
-#define NCS_P2L_POLYLOG 0
-#endif
 
 // One block per work item (grid group g, a slice of its interaction-list patches).
 template <typename R, int MODE>
@@ -127,48 +122,19 @@ __global__ void __launch_bounds__(P2L_THREADS) p2l_kernel(
       // warps whose every target slot lies beyond the grid skip the pair work
       const int wbase = base + (threadIdx.x & ~31);
       const int nact = (wbase >= q) ? 0 : ((wbase + P2L_THREADS >= q) ? 1 : P2L_NT);
-      if (nact == P2L_NT) {
-        int s = 0;
-        if constexpr (sizeof(R) == 4 && NCS_P2L_POLYLOG > 0) {
-          // sources in groups of 8: the last source of a group takes lg2_poly for its
-          // first NCS_P2L_POLYLOG target slots (1 or 2 of the group's 16 pairs)
-          for (; s + 8 <= ns; s += 8) {
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-              const V4 v = S[s + u];
-#pragma unroll
-              for (int t = 0; t < P2L_NT; ++t) {
-                const R dx = ax[t] - v.x, dy = ay[t] - v.y, dz = az[t] - v.z;
-                const R d2 = fma(dx, dx, fma(dy, dy, dz * dz));
-                if (u == 7 && t < NCS_P2L_POLYLOG)
-                  part[t] = pair32_poly<MODE>(d2, v.w, part[t]);
-                else
-                  part[t] = pair32<MODE>(d2, v.w, part[t]);
-              }
-            }
-          }
-        }
-        for (; s < ns; ++s) {
+      if constexpr (sizeof(R) == 4) {
+        if (nact == P2L_NT)
+          pair_loop32<MODE, P2L_NT>(S, ns, ax, ay, az, part);
+        else if (nact == 1)
+          pair_loop32<MODE, 1>(S, ns, ax, ay, az, part);
+      } else if (nact > 0) {
+        for (int s = 0; s < ns; ++s) {
           const V4 v = S[s];
 #pragma unroll
           for (int t = 0; t < P2L_NT; ++t) {
             const R dx = ax[t] - v.x, dy = ay[t] - v.y, dz = az[t] - v.z;
-            const R d2 = fma(dx, dx, fma(dy, dy, dz * dz));
-            if constexpr (sizeof(R) == 8)
-              part[t] = fma(green64<MODE>(d2), v.w, part[t]);
-            else
-              part[t] = pair32<MODE>(d2, v.w, part[t]);
+            part[t] = fma(green64<MODE>(fma(dx, dx, fma(dy, dy, dz * dz))), v.w, part[t]);
           }
-        }
-      } else if (nact == 1) {
-        for (int s = 0; s < ns; ++s) {
-          const V4 v = S[s];
-          const R dx = ax[0] - v.x, dy = ay[0] - v.y, dz = az[0] - v.z;
-          const R d2 = fma(dx, dx, fma(dy, dy, dz * dz));
-          if constexpr (sizeof(R) == 8)
-            part[0] = fma(green64<MODE>(d2), v.w, part[0]);
-          else
-            part[0] = pair32<MODE>(d2, v.w, part[0]);
         }
       }
 #pragma unroll
@@ -305,16 +271,16 @@ __global__ void __launch_bounds__(DT_THREADS) direct_list_kernel(
     R part[DT_NT];
 #pragma unroll
     for (int t = 0; t < DT_NT; ++t) part[t] = 0;
-    for (int s = 0; s < ns; ++s) {
-      const V4 v = S[s];
+    if constexpr (sizeof(R) == 4) {
+      pair_loop32<MODE, DT_NT>(S, ns, ax, ay, az, part);
+    } else {
+      for (int s = 0; s < ns; ++s) {
+        const V4 v = S[s];
 #pragma unroll
-      for (int t = 0; t < DT_NT; ++t) {
-        const R dx = ax[t] - v.x, dy = ay[t] - v.y, dz = az[t] - v.z;
-        const R d2 = fma(dx, dx, fma(dy, dy, dz * dz));
-        if constexpr (sizeof(R) == 8)
-          part[t] = fma(green64<MODE>(d2), v.w, part[t]);
-        else
-          part[t] = pair32<MODE>(d2, v.w, part[t]);
+        for (int t = 0; t < DT_NT; ++t) {
+          const R dx = ax[t] - v.x, dy = ay[t] - v.y, dz = az[t] - v.z;
+          part[t] = fma(green64<MODE>(fma(dx, dx, fma(dy, dy, dz * dz))), v.w, part[t]);
+        }
       }
     }
 #pragma unroll

@@ -66,6 +66,24 @@ def test_tree_vs_compressed_sums(small_pre, mode):
     assert np.abs(zd - ref).max() <= 1e-12 * scale
 
 
+@pytest.mark.parametrize("layout", ["uniform", "vmf"])
+def test_default_grid_tolerance(small_pre, layout):
+    """At the default incoming-grid tolerance (1e-8) the tree product stays within 1e-8
+    of the oracle's compressed sums (grid sizes from the trailing-coefficient rule)."""
+    eps = 0.01
+    pre = small_pre(INTERIOR, eps=eps)
+    N = 4000
+    c = L.uniform(N, eps, L.rng(99)) if layout == "uniform" else L.vmf_clusters(N, eps, L.rng(99))
+    x = np.random.default_rng(19).standard_normal(N * pre.K)
+    ctx = _ctx(pre, method=ncs.METHOD_TREE)
+    ctx.set_patches(c)
+    assert ctx.tree_stats()["grid_groups"] > 0
+    patches = np.random.default_rng(20).choice(N, 12, replace=False)
+    ref = O.id_field(pre, c, x, patches)
+    z64 = _field(ctx, x, ncs.FP64, N, pre.Kstar)[patches]
+    assert np.abs(z64 - ref).max() <= 1e-8 * np.abs(ref).max()
+
+
 @pytest.mark.parametrize("mode", [EXTERIOR, INTERIOR])
 def test_tree_solve_matches_direct(small_pre, mode):
     eps = 0.01
