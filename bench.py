@@ -228,7 +228,10 @@ def run_ours(args):
     solve = None
     if args.solve:
         solve = {}
-        for name, p in (("mixed", ncs.MIXED), ("fp64", ncs.FP64)):
+        # mixed: FP32 inner GMRES + float-float residual; df64: every product in float-float
+        # (FP64-accurate on the FP32 pipes); fp64: every product on the FP64 pipe (slow on
+        # this part, only with --solve-fp64)
+        for name, p in (("mixed", ncs.MIXED), ("df64", ncs.DF64), ("fp64", ncs.FP64)):
             if name == "fp64" and not args.solve_fp64:
                 continue
             t0 = time.time()
@@ -352,7 +355,7 @@ def main():
     ap.add_argument("--solve", action="store_true")
     # a smaller layout of the same family (profiler captures only; the line names its N)
     ap.add_argument("--patches", type=int, default=None)
-    ap.add_argument("--tensor-cores", type=int, default=0, choices=[0, 1])
+    ap.add_argument("--tensor-cores", type=int, default=1, choices=[0, 1])
     ap.add_argument("--solve-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

@@ -78,13 +78,19 @@ typedef struct ncs_params {
   int verbose;         /* 0 silent .. 3 chatty (stderr) */
   int mixed_residual;  /* precision of the refinement residual of NCS_MIXED:
                           NCS_DF64 (default) or NCS_FP64 */
-  int tensor_cores;    /* 1: the FP32 product runs its dense contractions
-                          (rho = T x, y = x + P z) on the tcgen05 tensor cores (3xTF32);
-                          0 (default): FP32 SIMT kernels */
+  int tensor_cores;    /* 1 (default): the FP32 product runs its dense contractions
+                          (rho = T x, y = x + P z) on the tcgen05 tensor cores (3xTF32
+                          splits, ~2^-22 per operand: product error a few 1e-6 relative);
+                          0: FP32 SIMT kernels (~1e-6) */
   int residual_update; /* NCS_MIXED: 1 (default) forms the refinement residual as
                           r - A corr with an FP32 product once |r| <= 1e-4 |b| (its error,
                           ~1e-6 |r|, is then below 1e-10 |b|); 0 always recomputes
                           b - A x at mixed_residual precision */
+  double id_ladder_max;/* largest far-field radius (radians) for which an extra, smaller ID
+                          representation is built (far fields beyond 2, 3, 4, 6, 8, ... eps;
+                          Section 7.1 recompression), default 1.0; 0: only the 2 eps one.
+                          Fewer representations shorten the host precompute (one CPQR of
+                          the sketch per representation) and lengthen the products */
 } ncs_params;
 
 /* Fills *p with the defaults listed above. */

@@ -79,6 +79,7 @@ void free_layout(ncs_ctx* c) {
   dev_free(d.rho64);
   dev_free(d.rho32);
   dev_free(d.z);
+  dev_free(d.Apack);
   dev_free(c->V);
   dev_free(c->work);
   dev_free(c->partial);
@@ -152,10 +153,10 @@ void upload_operator(ncs_ctx* c) {
     // tensor-core operands: TF32 hi/lo blocks packed once on the device
     float* T32d = dev_upload(T32);
     float* P32d = dev_upload(P32);
-    d.Tpack = dev_alloc<uint32_t>((size_t)ncs::tc_pack_words(pt, pc.K));
-    d.Ppack = dev_alloc<uint32_t>((size_t)ncs::tc_pack_words(pc.K, pc.Kstar));
-    CU(ncs::launch_tc_pack(T32d, pt, pc.K, d.Tpack, 0));
-    CU(ncs::launch_tc_pack(P32d, pc.K, pc.Kstar, d.Ppack, 0));
+    d.Tpack = dev_alloc<uint32_t>((size_t)ncs::tc_pack_words(pt, pc.K, ncs::tc_block_cols(pt)));
+    d.Ppack = dev_alloc<uint32_t>((size_t)ncs::tc_pack_words(pc.K, pc.Kstar, ncs::tc_block_cols(pc.K)));
+    CU(ncs::launch_tc_pack_b(T32d, pt, pc.K, d.Tpack, 0));
+    CU(ncs::launch_tc_pack_b(P32d, pc.K, pc.Kstar, d.Ppack, 0));
     CU(cudaDeviceSynchronize());
     dev_free(T32d);
     dev_free(P32d);
@@ -217,6 +218,8 @@ void ensure_layout(ncs_ctx* c) {
   d.rho64 = dev_alloc<double>((size_t)N * d.p);
   d.rho32 = dev_alloc<float>((size_t)N * d.p);
   d.z = dev_alloc<double>((size_t)N * d.Kstar);
+  if (c->prm.tensor_cores)  // TF32 hi/lo blocks of x or z for the tensor-core GEMMs
+    d.Apack = dev_alloc<uint32_t>((size_t)ncs::tc_pack_words(N, std::max(d.K, d.Kstar), 128));
   d.N = N;
   CU(ncs::launch_skeleton_offsets(d, c->stream));
   CU(cudaStreamSynchronize(c->stream));
@@ -441,6 +444,7 @@ ncs_ctx* new_ctx(const ncs_params* params) {
 void validate_params(const ncs_params& p) {
   if (p.npan < 2 || p.npan > 40 || p.nord < 2 || p.nord > 64) throw Fail{NCS_E_INPUT, "bad panel parameters"};
   if (!(p.id_tol > 0.0 && p.id_tol < 1e-2)) throw Fail{NCS_E_INPUT, "id_tol out of range"};
+  if (!(p.id_ladder_max >= 0.0 && p.id_ladder_max <= 4.0)) throw Fail{NCS_E_INPUT, "id_ladder_max out of range"};
   if (!(p.grid_tol > 0.0 && p.grid_tol < 1e-1)) throw Fail{NCS_E_INPUT, "grid_tol out of range"};
   if (p.gmres_maxit < 1 || p.gmres_maxit > 2000) throw Fail{NCS_E_INPUT, "gmres_maxit out of range"};
   if (p.method < 0 || p.method > 2) throw Fail{NCS_E_INPUT, "bad method"};
@@ -465,8 +469,9 @@ void ncs_default_params(ncs_params* p) {
   p->gmres_maxit = 200;
   p->verbose = 0;
   p->mixed_residual = NCS_DF64;
-  p->tensor_cores = 0;
+  p->tensor_cores = 1;
   p->residual_update = 1;
+  p->id_ladder_max = 1.0;
 }
 
 int ncs_create(double eps, int mode, int K, const ncs_params* params, ncs_ctx** out) {
@@ -485,6 +490,7 @@ int ncs_create(double eps, int mode, int K, const ncs_params* params, ncs_ctx** 
     o.ntheta_fine = c->prm.ntheta_fine;
     o.id_tol = c->prm.id_tol;
     o.threads = c->prm.threads;
+    o.id_ladder_max = c->prm.id_ladder_max;
     try {
       ncs::precompute(eps, mode, K, o, c->pc);
     } catch (const std::exception& e) {
@@ -979,17 +985,20 @@ int ncs_tc_gemm_f32(int64_t rows, int cols, int kdim, const float* A, const floa
   if (rows < 0 || cols < 0 || kdim < 1 || !A || !B || !D) return NCS_E_INPUT;
   if (rows == 0 || cols == 0) return NCS_OK;
   int* err = nullptr;
-  uint32_t* pack = nullptr;
+  uint32_t *pack = nullptr, *apack = nullptr;
   if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) return NCS_E_OOM;
-  if (cudaMalloc(&pack, (size_t)ncs::tc_pack_words(cols, kdim) * sizeof(uint32_t)) != cudaSuccess) {
+  if (cudaMalloc(&pack, (size_t)ncs::tc_pack_words(cols, kdim, ncs::tc_block_cols(cols)) * sizeof(uint32_t)) !=
+          cudaSuccess ||
+      cudaMalloc(&apack, (size_t)ncs::tc_pack_words(rows, kdim, 128) * sizeof(uint32_t)) != cudaSuccess) {
+    cudaFree(pack);
     cudaFree(err);
     return NCS_E_OOM;
   }
   int rc = NCS_OK;
   cudaStream_t s = (cudaStream_t)stream;
   if (cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess ||
-      ncs::launch_tc_pack(B, cols, kdim, pack, s) != cudaSuccess ||
-      ncs::launch_tc_gemm_f32(rows, cols, kdim, A, pack, D, err, s) != cudaSuccess ||
+      ncs::launch_tc_pack_b(B, cols, kdim, pack, s) != cudaSuccess ||
+      ncs::launch_tc_gemm_f32(rows, cols, kdim, A, apack, pack, D, err, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess) {
     rc = NCS_E_CUDA;
   } else {
@@ -997,6 +1006,7 @@ int ncs_tc_gemm_f32(int64_t rows, int cols, int kdim, const float* A, const floa
     if (cudaMemcpy(&f, err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) rc = NCS_E_CUDA;
     else if (f) rc = NCS_E_TIMEOUT;
   }
+  cudaFree(apack);
   cudaFree(pack);
   cudaFree(err);
   return rc;

@@ -137,7 +137,9 @@ __device__ __forceinline__ f2 green_f2(f2 d2, const float4* __restrict__ tab) {
 }
 
 // acc += G * rho for one pair in float-float: target offset a (3 float-float words),
-// source (hi, lo) quadruples (offset, strength).
+// source (hi, lo) quadruples (offset, strength). The sum is compensated (Ogita, Rump and
+// Oishi's Sum2): acc.hi is the running FP32 sum, acc.lo collects every rounding error by
+// TwoSum plus the low words, and the caller folds hi + lo into FP64 per tile.
 template <int MODE>
 __device__ __forceinline__ void pair_f2_acc(const f2* a, float4 sh, float4 sl, const float4* __restrict__ tab,
                                             f2& acc) {
@@ -155,7 +157,10 @@ __device__ __forceinline__ void pair_f2_acc(const f2* a, float4 sh, float4 sl, c
   lo = fmaf(fmaf(2.0f, dy.hi, dy.lo), dy.lo, lo);
   lo = fmaf(fmaf(2.0f, dz.hi, dz.lo), dz.lo, lo);
   const f2 d2 = fast_two_sum(s2.hi, lo);
-  acc = f2_add_sloppy(acc, f2_mul(green_f2<MODE>(d2, tab), f2{sh.w, sl.w}));
+  const f2 g = f2_mul(green_f2<MODE>(d2, tab), f2{sh.w, sl.w});
+  const f2 t = two_sum(acc.hi, g.hi);
+  acc.hi = t.hi;
+  acc.lo += t.lo + g.lo;
 }
 
 }  // namespace ncs

@@ -45,6 +45,7 @@ struct DeviceData {
   float4* logtab = nullptr;    // 64 x (log c hi, lo, 1/c hi, lo), c = 1 + (i + 0.5)/64
   uint32_t* Tpack = nullptr;   // all T_k stacked (p x K), TF32 hi/lo tensor-core blocks
   uint32_t* Ppack = nullptr;   // P (K x Kstar), TF32 hi/lo tensor-core blocks
+  uint32_t* Apack = nullptr;   // x or z of one product as TF32 hi/lo blocks (tensor_cores only)
   int* tc_err = nullptr;       // set by a tensor-core kernel whose bounded wait gave up
 };
 
@@ -57,15 +58,17 @@ cudaError_t launch_eval(const DeviceData& d, int mode, int64_t M, const double* 
                         double* out, cudaStream_t s);
 
 // ---- tensor-core GEMMs (tc_gemm.cu)
-// B operands are packed once into TF32 hi/lo blocks (launch_tc_pack, tc_pack_words
-// 32-bit words for a cols x Kd row-major FP32 matrix).
+// Operands of the tensor-core GEMMs as TF32 hi/lo blocks in the shared-memory layout:
+// tc_pack_words 32-bit words for nrows x Kd in row tiles of H; B operands (the constant
+// operators) use tiles of tc_block_cols(cols) and are packed once by launch_tc_pack_b,
+// A operands (x, z) use tiles of 128 and are packed by each GEMM launcher.
 int tc_block_cols(int cols);
-int64_t tc_pack_words(int cols, int Kd);
-cudaError_t launch_tc_pack(const float* B, int cols, int Kd, uint32_t* out, cudaStream_t s);
+int64_t tc_pack_words(int64_t nrows, int Kd, int H);
+cudaError_t launch_tc_pack_b(const float* B, int cols, int Kd, uint32_t* out, cudaStream_t s);
 cudaError_t launch_tc_outgoing(const DeviceData& d, const double* x, int* err, cudaStream_t s);
 cudaError_t launch_tc_apply_P(const DeviceData& d, const double* x, double* y, int* err, cudaStream_t s);
-cudaError_t launch_tc_gemm_f32(int64_t rows, int cols, int Kd, const float* A, const uint32_t* Bpack, float* D,
-                               int* err, cudaStream_t s);
+cudaError_t launch_tc_gemm_f32(int64_t rows, int cols, int Kd, const float* A, uint32_t* Apack,
+                               const uint32_t* Bpack, float* D, int* err, cudaStream_t s);
 
 // ---- dense-vector kernels for GMRES (blas.cu)
 cudaError_t launch_dots(int64_t n, int k, const double* V, int64_t ld, const double* w,

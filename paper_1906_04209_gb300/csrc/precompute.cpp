@@ -600,20 +600,32 @@ void precompute(double eps, int mode, int K, const PrecomputeOptions& opt, Preco
 #pragma omp for schedule(dynamic, 1)
         for (int cb = 0; cb < (nf + CB - 1) / CB; ++cb) {
           const int l0 = cb * CB, nl = std::min(CB, nf - l0);
-          for (int j = 0; j < nrw; ++j)
-            for (int c = 0; c < nl; ++c) {
+          // kernel block stored column by column (Ab[c][j]) so that the sketch update
+          // below runs over contiguous rows of Omega and of the block
+          for (int c = 0; c < nl; ++c) {
+            const double* bp = &xf[3 * (size_t)(l0 + c)];
+            double* ac = &Ab[(size_t)c * nrw];
+            for (int j = 0; j < nrw; ++j) {
               const double* a = &xt[3 * (size_t)(r0 + j)];
-              const double* b = &xf[3 * (size_t)(l0 + c)];
-              const double dx = a[0] - b[0], dy = a[1] - b[1], dz = a[2] - b[2];
-              Ab[(size_t)j * CB + c] = Gsurf(std::sqrt(dx * dx + dy * dy + dz * dz));
+              const double dx = a[0] - bp[0], dy = a[1] - bp[1], dz = a[2] - bp[2];
+              ac[j] = Gsurf(std::sqrt(dx * dx + dy * dy + dz * dz));
             }
+          }
           for (int c = 0; c < nl; ++c) {
             double* ycol = &Yrun[(size_t)(l0 + c) * ks];
+            const double* ac = &Ab[(size_t)c * nrw];
             for (int r = 0; r < ks; ++r) {
               const double* om = &Om[(size_t)r * nt + r0];
-              double v = 0.0;
-              for (int j = 0; j < nrw; ++j) v += om[j] * Ab[(size_t)j * CB + c];
-              ycol[r] += v;
+              double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+              int j = 0;
+              for (; j + 4 <= nrw; j += 4) {
+                v0 += om[j] * ac[j];
+                v1 += om[j + 1] * ac[j + 1];
+                v2 += om[j + 2] * ac[j + 2];
+                v3 += om[j + 3] * ac[j + 3];
+              }
+              for (; j < nrw; ++j) v0 += om[j] * ac[j];
+              ycol[r] += (v0 + v1) + (v2 + v3);
             }
           }
         }

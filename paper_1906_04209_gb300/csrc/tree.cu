@@ -50,7 +50,11 @@ void fr(T*& p) {
 
 constexpr int P2L_THREADS = 256;
 constexpr int P2L_NT = 2;
-constexpr int P2L_JT = 8;
+// source patches staged per shared-memory tile of a P2L work item
+#ifndef NCS_P2L_JT
+#define NCS_P2L_JT 16
+#endif
+constexpr int P2L_JT = NCS_P2L_JT;
 
 // One block per work item (grid group g, a slice of its interaction-list patches).
 template <typename R, int MODE>

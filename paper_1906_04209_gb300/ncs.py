@@ -38,7 +38,7 @@ class ncs_params(ctypes.Structure):
                 ("id_tol", ctypes.c_double), ("threads", ctypes.c_int), ("grid_tol", ctypes.c_double),
                 ("method", ctypes.c_int), ("tree_min_patches", ctypes.c_int), ("gmres_maxit", ctypes.c_int),
                 ("verbose", ctypes.c_int), ("mixed_residual", ctypes.c_int), ("tensor_cores", ctypes.c_int),
-                ("residual_update", ctypes.c_int)]
+                ("residual_update", ctypes.c_int), ("id_ladder_max", ctypes.c_double)]
 
 
 class NcsError(RuntimeError):

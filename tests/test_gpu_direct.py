@@ -31,15 +31,22 @@ def _field_gpu(ctx, x, prec, N, Kstar):
     return zd.cpu().numpy().reshape(N, Kstar)
 
 
+# FP32 field tolerance relative to max |z|: SIMT outgoing map ~FP32 rounding; the 3xTF32
+# tensor-core map splits each operand into TF32 hi + lo (2^-22 relative per operand), so
+# its coefficients, and the field, carry a few times more error.
+FP32_TOL = {0: 2e-6, 1: 6e-6}
+
+
+@pytest.mark.parametrize("tc", [0, 1])
 @pytest.mark.parametrize("mode", [EXTERIOR, INTERIOR])
 @pytest.mark.parametrize("N", [1, 2, 9, 37])
-def test_field_parity_shared_operator(small_pre, mode, N):
+def test_field_parity_shared_operator(small_pre, mode, N, tc):
     """Same operator data on both sides: GPU z vs oracle compressed sums, element by
     element. N = 9 and 37 leave ragged source tiles (8 patches per tile)."""
     pre = small_pre(mode)
     c = L.uniform(N, 0.1, L.rng(91, N))
     x = np.random.default_rng(N).standard_normal(N * pre.K)
-    ctx = _ctx_from_oracle(pre, method=ncs.METHOD_DIRECT)
+    ctx = _ctx_from_oracle(pre, method=ncs.METHOD_DIRECT, tensor_cores=tc)
     ctx.set_patches(c)
     ref = O.id_field(pre, c, x)
     scale = max(np.abs(ref).max(), 1e-300)
@@ -51,7 +58,7 @@ def test_field_parity_shared_operator(small_pre, mode, N):
         return
     assert np.abs(z64 - ref).max() <= 1e-12 * scale
     assert np.abs(zdf - ref).max() <= 1e-12 * scale
-    assert np.abs(z32 - ref).max() <= 2e-6 * scale
+    assert np.abs(z32 - ref).max() <= FP32_TOL[tc] * scale
 
 
 @pytest.mark.parametrize("mode", [EXTERIOR, INTERIOR])

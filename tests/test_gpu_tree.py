@@ -53,11 +53,13 @@ def test_tree_vs_compressed_sums(small_pre, mode):
     z32 = _field(ctx, x, ncs.FP32, N, pre.Kstar)[patches]
     n1 = ncs.launch_count()
     _field(ctx, x, ncs.FP32, N, pre.Kstar)
-    # outgoing, P2L, direct lists, L2P, plus one coefficient and at most one L2L launch per level
+    # outgoing (pack + tensor-core GEMM), P2L, direct lists, L2P, plus one coefficient and
+    # at most one L2L launch per level
     assert n1 - n0 == ncs.launch_count() - n1
-    assert 4 + 1 <= n1 - n0 <= 4 + 2 * st["levels"]
+    assert 5 + 1 <= n1 - n0 <= 5 + 2 * st["levels"]
     assert np.abs(z64 - ref).max() <= 1e-8 * scale
-    assert np.abs(z32 - ref).max() <= 5e-6 * scale
+    # FP32 pair sums with the 3xTF32 outgoing map (a few 1e-6, see the direct parity test)
+    assert np.abs(z32 - ref).max() <= 8e-6 * scale
     # float-float tree product = FP64 tree product to rounding (same grids, same lists)
     assert np.abs(zfdf - zf64).max() <= 1e-12 * np.abs(zf64).max()
     # the direct product on the same context agrees as well

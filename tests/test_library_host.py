@@ -81,3 +81,19 @@ def test_set_patches_validation(libncs):
 def test_launch_count_without_gpu(libncs):
     # no kernel has been launched by the CPU-only tests; the counter is readable anyway
     assert ncs.launch_count() >= 0
+
+
+def test_id_ladder_max(libncs):
+    """id_ladder_max = 0 keeps only the far-field-beyond-2-eps representation; a larger
+    radius adds the ladder (more, smaller representations, decreasing p)."""
+    kw = dict(npan=6, nord=10, ntheta_fine=24)
+    one = ncs.Context(0.05, INTERIOR, 10, id_ladder_max=0.0, **kw)
+    rm1, p1 = one.reps()
+    assert len(p1) == 1 and abs(rm1[0] - 2 * 0.05) < 1e-12
+    lad = ncs.Context(0.05, INTERIOR, 10, id_ladder_max=0.5, **kw)
+    rm, ps = lad.reps()
+    assert len(ps) > 1 and ps[0] == p1[0]
+    assert all(ps[i] >= ps[i + 1] for i in range(len(ps) - 1))
+    assert rm.max() <= 0.5 + 1e-12
+    with pytest.raises(ncs.NcsError):
+        ncs.Context(0.05, INTERIOR, 10, id_ladder_max=-1.0, **kw)
