@@ -36,7 +36,7 @@ WORKLOAD = "interior narrow escape, N=100000 patches, eps=0.001, K=136, jittered
 FLOPS_PER_PAIR = 20
 
 
-P2L_BYTES_PER_PAIR = 155.5e6 / 1.5108e10
+P2L_BYTES_PER_PAIR = 156.0e6 / 1.5108e10
 # MUFU operations per FP32 pair in the P2L kernel: rsqrt always, log2 on the MUFU unit for
 # 15 pairs in 16 (the 16th takes a polynomial log2 on the FMA pipe)
 MUFU_PER_PAIR = 2.0 - 1.0 / 16.0
@@ -255,7 +255,7 @@ def run_ours(args):
         "unit": "TFLOP/s",
         "frac": round(achieved_pairs / pair_peak, 4) if pair_peak else None,
         # DRAM bytes per launch: an ncu capture of this kernel on the N = 2e4 layout of the
-        # same family measured 155.5 MB for 1.5108e10 pairs; the P2L reads scale with its
+        # same family measured 156.0 MB for 1.5108e10 pairs; the P2L reads scale with its
         # work items, so it is scaled by the pair ratio (null for other precisions)
         "traffic": round(P2L_BYTES_PER_PAIR * p2l_pairs) if prec == ncs.FP32 else None,
         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum at N=2e4, scaled by pairs",

@@ -55,6 +55,9 @@ constexpr int P2L_NT = 2;
 #define NCS_P2L_JT 16
 #endif
 constexpr int P2L_JT = NCS_P2L_JT;
+// the float-float P2L stages (hi, lo) pairs of float4: 8 patches per tile keep its shared
+// memory (43 KB at p = 169) at the FP32 kernel's, and its blocks per SM with it
+constexpr int P2L_DF_JT = 8;
 
 // One block per work item (grid group g, a slice of its interaction-list patches).
 template <typename R, int MODE>
@@ -628,13 +631,13 @@ __global__ void __launch_bounds__(P2L_THREADS) p2l_df_kernel(
     const double* __restrict__ rho, const float4* __restrict__ logtab, double* __restrict__ grid) {
   extern __shared__ float4 p2d_smem[];
   __shared__ float4 tab[kLogTable];
-  __shared__ double D[P2L_JT][3];
+  __shared__ double D[P2L_DF_JT][3];
   const int item = blockIdx.x;
   const int g = witem_group[item];
   const int rk = witem_rep[item];
   const int p = rep_p[rk], col = rep_off[rk];
   float4* Sh = p2d_smem;
-  float4* Sl = p2d_smem + P2L_JT * p;
+  float4* Sl = p2d_smem + P2L_DF_JT * p;
   for (int t = threadIdx.x; t < kLogTable; t += blockDim.x) tab[t] = logtab[t];
   const int64_t lo = witem_lo[item], hi = witem_hi[item];
   const int sh = gshape[g];
@@ -651,8 +654,8 @@ __global__ void __launch_bounds__(P2L_THREADS) p2l_df_kernel(
       for (int c = 0; c < 3; ++c) a[t][c] = f2_from_double(ap < q ? gpos[3 * (off + ap) + c] : 0.0);
       acc[t] = 0.0;
     }
-    for (int64_t s0 = lo; s0 < hi; s0 += P2L_JT) {
-      const int nj = (int)min((int64_t)P2L_JT, hi - s0);
+    for (int64_t s0 = lo; s0 < hi; s0 += P2L_DF_JT) {
+      const int nj = (int)min((int64_t)P2L_DF_JT, hi - s0);
       __syncthreads();
       if (threadIdx.x < nj * 3) {
         const int jj = threadIdx.x / 3, c = threadIdx.x - 3 * jj;
@@ -1089,7 +1092,7 @@ static cudaError_t tree_field_df(const DeviceData& dd, const TreeDevice& t, cuda
   if (ev) cudaEventRecord(ev[0], s);
   if (t.nitems > 0) {
     if ((e = cudaMemsetAsync(t.grid, 0, t.ngrid * sizeof(double), s)) != cudaSuccess) return e;
-    const size_t smem = (size_t)2 * P2L_JT * dd.pmax * sizeof(float4);
+    const size_t smem = (size_t)2 * P2L_DF_JT * dd.pmax * sizeof(float4);
     if ((e = allow_smem(p2l_df_kernel<MODE>, smem)) != cudaSuccess) return e;
     count_launch(), p2l_df_kernel<MODE><<<t.nitems, P2L_THREADS, smem, s>>>(t.witem_group, t.witem_rep, dd.rep_p, dd.rep_off, dd.p,
                                                            t.witem_lo, t.witem_hi, t.isrc, t.gcen, t.gshape, t.goff,
