@@ -91,6 +91,10 @@ typedef struct ncs_params {
                           Section 7.1 recompression), default 1.0; 0: only the 2 eps one.
                           Fewer representations shorten the host precompute (one CPQR of
                           the sketch per representation) and lengthen the products */
+  int device_precompute;/* 1 (default): the precompute forms its ID sketch (a Gaussian
+                          sketch of the far-field kernel matrix, ~1e10 FP64 FMAs) on the
+                          CUDA device current at ncs_create when there is one, else on the
+                          host; 0: always on the host */
 } ncs_params;
 
 /* Fills *p with the defaults listed above. */
@@ -137,6 +141,14 @@ int ncs_create_from_operators(double eps, int mode, int K, int nrep, const doubl
 int ncs_get_reps(const ncs_ctx* ctx, int* nrep, double* rho_min, int* p);
 
 /*
+ * Representation r (0 <= r < nrep) of the outgoing operator (Section 7.1, eq. Tmap with
+ * the far field beyond rho_min[r]): T (p_r x K row-major) and the skeleton points' local
+ * polar coordinates skel_t, skel_theta (p_r each), copied into caller arrays; any
+ * pointer may be NULL. Errors: NCS_E_INPUT (bad r or context).
+ */
+int ncs_get_rep(const ncs_ctx* ctx, int r, double* T, double* skel_t, double* skel_theta);
+
+/*
  * Writes context sizes into out[0..n): K, Kstar, p, M, nf (fine-grid points),
  * N (patches set, 0 if none), nrad (radial nodes), tree levels (0 if no tree),
  * grid points over all tree groups, pair evaluations per tree matvec (FP counts
@@ -144,7 +156,8 @@ int ncs_get_reps(const ncs_ctx* ctx, int* nrep, double* rho_min, int* p);
  */
 int ncs_info(const ncs_ctx* ctx, int64_t* out, int n);
 
-/* Precompute timings in seconds: out[0] one-patch solve, out[1] ID. */
+/* Precompute timings in seconds: out[0] one-patch solve, out[1] ID; out[2] = 1 if the ID
+ * sketch ran on a CUDA device, else 0. */
 int ncs_timings(const ncs_ctx* ctx, double* out, int n);
 
 /*

@@ -472,6 +472,7 @@ void ncs_default_params(ncs_params* p) {
   p->tensor_cores = 1;
   p->residual_update = 1;
   p->id_ladder_max = 1.0;
+  p->device_precompute = 1;
 }
 
 int ncs_create(double eps, int mode, int K, const ncs_params* params, ncs_ctx** out) {
@@ -491,6 +492,7 @@ int ncs_create(double eps, int mode, int K, const ncs_params* params, ncs_ctx** 
     o.id_tol = c->prm.id_tol;
     o.threads = c->prm.threads;
     o.id_ladder_max = c->prm.id_ladder_max;
+    o.device_sketch = c->prm.device_precompute != 0;
     try {
       ncs::precompute(eps, mode, K, o, c->pc);
     } catch (const std::exception& e) {
@@ -597,6 +599,15 @@ int ncs_get_reps(const ncs_ctx* c, int* nrep, double* rho_min, int* p) {
   return NCS_OK;
 }
 
+int ncs_get_rep(const ncs_ctx* c, int r, double* T, double* skel_t, double* skel_theta) {
+  if (!c || r < 0 || r >= (int)c->pc.reps.size()) return NCS_E_INPUT;
+  const ncs::OutRep& rep = c->pc.reps[r];
+  if (T) std::memcpy(T, rep.T.data(), rep.T.size() * sizeof(double));
+  if (skel_t) std::memcpy(skel_t, rep.st.data(), rep.st.size() * sizeof(double));
+  if (skel_theta) std::memcpy(skel_theta, rep.sth.data(), rep.sth.size() * sizeof(double));
+  return NCS_OK;
+}
+
 int ncs_info(const ncs_ctx* c, int64_t* out, int n) {
   if (!c || !out) return NCS_E_INPUT;
   const int64_t v[11] = {c->pc.K,
@@ -619,6 +630,7 @@ int ncs_timings(const ncs_ctx* c, double* out, int n) {
   if (!c || !out) return NCS_E_INPUT;
   if (n > 0) out[0] = c->pc.seconds_onepatch;
   if (n > 1) out[1] = c->pc.seconds_id;
+  if (n > 2) out[2] = c->pc.sketch_on_device ? 1.0 : 0.0;
   return NCS_OK;
 }
 

@@ -15,6 +15,7 @@
 //   * interpolative decomposition of the far field by a Gaussian sketch followed by
 //     column-pivoted Householder QR, T = Pi W B (Section 7.1, eq. Tmap).
 #include "precompute.hpp"
+#include "sketch.hpp"
 
 #include <algorithm>
 #include <chrono>
@@ -290,7 +291,9 @@ void precompute(double eps, int mode, int K, const PrecomputeOptions& opt, Preco
   if (K < 1 || K > 2000) throw std::runtime_error("precompute: K out of range");
   if (mode != 0 && mode != 1) throw std::runtime_error("precompute: mode must be 0 or 1");
 #ifdef _OPENMP
-  if (opt.threads > 0) omp_set_num_threads(opt.threads);
+  // the thread count is an ICV of the calling host thread: set it on every call, so that a
+  // single-threaded precompute does not leave the next one on this thread single-threaded
+  omp_set_num_threads(opt.threads > 0 ? opt.threads : omp_get_num_procs());
 #endif
   const double t0 = now_s();
   precompute_zernike(eps, K, out);
@@ -592,8 +595,17 @@ void precompute(double eps, int mode, int K, const PrecomputeOptions& opt, Preco
     std::vector<double> Yrun((size_t)ks * nf, 0.0), Yc;
     bool enlarge = false;
     const int CB = 32;
+    // the sketch products on the device when one is available (same Omega, FP64)
+    DeviceSketch* dsk = opt.device_sketch ? sketch_create(ks, nt, nf, mode, Om.data(), xt.data(), xf.data()) : nullptr;
+    out.sketch_on_device = dsk != nullptr;
     for (int pan = npanel - 1; pan >= 0 && !enlarge; --pan) {
       const int r0 = prow[pan], r1 = prow[pan + 1], nrw = r1 - r0;
+      if (dsk) {
+        if (!sketch_add_rows(dsk, r0, r1) || (pan < nlev && !sketch_read(dsk, Yrun.data()))) {
+          sketch_destroy(dsk);
+          throw std::runtime_error("precompute: device sketch failed");
+        }
+      } else
 #pragma omp parallel
       {
         std::vector<double> Ab((size_t)nrw * CB);
@@ -631,17 +643,31 @@ void precompute(double eps, int mode, int K, const PrecomputeOptions& opt, Preco
         }
       }
       if (pan < nlev) {
-        Yc = Yrun;
+        // CPQR on the first kse rows of the sketch (itself a Gaussian sketch), starting
+        // small and doubling until at least 16 rows of oversampling remain past the rank:
+        // the outer levels of the ladder have small ranks
         std::vector<int> piv;
-        const int p = cpqr(Yc, ks, piv);
+        int kse = std::min(ks, 64), p = 0;
+        for (;;) {
+          Yc.resize((size_t)kse * nf);
+          for (int l = 0; l < nf; ++l)
+            std::copy(&Yrun[(size_t)l * ks], &Yrun[(size_t)l * ks] + kse, &Yc[(size_t)l * kse]);
+          p = cpqr(Yc, kse, piv);
+          if (p >= kse - 16 && kse < ks) {
+            kse = std::min(2 * kse, ks);
+            continue;
+          }
+          break;
+        }
         if (p >= ks - 16 && ks < nt) {
           enlarge = true;
           break;
         }
         if (p < 1) throw std::runtime_error("precompute: ID rank is zero");
-        finish_level(Yc, ks, piv, p, ladder[pan] * eps, out.reps[pan]);
+        finish_level(Yc, kse, piv, p, ladder[pan] * eps, out.reps[pan]);
       }
     }
+    sketch_destroy(dsk);
     if (!enlarge) break;
     ks = std::min(2 * ks, nt);  // rank not revealed by the sketch: enlarge it
   }

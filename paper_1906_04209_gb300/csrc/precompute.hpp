@@ -17,6 +17,7 @@ struct PrecomputeOptions {
   double id_rho_min = 2.0;  // far region starts at id_rho_min * eps
   bool multilevel = true;   // also compress against farther regions (ladder x1.5, x4/3, ...)
   double id_ladder_max = 1.0;  // largest far-field radius of the ladder (radians)
+  bool device_sketch = false;  // form the ID sketch on the current CUDA device when one exists
   bool keep_collocation = false;  // keep the modal collocation matrices (diagnostics)
 };
 
@@ -43,6 +44,7 @@ struct Precomputed {
   std::vector<double> sloc;          // p x 3 offsets in the patch frame
   std::vector<double> I;             // K
   std::vector<OutRep> reps;          // increasing rho_min; reps[0] equals (T, st, sth, sloc)
+  bool sketch_on_device = false;     // the ID sketch was formed on a CUDA device
   std::vector<double> trad;          // radial collocation nodes
   std::vector<double> beta;          // nrad x K radial profiles
   std::vector<double> w;             // nf fine-grid weights

@@ -207,8 +207,15 @@ __global__ void __launch_bounds__(256) coef_kernel(int g0, const int* __restrict
 }
 
 // Direct sums at the Zernike nodes over a per-patch source list (overwrites z).
-constexpr int DT_THREADS = 256;
-constexpr int DT_NT = 2;
+// direct lists: one block per target patch, DT_NT Zernike nodes per thread
+#ifndef NCS_DT_NT
+#define NCS_DT_NT 2
+#endif
+constexpr int DT_NT = NCS_DT_NT;
+constexpr int DT_THREADS = 512 / DT_NT;
+// the float-float direct lists keep two nodes per thread (register pressure)
+constexpr int DTD_NT = 2;
+constexpr int DTD_THREADS = 256;
 constexpr int DT_JT = 8;
 
 template <typename R, int MODE>
@@ -698,7 +705,7 @@ __global__ void __launch_bounds__(P2L_THREADS) p2l_df_kernel(
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(DT_THREADS) direct_list_df_kernel(
+__global__ void __launch_bounds__(DTD_THREADS) direct_list_df_kernel(
     int pt, int Kstar, const int* __restrict__ rep_p, const int* __restrict__ rep_off,
     const int64_t* __restrict__ pd_off, const int* __restrict__ pd, const int* __restrict__ pdk,
     const double* __restrict__ centres, const double* __restrict__ zloc, const double* __restrict__ soff,
@@ -714,12 +721,12 @@ __global__ void __launch_bounds__(DT_THREADS) direct_list_df_kernel(
   const double cx = centres[3 * i], cy = centres[3 * i + 1], cz = centres[3 * i + 2];
   double e1[3], e2[3];
   patch_frame(cx, cy, cz, e1, e2);
-  f2 a[DT_NT][3];
-  double acc[DT_NT];
-  int kk[DT_NT];
+  f2 a[DTD_NT][3];
+  double acc[DTD_NT];
+  int kk[DTD_NT];
 #pragma unroll
-  for (int t = 0; t < DT_NT; ++t) {
-    kk[t] = (blockIdx.y * DT_NT + t) * DT_THREADS + threadIdx.x;
+  for (int t = 0; t < DTD_NT; ++t) {
+    kk[t] = (blockIdx.y * DTD_NT + t) * DTD_THREADS + threadIdx.x;
     double gq[3] = {0.0, 0.0, 0.0};
     if (kk[t] < Kstar) frame_apply(e1, e2, cx, cy, cz, zloc[3 * kk[t]], zloc[3 * kk[t] + 1], zloc[3 * kk[t] + 2], gq);
     for (int c = 0; c < 3; ++c) a[t][c] = f2_from_double(gq[c]);
@@ -743,7 +750,7 @@ __global__ void __launch_bounds__(DT_THREADS) direct_list_df_kernel(
     }
     __syncthreads();
     const int ns = toff[nj];
-    for (int idx = threadIdx.x; idx < ns; idx += DT_THREADS) {
+    for (int idx = threadIdx.x; idx < ns; idx += DTD_THREADS) {
       int jj = 0;
       while (idx >= toff[jj + 1]) ++jj;
       const int64_t gs = (int64_t)pd[s0 + jj] * pt + tcol[jj] + (idx - toff[jj]);
@@ -753,19 +760,19 @@ __global__ void __launch_bounds__(DT_THREADS) direct_list_df_kernel(
       Sl[idx] = make_float4(x.lo, y.lo, zz.lo, r.lo);
     }
     __syncthreads();
-    f2 part[DT_NT];
+    f2 part[DTD_NT];
 #pragma unroll
-    for (int t = 0; t < DT_NT; ++t) part[t] = f2{0.0f, 0.0f};
+    for (int t = 0; t < DTD_NT; ++t) part[t] = f2{0.0f, 0.0f};
     for (int s = 0; s < ns; ++s) {
       const float4 h = Sh[s], l = Sl[s];
 #pragma unroll
-      for (int t = 0; t < DT_NT; ++t) pair_f2_acc<MODE>(a[t], h, l, tab, part[t]);
+      for (int t = 0; t < DTD_NT; ++t) pair_f2_acc<MODE>(a[t], h, l, tab, part[t]);
     }
 #pragma unroll
-    for (int t = 0; t < DT_NT; ++t) acc[t] += f2_to_double(part[t]);
+    for (int t = 0; t < DTD_NT; ++t) acc[t] += f2_to_double(part[t]);
   }
 #pragma unroll
-  for (int t = 0; t < DT_NT; ++t)
+  for (int t = 0; t < DTD_NT; ++t)
     if (kk[t] < Kstar) z[i * Kstar + kk[t]] = acc[t];
 }
 
@@ -1108,8 +1115,8 @@ static cudaError_t tree_field_df(const DeviceData& dd, const TreeDevice& t, cuda
   {
     const size_t smem = (size_t)2 * DT_JT * dd.pmax * sizeof(float4);
     if ((e = allow_smem(direct_list_df_kernel<MODE>, smem)) != cudaSuccess) return e;
-    dim3 grid((unsigned)dd.N, (unsigned)((dd.Kstar + DT_THREADS * DT_NT - 1) / (DT_THREADS * DT_NT)));
-    count_launch(), direct_list_df_kernel<MODE><<<grid, DT_THREADS, smem, s>>>(dd.p, dd.Kstar, dd.rep_p, dd.rep_off, t.pd_off, t.pd,
+    dim3 grid((unsigned)dd.N, (unsigned)((dd.Kstar + DTD_THREADS * DTD_NT - 1) / (DTD_THREADS * DTD_NT)));
+    count_launch(), direct_list_df_kernel<MODE><<<grid, DTD_THREADS, smem, s>>>(dd.p, dd.Kstar, dd.rep_p, dd.rep_off, t.pd_off, t.pd,
                                                               t.pdk, dd.centres, dd.zloc, dd.soff64, dd.rho64,
                                                               dd.logtab, dd.pmax, dd.z);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

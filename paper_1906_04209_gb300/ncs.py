@@ -30,7 +30,7 @@ EXPORTS = ["ncs_default_params", "ncs_create", "ncs_create_from_operator", "ncs_
            "ncs_matvec_dev", "ncs_field_dev", "ncs_solve", "ncs_eval", "ncs_last_error", "ncs_destroy",
            "ncs_tree_pairs", "ncs_tree_stats", "ncs_profile_matvec", "ncs_create_from_operators", "ncs_get_reps",
            "ncs_tc_gemm_f32", "ncs_batch_solve", "ncs_block_dots", "ncs_block_dots_noalloc",
-           "ncs_launch_count"]
+           "ncs_launch_count", "ncs_get_rep"]
 
 
 class ncs_params(ctypes.Structure):
@@ -38,7 +38,8 @@ class ncs_params(ctypes.Structure):
                 ("id_tol", ctypes.c_double), ("threads", ctypes.c_int), ("grid_tol", ctypes.c_double),
                 ("method", ctypes.c_int), ("tree_min_patches", ctypes.c_int), ("gmres_maxit", ctypes.c_int),
                 ("verbose", ctypes.c_int), ("mixed_residual", ctypes.c_int), ("tensor_cores", ctypes.c_int),
-                ("residual_update", ctypes.c_int), ("id_ladder_max", ctypes.c_double)]
+                ("residual_update", ctypes.c_int), ("id_ladder_max", ctypes.c_double),
+                ("device_precompute", ctypes.c_int)]
 
 
 class NcsError(RuntimeError):
@@ -94,6 +95,7 @@ def load(path: str = LIB_PATH):
                                     ctypes.POINTER(ctypes.c_int), D]
     lib.ncs_block_dots.argtypes = [ctypes.c_int64, ctypes.c_int, VP, ctypes.c_int64, VP, VP, VP]
     lib.ncs_block_dots_noalloc.argtypes = [ctypes.c_int64, ctypes.c_int, VP, ctypes.c_int64, VP, VP, VP]
+    lib.ncs_get_rep.argtypes = [VP, ctypes.c_int, D, D, D]
     lib.ncs_launch_count.argtypes = []
     lib.ncs_launch_count.restype = ctypes.c_int64
     lib.ncs_destroy.argtypes = [VP]
@@ -224,8 +226,9 @@ class Context:
         return dict(zip(keys, [int(v) for v in out]))
 
     def timings(self):
-        out = np.zeros(2)
-        load().ncs_timings(self.h, _ptr(out), 2)
+        """[one-patch seconds, ID seconds, 1 if the ID sketch ran on the device]"""
+        out = np.zeros(3)
+        load().ncs_timings(self.h, _ptr(out), 3)
         return out
 
     def operator(self):
@@ -248,6 +251,14 @@ class Context:
         ps = np.zeros(n.value, dtype=np.int32)
         self._check(lib.ncs_get_reps(self.h, ctypes.byref(n), _ptr(rm), ps.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
         return rm, ps
+
+    def rep(self, r):
+        """(T, skel_t, skel_theta) of outgoing representation r."""
+        rm, ps = self.reps()
+        p = int(ps[r])
+        T, st, sth = np.zeros((p, self.K)), np.zeros(p), np.zeros(p)
+        self._check(load().ncs_get_rep(self.h, r, _ptr(T), _ptr(st), _ptr(sth)))
+        return T, st, sth
 
     def onepatch(self):
         i = self.info()

@@ -56,6 +56,27 @@ def test_library_outgoing_operator(libncs, mode):
     assert np.abs(lib - ref).max() < 1e-9 * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("mode", [EXTERIOR, INTERIOR])
+def test_library_id_ladder_accuracy(libncs, mode):
+    """Every representation of the library's ID ladder (far fields beyond 2, 3, 4, 6, ...
+    eps) reproduces the fine-grid far field at held-out targets beyond its radius."""
+    eps, K = 0.02, 21
+    c = ncs.Context(eps, mode, K, npan=7, nord=12, ntheta_fine=30, id_ladder_max=0.5)
+    op = onepatch.solve_one_patch(eps, mode, K, 7, 12, 30)
+    xf = idcomp.fine_points(op)
+    f = np.random.default_rng(6).standard_normal(K)
+    src = op.w * (op.B @ f)
+    rm, ps = c.reps()
+    assert len(ps) >= 6
+    for r in range(len(ps)):
+        T, st, sth = c.rep(r)
+        xt = idcomp.training_grid(eps, 1e-11, nper=5, rho_min_factor=1.03 * rm[r] / eps)
+        xs = np.stack([np.sin(st) * np.cos(sth), np.sin(st) * np.sin(sth), np.cos(st)], 1)
+        ref = G_on_surface(chord(xt[:, None], xf[None]), mode) @ src
+        lib = G_on_surface(chord(xt[:, None], xs[None]), mode) @ (T @ f)
+        assert np.abs(lib - ref).max() < 1e-9 * np.abs(ref).max(), (r, rm[r], ps[r])
+
+
 def test_create_validation(libncs):
     for args in [(0.0, 0, 10), (1.5, 0, 10), (0.1, 2, 10), (0.1, 0, 0)]:
         with pytest.raises(ncs.NcsError) as e:
@@ -76,6 +97,15 @@ def test_set_patches_validation(libncs):
     with pytest.raises(ncs.NcsError) as e:  # arguments are checked before any device work
         c.solve(tol=0)
     assert e.value.code == ncs.NCS_E_INPUT
+
+
+def test_precompute_without_device_uses_host_sketch(libncs):
+    # without a CUDA device the ID sketch is formed on the host whatever the parameter says
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    c = ncs.Context(0.05, INTERIOR, 10, npan=6, nord=10, ntheta_fine=24, device_precompute=1)
+    assert c.timings()[2] == 0.0
 
 
 def test_launch_count_without_gpu(libncs):
