@@ -87,7 +87,7 @@ typedef struct ncs_params {
                           ~1e-6 |r|, is then below 1e-10 |b|); 0 always recomputes
                           b - A x at mixed_residual precision */
   double id_ladder_max;/* largest far-field radius (radians) for which an extra, smaller ID
-                          representation is built (far fields beyond 2, 3, 4, 6, 8, ... eps;
+                          representation is built (far fields beyond 2, 2.52, 3.17, 4, ... eps;
                           Section 7.1 recompression), default 1.0; 0: only the 2 eps one.
                           Fewer representations shorten the host precompute (one CPQR of
                           the sketch per representation) and lengthen the products */

@@ -419,11 +419,15 @@ void precompute(double eps, int mode, int K, const PrecomputeOptions& opt, Preco
       for (int j = 0; j < K; ++j) out.I[j] += row[j];
     }
   }
+  // W B rows of every fine-grid point (nf x K), used by every representation's T
+  std::vector<double> WBall((size_t)nf * K);
+#pragma omp parallel for schedule(static)
+  for (int l = 0; l < nf; ++l) WB(l, &WBall[(size_t)l * K]);
   const double t1 = now_s();
   out.seconds_onepatch = t1 - t0;
 
   // ---- interpolative decompositions of the far field (Section 7.1), one per far-field
-  // radius of a ladder rho_min = 2, 3, 4, 6, 8, 12, ... eps (the per-level recompression
+  // radius of a ladder rho_min = 2, 2.52, 3.17, 4, 5.04, ... eps (the per-level recompression
   // of "Optimizations and parallelization": a source seen from farther away needs fewer
   // skeleton points). The training grid on {rho > rho_min} is made of radial panels whose
   // lower edges are the ladder radii (then doubling up to pi), with Gauss-Legendre nodes
@@ -434,7 +438,7 @@ void precompute(double eps, int mode, int K, const PrecomputeOptions& opt, Preco
     ladder.push_back(r);
     if (opt.multilevel) {
       for (int it = 0; it < 64; ++it) {
-        r *= (it % 2 == 0) ? 1.5 : 4.0 / 3.0;
+        r *= 1.2599210498948732;  // 2^(1/3): three rungs per doubling of the radius
         if (r * eps > opt.id_ladder_max) break;
         ladder.push_back(r);
       }
@@ -555,19 +559,24 @@ void precompute(double eps, int mode, int K, const PrecomputeOptions& opt, Preco
     rep.rho_min = rho_min;
     rep.p = p;
     rep.T.assign((size_t)p * K, 0.0);
-#pragma omp parallel
-    {
-      std::vector<double> row(K);
-#pragma omp for schedule(static)
+    // T = W B[skeleton] + X W B[rest] (eq. Tmap), as a product blocked over the rest
+    // columns: each block of WB rows is gathered once and applied to all rows of T
+    for (int m = 0; m < p; ++m)
+      std::copy(&WBall[(size_t)piv[m] * K], &WBall[(size_t)piv[m] * K] + K, &rep.T[(size_t)m * K]);
+    constexpr int CBL = 64;
+    std::vector<double> blk((size_t)CBL * K);
+    for (int c0 = 0; c0 < nrest; c0 += CBL) {
+      const int nc = std::min(CBL, nrest - c0);
+      for (int c = 0; c < nc; ++c)
+        std::copy(&WBall[(size_t)piv[p + c0 + c] * K], &WBall[(size_t)piv[p + c0 + c] * K] + K, &blk[(size_t)c * K]);
+#pragma omp parallel for schedule(static)
       for (int m = 0; m < p; ++m) {
         double* Tm = &rep.T[(size_t)m * K];
-        WB(piv[m], row.data());
-        for (int j = 0; j < K; ++j) Tm[j] = row[j];
-        for (int c = 0; c < nrest; ++c) {
-          const double x = X[(size_t)m * nrest + c];
-          if (x == 0.0) continue;
-          WB(piv[p + c], row.data());
-          for (int j = 0; j < K; ++j) Tm[j] += x * row[j];
+        const double* xm = &X[(size_t)m * nrest + c0];
+        for (int c = 0; c < nc; ++c) {
+          const double x = xm[c];
+          const double* b = &blk[(size_t)c * K];
+          for (int j = 0; j < K; ++j) Tm[j] += x * b[j];
         }
       }
     }

@@ -15,7 +15,7 @@ struct PrecomputeOptions {
   int id_nper = 10;         // training-grid Gauss nodes per radial panel
   int threads = 0;          // host threads (0: all)
   double id_rho_min = 2.0;  // far region starts at id_rho_min * eps
-  bool multilevel = true;   // also compress against farther regions (ladder x1.5, x4/3, ...)
+  bool multilevel = true;   // also compress against farther regions (ladder x 2^(1/3))
   double id_ladder_max = 1.0;  // largest far-field radius of the ladder (radians)
   bool device_sketch = false;  // form the ID sketch on the current CUDA device when one exists
   bool keep_collocation = false;  // keep the modal collocation matrices (diagnostics)

@@ -58,8 +58,8 @@ def test_library_outgoing_operator(libncs, mode):
 
 @pytest.mark.parametrize("mode", [EXTERIOR, INTERIOR])
 def test_library_id_ladder_accuracy(libncs, mode):
-    """Every representation of the library's ID ladder (far fields beyond 2, 3, 4, 6, ...
-    eps) reproduces the fine-grid far field at held-out targets beyond its radius."""
+    """Every representation of the library's ID ladder (far fields beyond
+    2, 2.52, 3.17, 4, ... eps) reproduces the fine-grid far field at held-out targets beyond its radius."""
     eps, K = 0.02, 21
     c = ncs.Context(eps, mode, K, npan=7, nord=12, ntheta_fine=30, id_ladder_max=0.5)
     op = onepatch.solve_one_patch(eps, mode, K, 7, 12, 30)
@@ -122,7 +122,9 @@ def test_id_ladder_max(libncs):
     assert len(p1) == 1 and abs(rm1[0] - 2 * 0.05) < 1e-12
     lad = ncs.Context(0.05, INTERIOR, 10, id_ladder_max=0.5, **kw)
     rm, ps = lad.reps()
-    assert len(ps) > 1 and ps[0] == p1[0]
+    # the training grids differ (panel edges at the ladder radii), so the rank of the
+    # 2 eps representation may move by a few points
+    assert len(ps) > 1 and abs(int(ps[0]) - int(p1[0])) <= 4
     assert all(ps[i] >= ps[i + 1] for i in range(len(ps) - 1))
     assert rm.max() <= 0.5 + 1e-12
     with pytest.raises(ncs.NcsError):
