@@ -173,18 +173,28 @@ __global__ void __launch_bounds__(256) coef_kernel(int g0, const int* __restrict
   const int64_t off = goff[g];
   double* F = cf_smem;        // q
   double* CS = cf_smem + q;   // 2 * mh * nr: C then S, [m][a]
+  // tables (after F and CS, sized for the largest shape): cos and sin of 2 pi k / nth, and
+  // the Chebyshev values T_d(x_a) = cos(d (2a + 1) pi / (4 nr)), d < 2 nr
+  R* CT = reinterpret_cast<R*>(cf_smem + 2 * q);
+  R* ST = CT + nth;
+  R* TD = ST + nth;  // [d][a]
   for (int i = threadIdx.x; i < q; i += blockDim.x) F[i] = grid[off + i];
+  for (int k = threadIdx.x; k < nth; k += blockDim.x) sincospi((R)(2 * k) / (R)nth, &ST[k], &CT[k]);
+  for (int i = threadIdx.x; i < 2 * nr * nr; i += blockDim.x) {
+    const int d = i / nr, a = i - d * nr;
+    TD[i] = cospi((R)(d * (2 * a + 1)) / (R)(4 * nr));
+  }
   __syncthreads();
   for (int i = threadIdx.x; i < mh * nr; i += blockDim.x) {
     const int m = i / nr, a = i - m * nr;
     R c = 0, s = 0;
+    int k = 0;  // (m * b) mod nth
     for (int b = 0; b < nth; ++b) {
-      R sn, cs;
-      // angle m * 2 pi b / nth, reduced to (m*b mod nth) for accuracy
-      sincospi((R)(2 * ((m * b) % nth)) / (R)nth, &sn, &cs);
       const R f = (R)F[a * nth + b];
-      c = fma(f, cs, c);
-      s = fma(f, sn, s);
+      c = fma(f, CT[k], c);
+      s = fma(f, ST[k], s);
+      k += m;
+      if (k >= nth) k -= nth;
     }
     const R w = (m == 0 ? (R)1 : (R)2) / (R)nth;
     CS[m * nr + a] = (double)(w * c);
@@ -194,11 +204,11 @@ __global__ void __launch_bounds__(256) coef_kernel(int g0, const int* __restrict
   for (int i = threadIdx.x; i < mh * nr; i += blockDim.x) {
     const int m = i / nr, j = i - m * nr;
     const int d = 2 * j + (m & 1);
+    const R* Td = TD + d * nr;
     R A = 0, B = 0;
     for (int a = 0; a < nr; ++a) {
-      const R T = cospi((R)(d * (2 * a + 1)) / (R)(4 * nr));
-      A = fma((R)CS[m * nr + a], T, A);
-      B = fma((R)CS[mh * nr + m * nr + a], T, B);
+      A = fma((R)CS[m * nr + a], Td[a], A);
+      B = fma((R)CS[mh * nr + m * nr + a], Td[a], B);
     }
     const R w = (d == 0 ? (R)1 : (R)2) / (R)nr;
     coef[off + i] = (double)(w * A);
@@ -427,13 +437,14 @@ __global__ void __launch_bounds__(256) l2l_kernel(int l0, const int* __restrict_
 // and every point then needs 9 FMAs, a square root and an atan2 on the FP32 pipes. Each
 // thread evaluates two points, so every coefficient load from shared memory serves both.
 
-// Clenshaw as eval_expansion for two points at once, the A and B coefficients of each
+// Clenshaw as eval_expansion for NP points at once, the A and B coefficients of each
 // (m, j) interleaved.
-__device__ __forceinline__ void eval_expansion_ab2(const float2* C, int nr, int mh, const float* rho,
-                                                   const float* ct, const float* st, float* out) {
-  float y[2], y2[2], cm[2], sm[2], val[2];
+template <int NP>
+__device__ __forceinline__ void eval_expansion_ab(const float2* C, int nr, int mh, const float* rho,
+                                                  const float* ct, const float* st, float* out) {
+  float y[NP], y2[NP], cm[NP], sm[NP], val[NP];
 #pragma unroll
-  for (int t = 0; t < 2; ++t) {
+  for (int t = 0; t < NP; ++t) {
     y[t] = fmaf(2.0f * rho[t], rho[t], -1.0f);
     y2[t] = y[t] + y[t];
     cm[t] = 1.0f;
@@ -442,11 +453,13 @@ __device__ __forceinline__ void eval_expansion_ab2(const float2* C, int nr, int 
   }
   for (int m = 0; m < mh; ++m) {
     const float2* c = C + m * nr;
-    float ba1[2] = {0.0f, 0.0f}, ba2[2] = {0.0f, 0.0f}, bb1[2] = {0.0f, 0.0f}, bb2[2] = {0.0f, 0.0f};
+    float ba1[NP], ba2[NP], bb1[NP], bb2[NP];
+#pragma unroll
+    for (int t = 0; t < NP; ++t) ba1[t] = ba2[t] = bb1[t] = bb2[t] = 0.0f;
     for (int j = nr - 1; j >= 0; --j) {
       const float2 ab = c[j];
 #pragma unroll
-      for (int t = 0; t < 2; ++t) {
+      for (int t = 0; t < NP; ++t) {
         const float ta = fmaf(y2[t], ba1[t], ab.x - ba2[t]);
         const float tb = fmaf(y2[t], bb1[t], ab.y - bb2[t]);
         ba2[t] = ba1[t];
@@ -456,7 +469,7 @@ __device__ __forceinline__ void eval_expansion_ab2(const float2* C, int nr, int 
       }
     }
 #pragma unroll
-    for (int t = 0; t < 2; ++t) {
+    for (int t = 0; t < NP; ++t) {
       float sa, sb;
       if ((m & 1) == 0) {
         sa = fmaf(-y[t], ba2[t], ba1[t]);
@@ -471,8 +484,8 @@ __device__ __forceinline__ void eval_expansion_ab2(const float2* C, int nr, int 
       cm[t] = cn;
     }
   }
-  out[0] = val[0];
-  out[1] = val[1];
+#pragma unroll
+  for (int t = 0; t < NP; ++t) out[t] = val[t];
 }
 
 // Stages group coefficients (FP64, A block then B block) as interleaved FP32 pairs.
@@ -536,7 +549,12 @@ __device__ __forceinline__ void polar32(const float* M, float v0, float v1, floa
   }
 }
 
-constexpr int L2P32_THREADS = 256;  // two Zernike nodes per thread (K* <= 512)
+// L2P of the FP32 product: NCS_L2P_NP Zernike nodes per thread (K* <= 512)
+#ifndef NCS_L2P_NP
+#define NCS_L2P_NP 2
+#endif
+constexpr int L2P_NP = NCS_L2P_NP;
+constexpr int L2P32_THREADS = 512 / L2P_NP;
 
 // L2P, FP32 product: z_i(k) += expansion of every listed grid group of patch i at node k.
 __global__ void __launch_bounds__(L2P32_THREADS) l2p_f32_kernel(
@@ -549,11 +567,13 @@ __global__ void __launch_bounds__(L2P32_THREADS) l2p_f32_kernel(
   float2* C = reinterpret_cast<float2*>(lp32_smem);
   __shared__ float M[12];
   const int64_t i = blockIdx.x;
-  const int k[2] = {(int)threadIdx.x, (int)threadIdx.x + L2P32_THREADS};
-  float v[2][3];
+  int k[L2P_NP];
+  float v[L2P_NP][3];
 #pragma unroll
-  for (int t = 0; t < 2; ++t)
+  for (int t = 0; t < L2P_NP; ++t) {
+    k[t] = (int)threadIdx.x + t * L2P32_THREADS;
     for (int c = 0; c < 3; ++c) v[t][c] = (k[t] < Kstar) ? (float)zloc[3 * k[t] + c] : 0.0f;
+  }
   const double cx = centres[3 * i], cy = centres[3 * i + 1], cz = centres[3 * i + 2];
   float acol[3] = {0.0f, 0.0f, 0.0f};  // column (threadIdx mod 3) of the patch frame (e1, e2, c)
   if (threadIdx.x < 9) {
@@ -564,7 +584,9 @@ __global__ void __launch_bounds__(L2P32_THREADS) l2p_f32_kernel(
 #pragma unroll
     for (int k = 0; k < 3; ++k) acol[k] = c == 0 ? e1[k] : (c == 1 ? e2[k] : cc[k]);
   }
-  double acc[2] = {0.0, 0.0};
+  double acc[L2P_NP];
+#pragma unroll
+  for (int t = 0; t < L2P_NP; ++t) acc[t] = 0.0;
   for (int64_t s = pg_off[i]; s < pg_off[i + 1]; ++s) {
     const int g = pg[s];
     const int sh = gshape[g];
@@ -574,15 +596,15 @@ __global__ void __launch_bounds__(L2P32_THREADS) l2p_f32_kernel(
     group_transform32(gframe + 9 * (size_t)g, gcen + 3 * g, acol, false, cx, cy, cz, M);
     __syncthreads();
     const float invR = (float)(1.0 / gR[g]);
-    float rho[2], ct[2], st[2], out[2];
+    float rho[L2P_NP], ct[L2P_NP], st[L2P_NP], out[L2P_NP];
 #pragma unroll
-    for (int t = 0; t < 2; ++t) polar32(M, v[t][0], v[t][1], v[t][2], invR, &rho[t], &ct[t], &st[t]);
-    eval_expansion_ab2(C, nr, mh, rho, ct, st, out);
-    acc[0] += (double)out[0];
-    acc[1] += (double)out[1];
+    for (int t = 0; t < L2P_NP; ++t) polar32(M, v[t][0], v[t][1], v[t][2], invR, &rho[t], &ct[t], &st[t]);
+    eval_expansion_ab<L2P_NP>(C, nr, mh, rho, ct, st, out);
+#pragma unroll
+    for (int t = 0; t < L2P_NP; ++t) acc[t] += (double)out[t];
   }
 #pragma unroll
-  for (int t = 0; t < 2; ++t)
+  for (int t = 0; t < L2P_NP; ++t)
     if (k[t] < Kstar) z[i * Kstar + k[t]] += acc[t];
 }
 
@@ -618,7 +640,7 @@ __global__ void __launch_bounds__(L2L32_THREADS) l2l_f32_kernel(
       const float* o = gpos + 3 * (offc + aa);
       polar32(M, o[0], o[1], o[2], invR, &rho[t], &ct[t], &st[t]);
     }
-    eval_expansion_ab2(C, nrp, mhp, rho, ct, st, out);
+    eval_expansion_ab<2>(C, nrp, mhp, rho, ct, st, out);
 #pragma unroll
     for (int t = 0; t < 2; ++t)
       if (a[t] < qc) grid[offc + a[t]] += (double)out[t];
@@ -1006,7 +1028,8 @@ template <typename R>
 static cudaError_t downward(const TreeDevice& t, cudaStream_t s) {
   cudaError_t e;
   using CR = typename std::conditional<std::is_same<R, f2>::value, double, R>::type;
-  const size_t csm = (size_t)t.max_q * sizeof(double) + (size_t)t.max_nth * t.max_nr * sizeof(double);
+  const size_t csm = (size_t)t.max_q * sizeof(double) + (size_t)t.max_nth * t.max_nr * sizeof(double) +
+                     (2 * (size_t)t.max_nth + 2 * (size_t)t.max_nr * t.max_nr) * sizeof(CR);
   if ((e = allow_smem(coef_kernel<CR>, csm)) != cudaSuccess) return e;
   const int nl = (int)t.gl_off.size() - 1;
   for (int l = 0; l < nl; ++l) {

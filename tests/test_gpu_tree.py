@@ -129,11 +129,14 @@ def test_mixed_solve_true_residual(small_pre, update):
     assert abs(true_rel - rm["relres"]) <= 0.05 * tol
 
 
-def test_full_size_sampled(libncs):
-    """The 100 000-patch workload (eps = 0.001, K = 136, jittered Fibonacci, interior):
-    tree product in the launch configuration the benchmark times, checked at 48
-    sampled (patch, node) outputs against the plain-C oracle sums."""
-    c, eps, mode, K = L.workload(3)
+@pytest.mark.parametrize("layout,mode", [("fibonacci", INTERIOR), ("fibonacci", EXTERIOR), ("vmf", INTERIOR),
+                                         ("vmf", EXTERIOR)])
+def test_full_size_sampled(libncs, layout, mode):
+    """The 100 000-patch workloads (eps = 0.001, K = 136; jittered Fibonacci and 20 vMF
+    clusters; interior and exterior): tree product in the launch configuration the
+    benchmark times, checked at 48 sampled (patch, node) outputs against the plain-C
+    oracle sums."""
+    c, eps, _, K = L.workload(3, layout=layout)
     pre = O.make_precompute(eps, mode, K, npan=8, nord=12, ntheta=40, tau=1e-10)
     N = len(c)
     ctx = _ctx(pre, method=ncs.METHOD_TREE)
@@ -146,8 +149,11 @@ def test_full_size_sampled(libncs):
     scale = np.abs(ref).max()
     zdf = _field(ctx, x, ncs.DF64, N, pre.Kstar)[patches, nodes]
     z32 = _field(ctx, x, ncs.FP32, N, pre.Kstar)[patches, nodes]
-    assert np.abs(zdf - ref).max() <= 1e-6 * scale
-    assert np.abs(z32 - ref).max() <= 1e-5 * scale
+    edf, e32 = np.abs(zdf - ref).max() / scale, np.abs(z32 - ref).max() / scale
+    print(f"N=1e5 {layout} mode {mode}: float-float error {edf:.2e}, FP32 error {e32:.2e}")
+    # float-float: only the incoming-grid interpolation separates the tree from the sums
+    assert edf <= 1e-8
+    assert e32 <= 1e-5
 
 
 @pytest.mark.parametrize("mode", [EXTERIOR, INTERIOR])
