@@ -551,7 +551,7 @@ __device__ __forceinline__ void polar32(const float* M, float v0, float v1, floa
 
 // L2P of the FP32 product: NCS_L2P_NP Zernike nodes per thread (K* <= 512)
 #ifndef NCS_L2P_NP
-#define NCS_L2P_NP 2
+#define NCS_L2P_NP 4
 #endif
 constexpr int L2P_NP = NCS_L2P_NP;
 constexpr int L2P32_THREADS = 512 / L2P_NP;
