@@ -58,6 +58,8 @@ extern "C" {
                        significand, ~1e-14 relative) on the FP32 pipes; GEMMs, grid
                        transforms and offsets in FP64: FP64-accurate products at a
                        fraction of the FP64-pipe cost */
+#define NCS_PRECISION_DEFAULT (-1) /* the context's precision (ncs_set_precision); for a
+                                      product, NCS_MIXED means NCS_FP32 */
 
 #define NCS_METHOD_AUTO 0   /* tree when N >= tree_min_patches, else direct */
 #define NCS_METHOD_DIRECT 1 /* compressed sums over all other patches, O(N^2) (Section 7.1) */
@@ -205,6 +207,14 @@ int ncs_tree_stats(ncs_ctx* ctx, int64_t* out, int n);
 
 /* Selects NCS_METHOD_AUTO / DIRECT / TREE for later products and solves. */
 int ncs_set_method(ncs_ctx* ctx, int method);
+
+/*
+ * Sets the context's precision (NCS_FP64, NCS_FP32, NCS_MIXED or NCS_DF64; default
+ * NCS_MIXED), used by every call whose precision argument is NCS_PRECISION_DEFAULT: solves
+ * run at it, products at it with NCS_MIXED read as NCS_FP32 (the inner products of the mixed
+ * solve). Errors: NCS_E_INPUT.
+ */
+int ncs_set_precision(ncs_ctx* ctx, int precision);
 
 /*
  * y = A x for the system of eq. (opinteqnsdisc): y_i = x_i + P sum_{j != i} S_ij B x_j,

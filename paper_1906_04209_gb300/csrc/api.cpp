@@ -599,6 +599,16 @@ int ncs_get_reps(const ncs_ctx* c, int* nrep, double* rho_min, int* p) {
   return NCS_OK;
 }
 
+int ncs_set_precision(ncs_ctx* c, int precision) {
+  if (!c) return NCS_E_INPUT;
+  if (precision != NCS_FP64 && precision != NCS_FP32 && precision != NCS_MIXED && precision != NCS_DF64) {
+    c->err = "ncs_set_precision: bad precision";
+    return NCS_E_INPUT;
+  }
+  c->precision = precision;
+  return NCS_OK;
+}
+
 int ncs_get_rep(const ncs_ctx* c, int r, double* T, double* skel_t, double* skel_theta) {
   if (!c || r < 0 || r >= (int)c->pc.reps.size()) return NCS_E_INPUT;
   const ncs::OutRep& rep = c->pc.reps[r];
@@ -735,6 +745,7 @@ int ncs_set_method(ncs_ctx* c, int method) {
 }
 
 int ncs_matvec_dev(ncs_ctx* c, const double* x, double* y, int precision, void* stream) {
+  if (c && precision == NCS_PRECISION_DEFAULT) precision = c->precision == NCS_MIXED ? NCS_FP32 : c->precision;
   try {
     if (!c) throw Fail{NCS_E_INPUT, "null context"};
     if (!x || !y) throw Fail{NCS_E_INPUT, "NULL vector"};
@@ -751,6 +762,7 @@ int ncs_matvec_dev(ncs_ctx* c, const double* x, double* y, int precision, void* 
 }
 
 int ncs_field_dev(ncs_ctx* c, const double* x, double* z, int precision, void* stream) {
+  if (c && precision == NCS_PRECISION_DEFAULT) precision = c->precision == NCS_MIXED ? NCS_FP32 : c->precision;
   try {
     if (!c) throw Fail{NCS_E_INPUT, "null context"};
     if (!x || !z) throw Fail{NCS_E_INPUT, "NULL vector"};
@@ -769,6 +781,7 @@ int ncs_field_dev(ncs_ctx* c, const double* x, double* z, int precision, void* s
 }
 
 int ncs_profile_matvec(ncs_ctx* c, const double* x, double* y, int precision, void* stream, double* ms, int n) {
+  if (c && precision == NCS_PRECISION_DEFAULT) precision = c->precision == NCS_MIXED ? NCS_FP32 : c->precision;
   cudaEvent_t ev[8] = {};
   int rc = NCS_OK;
   try {
@@ -810,6 +823,7 @@ int ncs_profile_matvec(ncs_ctx* c, const double* x, double* y, int precision, vo
 }
 
 int ncs_matvec(ncs_ctx* c, const double* x, double* y, int precision) {
+  if (c && precision == NCS_PRECISION_DEFAULT) precision = c->precision == NCS_MIXED ? NCS_FP32 : c->precision;
   try {
     if (!c) throw Fail{NCS_E_INPUT, "null context"};
     if (!x || !y) throw Fail{NCS_E_INPUT, "NULL vector"};
@@ -833,6 +847,7 @@ int ncs_matvec(ncs_ctx* c, const double* x, double* y, int precision) {
 
 int ncs_solve(ncs_ctx* c, double tol, int precision, double* fhat, double* scalar, double* Isigma, int* iterations,
               double* relres) {
+  if (c && precision == NCS_PRECISION_DEFAULT) precision = c->precision;
   try {
     if (!c) throw Fail{NCS_E_INPUT, "null context"};
     if (!(tol > 0.0 && tol < 1.0)) throw Fail{NCS_E_INPUT, "tol must be in (0, 1)"};

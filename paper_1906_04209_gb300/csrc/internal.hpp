@@ -87,6 +87,7 @@ constexpr int kDotChunks = 64;
 // The opaque context of the C ABI.
 struct ncs_ctx {
   ncs_params prm{};
+  int precision = NCS_MIXED;  // used when a call passes NCS_PRECISION_DEFAULT
   ncs::Precomputed pc;
   bool from_operator = false;
   std::string err;

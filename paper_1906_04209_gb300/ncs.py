@@ -23,6 +23,7 @@ NCS_E_OOM = -6
 NCS_E_STATE = -7
 EXTERIOR, INTERIOR = 0, 1
 FP64, FP32, MIXED, DF64 = 0, 1, 2, 3
+PRECISION_DEFAULT = -1  # the context precision set by Context.set_precision
 METHOD_AUTO, METHOD_DIRECT, METHOD_TREE = 0, 1, 2
 
 EXPORTS = ["ncs_default_params", "ncs_create", "ncs_create_from_operator", "ncs_info", "ncs_timings",
@@ -30,7 +31,7 @@ EXPORTS = ["ncs_default_params", "ncs_create", "ncs_create_from_operator", "ncs_
            "ncs_matvec_dev", "ncs_field_dev", "ncs_solve", "ncs_eval", "ncs_last_error", "ncs_destroy",
            "ncs_tree_pairs", "ncs_tree_stats", "ncs_profile_matvec", "ncs_create_from_operators", "ncs_get_reps",
            "ncs_tc_gemm_f32", "ncs_batch_solve", "ncs_block_dots", "ncs_block_dots_noalloc",
-           "ncs_launch_count", "ncs_get_rep"]
+           "ncs_launch_count", "ncs_get_rep", "ncs_set_precision"]
 
 
 class ncs_params(ctypes.Structure):
@@ -96,6 +97,7 @@ def load(path: str = LIB_PATH):
     lib.ncs_block_dots.argtypes = [ctypes.c_int64, ctypes.c_int, VP, ctypes.c_int64, VP, VP, VP]
     lib.ncs_block_dots_noalloc.argtypes = [ctypes.c_int64, ctypes.c_int, VP, ctypes.c_int64, VP, VP, VP]
     lib.ncs_get_rep.argtypes = [VP, ctypes.c_int, D, D, D]
+    lib.ncs_set_precision.argtypes = [VP, ctypes.c_int]
     lib.ncs_launch_count.argtypes = []
     lib.ncs_launch_count.restype = ctypes.c_int64
     lib.ncs_destroy.argtypes = [VP]
@@ -251,6 +253,10 @@ class Context:
         ps = np.zeros(n.value, dtype=np.int32)
         self._check(lib.ncs_get_reps(self.h, ctypes.byref(n), _ptr(rm), ps.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
         return rm, ps
+
+    def set_precision(self, precision):
+        """Context precision used by calls given PRECISION_DEFAULT."""
+        self._check(load().ncs_set_precision(self.h, precision))
 
     def rep(self, r):
         """(T, skel_t, skel_theta) of outgoing representation r."""

@@ -61,6 +61,27 @@ def test_field_parity_shared_operator(small_pre, mode, N, tc):
     assert np.abs(z32 - ref).max() <= FP32_TOL[tc] * scale
 
 
+def test_context_precision(small_pre):
+    """Calls given PRECISION_DEFAULT run at the context precision (ncs_set_precision):
+    a solve at the default (mixed) equals the explicit mixed solve, products at MIXED run
+    in FP32, and after set_precision(DF64) both run in float-float."""
+    pre = small_pre(INTERIOR)
+    N = 10
+    c = L.uniform(N, 0.1, L.rng(95))
+    ctx = _ctx_from_oracle(pre, method=ncs.METHOD_DIRECT)
+    ctx.set_patches(c)
+    x = np.random.default_rng(3).standard_normal(N * pre.K)
+    assert np.array_equal(ctx.matvec(x, ncs.PRECISION_DEFAULT), ctx.matvec(x, ncs.FP32))
+    r0 = ctx.solve(tol=1e-10, precision=ncs.PRECISION_DEFAULT)
+    r1 = ctx.solve(tol=1e-10, precision=ncs.MIXED)
+    assert r0["scalar"] == r1["scalar"] and r0["iterations"] == r1["iterations"]
+    ctx.set_precision(ncs.DF64)
+    assert np.array_equal(ctx.matvec(x, ncs.PRECISION_DEFAULT), ctx.matvec(x, ncs.DF64))
+    r2 = ctx.solve(tol=1e-10, precision=ncs.PRECISION_DEFAULT)
+    r3 = ctx.solve(tol=1e-10, precision=ncs.DF64)
+    assert r2["scalar"] == r3["scalar"]
+
+
 @pytest.mark.parametrize("mode", [EXTERIOR, INTERIOR])
 def test_matvec_host_and_device_agree(small_pre, mode):
     pre = small_pre(mode)

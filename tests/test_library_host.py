@@ -77,6 +77,15 @@ def test_library_id_ladder_accuracy(libncs, mode):
         assert np.abs(lib - ref).max() < 1e-9 * np.abs(ref).max(), (r, rm[r], ps[r])
 
 
+def test_set_precision_validation(libncs):
+    c = ncs.Context(0.05, INTERIOR, 10, npan=6, nord=10, ntheta_fine=24)
+    for p in (ncs.FP64, ncs.FP32, ncs.MIXED, ncs.DF64):
+        c.set_precision(p)
+    for bad in (-1, 4, 99):
+        with pytest.raises(ncs.NcsError):
+            c.set_precision(bad)
+
+
 def test_create_validation(libncs):
     for args in [(0.0, 0, 10), (1.5, 0, 10), (0.1, 2, 10), (0.1, 0, 0)]:
         with pytest.raises(ncs.NcsError) as e:
