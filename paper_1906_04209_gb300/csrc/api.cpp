@@ -641,6 +641,9 @@ int ncs_timings(const ncs_ctx* c, double* out, int n) {
   if (n > 0) out[0] = c->pc.seconds_onepatch;
   if (n > 1) out[1] = c->pc.seconds_id;
   if (n > 2) out[2] = c->pc.sketch_on_device ? 1.0 : 0.0;
+  if (n > 3) out[3] = c->pc.seconds_sketch;
+  if (n > 4) out[4] = c->pc.seconds_cpqr;
+  if (n > 5) out[5] = c->pc.seconds_assemble;
   return NCS_OK;
 }
 

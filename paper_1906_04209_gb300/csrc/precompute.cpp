@@ -540,6 +540,21 @@ void precompute(double eps, int mode, int K, const PrecomputeOptions& opt, Preco
     return p;
   };
 
+  // Skeleton coordinates of a representation from its pivot order.
+  auto set_skeleton = [&](const std::vector<int>& piv, int p, double rho_min, OutRep& rep) {
+    rep.rho_min = rho_min;
+    rep.p = p;
+    rep.st.resize(p);
+    rep.sth.resize(p);
+    rep.sloc.resize(3 * (size_t)p);
+    for (int m = 0; m < p; ++m) {
+      const int l = piv[m];
+      rep.st[m] = tr[l / nth];
+      rep.sth[m] = thf[l % nth];
+      local_offset(rep.st[m], rep.sth[m], &rep.sloc[3 * (size_t)m]);
+    }
+  };
+
   // Pi = [I, R11^-1 R12] in pivoted order; T = Pi W B; skeleton coordinates.
   auto finish_level = [&](const std::vector<double>& Y, int ks, const std::vector<int>& piv, int p,
                           double rho_min, OutRep& rep) {
@@ -580,15 +595,7 @@ void precompute(double eps, int mode, int K, const PrecomputeOptions& opt, Preco
         }
       }
     }
-    rep.st.resize(p);
-    rep.sth.resize(p);
-    rep.sloc.resize(3 * (size_t)p);
-    for (int m = 0; m < p; ++m) {
-      const int l = piv[m];
-      rep.st[m] = tr[l / nth];
-      rep.sth[m] = thf[l % nth];
-      local_offset(rep.st[m], rep.sth[m], &rep.sloc[3 * (size_t)m]);
-    }
+    set_skeleton(piv, p, rho_min, rep);
   };
 
   const int nlev = (int)ladder.size();
@@ -606,11 +613,16 @@ void precompute(double eps, int mode, int K, const PrecomputeOptions& opt, Preco
     const int CB = 32;
     // the sketch products on the device when one is available (same Omega, FP64)
     DeviceSketch* dsk = opt.device_sketch ? sketch_create(ks, nt, nf, mode, Om.data(), xt.data(), xf.data()) : nullptr;
+    if (dsk && !sketch_set_wb(dsk, K, WBall.data())) {
+      sketch_destroy(dsk);
+      dsk = nullptr;
+    }
     out.sketch_on_device = dsk != nullptr;
     for (int pan = npanel - 1; pan >= 0 && !enlarge; --pan) {
       const int r0 = prow[pan], r1 = prow[pan + 1], nrw = r1 - r0;
+      const double ts0 = now_s();
       if (dsk) {
-        if (!sketch_add_rows(dsk, r0, r1) || (pan < nlev && !sketch_read(dsk, Yrun.data()))) {
+        if (!sketch_add_rows(dsk, r0, r1)) {
           sketch_destroy(dsk);
           throw std::runtime_error("precompute: device sketch failed");
         }
@@ -651,17 +663,27 @@ void precompute(double eps, int mode, int K, const PrecomputeOptions& opt, Preco
           }
         }
       }
+      out.seconds_sketch += now_s() - ts0;
       if (pan < nlev) {
+        const double tc0 = now_s();
         // CPQR on the first kse rows of the sketch (itself a Gaussian sketch), starting
         // small and doubling until at least 16 rows of oversampling remain past the rank:
         // the outer levels of the ladder have small ranks
         std::vector<int> piv;
         int kse = std::min(ks, 64), p = 0;
         for (;;) {
-          Yc.resize((size_t)kse * nf);
-          for (int l = 0; l < nf; ++l)
-            std::copy(&Yrun[(size_t)l * ks], &Yrun[(size_t)l * ks] + kse, &Yc[(size_t)l * kse]);
-          p = cpqr(Yc, kse, piv);
+          if (dsk) {
+            p = sketch_cpqr(dsk, kse, opt.id_tol, piv);
+            if (p < 0) {
+              sketch_destroy(dsk);
+              throw std::runtime_error("precompute: device CPQR failed");
+            }
+          } else {
+            Yc.resize((size_t)kse * nf);
+            for (int l = 0; l < nf; ++l)
+              std::copy(&Yrun[(size_t)l * ks], &Yrun[(size_t)l * ks] + kse, &Yc[(size_t)l * kse]);
+            p = cpqr(Yc, kse, piv);
+          }
           if (p >= kse - 16 && kse < ks) {
             kse = std::min(2 * kse, ks);
             continue;
@@ -672,8 +694,22 @@ void precompute(double eps, int mode, int K, const PrecomputeOptions& opt, Preco
           enlarge = true;
           break;
         }
-        if (p < 1) throw std::runtime_error("precompute: ID rank is zero");
-        finish_level(Yc, kse, piv, p, ladder[pan] * eps, out.reps[pan]);
+        if (p < 1) {
+          sketch_destroy(dsk);
+          throw std::runtime_error("precompute: ID rank is zero");
+        }
+        const double tc1 = now_s();
+        out.seconds_cpqr += tc1 - tc0;
+        if (dsk) {
+          if (!sketch_assemble(dsk, p, out.reps[pan].T)) {
+            sketch_destroy(dsk);
+            throw std::runtime_error("precompute: device assembly failed");
+          }
+          set_skeleton(piv, p, ladder[pan] * eps, out.reps[pan]);
+        } else {
+          finish_level(Yc, kse, piv, p, ladder[pan] * eps, out.reps[pan]);
+        }
+        out.seconds_assemble += now_s() - tc1;
       }
     }
     sketch_destroy(dsk);

@@ -50,6 +50,7 @@ struct Precomputed {
   std::vector<double> w;             // nf fine-grid weights
   std::vector<double> colloc;        // (mmax+1) x nrad x nrad when kept
   double seconds_onepatch = 0, seconds_id = 0;
+  double seconds_sketch = 0, seconds_cpqr = 0, seconds_assemble = 0;  // parts of seconds_id
 };
 
 // Basis ordering: n ascending, then m ascending, cos before sin; first K kept.

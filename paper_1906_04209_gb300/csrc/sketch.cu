@@ -1,15 +1,29 @@
-// Device accumulation of the ID sketch (see sketch.hpp): Y += Omega[:, r0:r1] A[r0:r1, :]
-// in FP64, A_tl = G(|x_t - x_l|) evaluated on the fly. Each block owns a 64 x 64 tile of Y
-// (sketch rows x fine points), stages 32 training rows of Omega and of A per step in shared
-// memory and accumulates 4 x 4 register tiles per thread.
+// The one-patch interpolative decompositions on the device (see sketch.hpp), all FP64:
+//   * sketch_kernel: Y += Omega[:, r0:r1] A[r0:r1, :], A_tl = G(|x_t - x_l|) evaluated on
+//     the fly; each block owns a 64 x 64 tile of Y (sketch rows x fine points), stages 32
+//     training rows of Omega and of A per step in shared memory and accumulates 4 x 4
+//     register tiles per thread;
+//   * column-pivoted Householder QR of the leading sketch rows, one pivot/reflector block
+//     and one column-update kernel per step (a warp per column), the host reading the
+//     stopping flag every 16 steps;
+//   * X = R11^-1 R12 by one back-substitution per column, T = W B[skeleton] + X W B[rest].
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <vector>
 
 #include "internal.hpp"
 #include "sketch.hpp"
 
 namespace ncs {
+
+// Status of the device CPQR, read by the host every few steps.
+struct CpqrStatus {
+  int done;    // the stopping rule fired
+  int p;       // completed steps (the rank once done)
+  double r00;  // |R_00|
+  double vv;   // |v|^2 of the current Householder vector
+};
 
 namespace {
 
@@ -78,12 +92,205 @@ __global__ void __launch_bounds__(SK_THREADS) sketch_kernel(int ks, int nt, int 
     }
 }
 
+constexpr int CP_THREADS = 1024;
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum over CP_THREADS threads (all must call); result in every thread.
+__device__ __forceinline__ double block_sum64(double v, double* red) {
+  v = warp_sum(v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int i = 0; i < CP_THREADS / 32; ++i) s += red[i];
+  return s;
+}
+
+// Yc (kse x nf) = first kse rows of Y (ks x nf), column norms, identity order. One warp per column.
+__global__ void cpqr_init_kernel(int ks, int kse, int nf, const double* __restrict__ Y, double* __restrict__ Yc,
+                                 double* __restrict__ cn, double* __restrict__ cn0, int* __restrict__ piv) {
+  const int l = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (l >= nf) return;
+  double s = 0.0;
+  for (int r = lane; r < kse; r += 32) {
+    const double y = Y[(int64_t)l * ks + r];
+    Yc[(int64_t)l * kse + r] = y;
+    s += y * y;
+  }
+  s = warp_sum(s);
+  if (lane == 0) {
+    cn[l] = cn0[l] = s;
+    piv[l] = l;
+  }
+}
+
+// Step st, part 1 (one block): pivot column = largest remaining norm (lowest index on
+// ties), swapped into place; Householder vector v of its rows st.. and R_st,st.
+__global__ void __launch_bounds__(CP_THREADS) cpqr_pivot_kernel(int kse, int nf, int st, double tol,
+                                                                double* __restrict__ Yc, double* __restrict__ cn,
+                                                                double* __restrict__ cn0, int* __restrict__ piv,
+                                                                double* __restrict__ v, CpqrStatus* __restrict__ S) {
+  __shared__ double red[CP_THREADS / 32];
+  __shared__ double bv[CP_THREADS / 32];
+  __shared__ int bi[CP_THREADS / 32];
+  __shared__ int best_s;
+  if (S->done) return;
+  double best = -1.0;
+  int bidx = nf;
+  for (int l = st + threadIdx.x; l < nf; l += CP_THREADS)
+    if (cn[l] > best) {
+      best = cn[l];
+      bidx = l;
+    }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+    if (ob > best || (ob == best && oi < bidx)) {
+      best = ob;
+      bidx = oi;
+    }
+  }
+  if ((threadIdx.x & 31) == 0) {
+    bv[threadIdx.x >> 5] = best;
+    bi[threadIdx.x >> 5] = bidx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = bv[0];
+    int i = bi[0];
+    for (int w = 1; w < CP_THREADS / 32; ++w)
+      if (bv[w] > b || (bv[w] == b && bi[w] < i)) {
+        b = bv[w];
+        i = bi[w];
+      }
+    best_s = i < nf ? i : st;
+  }
+  __syncthreads();
+  const int bst = best_s;
+  double* col = Yc + (int64_t)st * kse;
+  if (bst != st) {
+    double* other = Yc + (int64_t)bst * kse;
+    for (int r = threadIdx.x; r < kse; r += CP_THREADS) {
+      const double t = col[r];
+      col[r] = other[r];
+      other[r] = t;
+    }
+    if (threadIdx.x == 0) {
+      double t = cn[st];
+      cn[st] = cn[bst];
+      cn[bst] = t;
+      t = cn0[st];
+      cn0[st] = cn0[bst];
+      cn0[bst] = t;
+      const int ti = piv[st];
+      piv[st] = piv[bst];
+      piv[bst] = ti;
+    }
+  }
+  __syncthreads();
+  double a = 0.0;
+  for (int r = st + threadIdx.x; r < kse; r += CP_THREADS) a += col[r] * col[r];
+  const double nrm = sqrt(block_sum64(a, red));
+  const double c0 = col[st];
+  const double rss = (c0 >= 0.0) ? -nrm : nrm;
+  const double r00 = (st == 0) ? fabs(rss) : S->r00;
+  __syncthreads();
+  if (fabs(rss) < tol * r00 || nrm == 0.0) {
+    if (threadIdx.x == 0) {
+      S->done = 1;
+      S->p = st;
+      if (st == 0) S->r00 = r00;
+    }
+    return;
+  }
+  double b2 = 0.0;
+  for (int r = threadIdx.x; r < kse; r += CP_THREADS) {
+    const double vr = (r < st) ? 0.0 : (r == st ? col[r] - rss : col[r]);
+    v[r] = vr;
+    b2 += vr * vr;
+  }
+  const double vv = block_sum64(b2, red);
+  for (int r = st + threadIdx.x; r < kse; r += CP_THREADS) col[r] = (r == st) ? rss : 0.0;
+  if (threadIdx.x == 0) {
+    S->vv = vv;
+    S->r00 = r00;
+    S->p = st + 1;
+  }
+}
+
+// Step st, part 2: apply the reflector to the remaining columns and downdate their norms
+// (recomputed after cancellation). One warp per column.
+__global__ void cpqr_update_kernel(int kse, int nf, int st, double* __restrict__ Yc, double* __restrict__ cn,
+                                   double* __restrict__ cn0, const double* __restrict__ v,
+                                   const CpqrStatus* __restrict__ S) {
+  if (S->done) return;
+  const int l = st + 1 + (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (l >= nf) return;
+  double* y = Yc + (int64_t)l * kse;
+  double d = 0.0;
+  for (int r = st + lane; r < kse; r += 32) d += v[r] * y[r];
+  d = warp_sum(d);
+  const double f = 2.0 * d / S->vv;
+  for (int r = st + lane; r < kse; r += 32) y[r] -= f * v[r];
+  __syncwarp();
+  const double yst = y[st];
+  double nn = cn[l] - yst * yst;
+  if (nn < 1e-10 * cn0[l]) {
+    double q = 0.0;
+    for (int r = st + 1 + lane; r < kse; r += 32) q += y[r] * y[r];
+    nn = warp_sum(q);
+    if (lane == 0) cn0[l] = nn;
+  }
+  if (lane == 0) cn[l] = nn;
+}
+
+// X = R11^-1 R12 (p x nrest, row-major): one back-substitution per rest column.
+__global__ void cpqr_solve_x_kernel(int kse, int p, int nf, const double* __restrict__ Yc, double* __restrict__ X) {
+  const int nrest = nf - p;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nrest) return;
+  const double* y = Yc + (int64_t)(p + c) * kse;
+  for (int m = p - 1; m >= 0; --m) {
+    double val = y[m];
+    for (int q = m + 1; q < p; ++q) val -= Yc[(int64_t)q * kse + m] * X[(int64_t)q * nrest + c];
+    X[(int64_t)m * nrest + c] = val / Yc[(int64_t)m * kse + m];
+  }
+}
+
+// T[m][j] = WB[piv[m]][j] + sum_c X[m][c] WB[piv[p + c]][j] (eq. Tmap); one thread per entry.
+__global__ void assemble_t_kernel(int p, int K, int nf, const int* __restrict__ piv, const double* __restrict__ X,
+                                  const double* __restrict__ WB, double* __restrict__ T) {
+  const int m = blockIdx.y, j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= K) return;
+  const int nrest = nf - p;
+  const double* xm = X + (int64_t)m * nrest;
+  double t0 = WB[(int64_t)piv[m] * K + j], t1 = 0.0, t2 = 0.0, t3 = 0.0;
+  int c = 0;
+  for (; c + 4 <= nrest; c += 4) {
+    t0 = fma(xm[c], WB[(int64_t)piv[p + c] * K + j], t0);
+    t1 = fma(xm[c + 1], WB[(int64_t)piv[p + c + 1] * K + j], t1);
+    t2 = fma(xm[c + 2], WB[(int64_t)piv[p + c + 2] * K + j], t2);
+    t3 = fma(xm[c + 3], WB[(int64_t)piv[p + c + 3] * K + j], t3);
+  }
+  for (; c < nrest; ++c) t0 = fma(xm[c], WB[(int64_t)piv[p + c] * K + j], t0);
+  T[(int64_t)m * K + j] = (t0 + t1) + (t2 + t3);
+}
+
 }  // namespace
 
 struct DeviceSketch {
   int ks = 0, nt = 0, nf = 0;
   double sgn = 1.0;
   double *Om = nullptr, *xt = nullptr, *xf = nullptr, *Y = nullptr;
+  // CPQR of the first kse rows and assembly of T
+  int kse = 0, K = 0;
+  double *Yc = nullptr, *cn = nullptr, *cn0 = nullptr, *v = nullptr, *X = nullptr, *WB = nullptr, *T = nullptr;
+  int* piv = nullptr;
+  CpqrStatus* st = nullptr;
   cudaStream_t stream = nullptr;
 };
 
@@ -93,6 +300,15 @@ void sketch_destroy(DeviceSketch* s) {
   cudaFree(s->xt);
   cudaFree(s->xf);
   cudaFree(s->Y);
+  cudaFree(s->Yc);
+  cudaFree(s->cn);
+  cudaFree(s->cn0);
+  cudaFree(s->v);
+  cudaFree(s->X);
+  cudaFree(s->WB);
+  cudaFree(s->T);
+  cudaFree(s->piv);
+  cudaFree(s->st);
   if (s->stream) cudaStreamDestroy(s->stream);
   delete s;
 }
@@ -143,5 +359,79 @@ bool sketch_read(DeviceSketch* s, double* Y) {
              cudaSuccess &&
          cudaStreamSynchronize(s->stream) == cudaSuccess;
 }
+
+int sketch_cpqr(DeviceSketch* s, int kse, double tol, std::vector<int>& piv) {
+  const int nf = s->nf;
+  if (kse > s->ks || kse < 1) return -1;
+  bool ok = true;
+  if (!s->Yc) {
+    ok = cudaMalloc(&s->Yc, (size_t)s->ks * nf * sizeof(double)) == cudaSuccess &&
+         cudaMalloc(&s->cn, (size_t)nf * sizeof(double)) == cudaSuccess &&
+         cudaMalloc(&s->cn0, (size_t)nf * sizeof(double)) == cudaSuccess &&
+         cudaMalloc(&s->v, (size_t)s->ks * sizeof(double)) == cudaSuccess &&
+         cudaMalloc(&s->piv, (size_t)nf * sizeof(int)) == cudaSuccess &&
+         cudaMalloc(&s->st, sizeof(CpqrStatus)) == cudaSuccess;
+    if (!ok) return -1;
+  }
+  s->kse = kse;
+  const CpqrStatus zero{0, 0, 0.0, 1.0};
+  if (cudaMemcpyAsync(s->st, &zero, sizeof(zero), cudaMemcpyHostToDevice, s->stream) != cudaSuccess) return -1;
+  const unsigned wblocks = (unsigned)(((int64_t)nf * 32 + 255) / 256);
+  count_launch(), cpqr_init_kernel<<<wblocks, 256, 0, s->stream>>>(s->ks, kse, nf, s->Y, s->Yc, s->cn, s->cn0,
+                                                                   s->piv);
+  if (cudaGetLastError() != cudaSuccess) return -1;
+  CpqrStatus h{};
+  for (int st = 0; st < kse; ++st) {
+    count_launch(), cpqr_pivot_kernel<<<1, CP_THREADS, 0, s->stream>>>(kse, nf, st, tol, s->Yc, s->cn, s->cn0, s->piv,
+                                                                       s->v, s->st);
+    const int rest = nf - st - 1;
+    if (rest > 0) {
+      const unsigned ub = (unsigned)(((int64_t)rest * 32 + 255) / 256);
+      count_launch(), cpqr_update_kernel<<<ub, 256, 0, s->stream>>>(kse, nf, st, s->Yc, s->cn, s->cn0, s->v, s->st);
+    }
+    if (cudaGetLastError() != cudaSuccess) return -1;
+    if ((st & 15) == 15 || st == kse - 1) {
+      if (cudaMemcpyAsync(&h, s->st, sizeof(h), cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
+          cudaStreamSynchronize(s->stream) != cudaSuccess)
+        return -1;
+      if (h.done) break;
+    }
+  }
+  piv.resize(nf);
+  if (cudaMemcpyAsync(piv.data(), s->piv, (size_t)nf * sizeof(int), cudaMemcpyDeviceToHost, s->stream) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(&h, s->st, sizeof(h), cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
+      cudaStreamSynchronize(s->stream) != cudaSuccess)
+    return -1;
+  return h.done ? h.p : kse;
+}
+
+bool sketch_set_wb(DeviceSketch* s, int K, const double* WB) {
+  s->K = K;
+  const size_t n = (size_t)s->nf * K;
+  return (s->WB || cudaMalloc(&s->WB, n * sizeof(double)) == cudaSuccess) &&
+         cudaMemcpyAsync(s->WB, WB, n * sizeof(double), cudaMemcpyHostToDevice, s->stream) == cudaSuccess &&
+         cudaStreamSynchronize(s->stream) == cudaSuccess;
+}
+
+bool sketch_assemble(DeviceSketch* s, int p, std::vector<double>& T) {
+  const int nf = s->nf, K = s->K, nrest = nf - p;
+  if (!s->WB || p < 1 || p > s->kse || nrest < 0) return false;
+  if (!s->X && cudaMalloc(&s->X, (size_t)s->ks * nf * sizeof(double)) != cudaSuccess) return false;
+  if (!s->T && cudaMalloc(&s->T, (size_t)s->ks * K * sizeof(double)) != cudaSuccess) return false;
+  if (nrest > 0) {
+    count_launch(), cpqr_solve_x_kernel<<<(unsigned)((nrest + 127) / 128), 128, 0, s->stream>>>(s->kse, p, nf, s->Yc,
+                                                                                                 s->X);
+    if (cudaGetLastError() != cudaSuccess) return false;
+  }
+  dim3 grid((unsigned)((K + 127) / 128), (unsigned)p);
+  count_launch(), assemble_t_kernel<<<grid, 128, 0, s->stream>>>(p, K, nf, s->piv, s->X, s->WB, s->T);
+  if (cudaGetLastError() != cudaSuccess) return false;
+  T.resize((size_t)p * K);
+  return cudaMemcpyAsync(T.data(), s->T, T.size() * sizeof(double), cudaMemcpyDeviceToHost, s->stream) ==
+             cudaSuccess &&
+         cudaStreamSynchronize(s->stream) == cudaSuccess;
+}
+
 
 }  // namespace ncs

@@ -228,9 +228,10 @@ class Context:
         return dict(zip(keys, [int(v) for v in out]))
 
     def timings(self):
-        """[one-patch seconds, ID seconds, 1 if the ID sketch ran on the device]"""
-        out = np.zeros(3)
-        load().ncs_timings(self.h, _ptr(out), 3)
+        """[one-patch s, ID s, 1 if the ID sketch ran on the device, sketch s, CPQR s,
+        T assembly s]"""
+        out = np.zeros(6)
+        load().ncs_timings(self.h, _ptr(out), 6)
         return out
 
     def operator(self):

@@ -1,6 +1,7 @@
-"""The ID sketch of the one-patch precompute (Section 7.1) formed on the device gives
-the same compressed operator as the host sketch: same skeleton counts, and products that
-agree to the ID tolerance."""
+"""The interpolative decompositions of the one-patch precompute (Section 7.1) run on the
+device (sketch, column-pivoted QRs, T assembly) give the same compressed operator as the
+host path: same skeleton counts (within one point), and products that agree to the ID
+tolerance."""
 import time
 
 import numpy as np
