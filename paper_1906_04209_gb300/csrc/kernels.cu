@@ -22,7 +22,7 @@ struct Vec4<float> {
 };
 template <>
 struct Vec4<double> {
-  using type = double4;
+  using type = double4_16a;
 };
 
 // ---------------------------------------------------------------------------
@@ -327,7 +327,7 @@ cudaError_t launch_direct_field(const DeviceData& d, int mode, int prec, double 
     }
     return cudaGetLastError();
   }
-  const size_t v4 = (prec == NCS_FP64) ? sizeof(double4) : sizeof(float4);
+  const size_t v4 = (prec == NCS_FP64) ? sizeof(double4_16a) : sizeof(float4);
   int JT = (int)std::min<size_t>(DF_JTMAX, (40 * 1024) / (v4 * (size_t)d.pmax));
   if (JT < 1) JT = 1;
   const size_t smem = (size_t)JT * d.pmax * v4;

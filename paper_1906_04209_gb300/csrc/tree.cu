@@ -31,7 +31,7 @@ struct V4T<float> {
 };
 template <>
 struct V4T<double> {
-  using type = double4;
+  using type = double4_16a;
 };
 
 template <typename T>
