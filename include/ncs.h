@@ -93,12 +93,14 @@ typedef struct ncs_params {
                           Section 7.1 recompression), default 1.0; 0: only the 2 eps one.
                           Fewer representations shorten the host precompute (one CPQR of
                           the sketch per representation) and lengthen the products */
-  int device_precompute;/* 1 (default): the precompute runs its interpolative
-                          decompositions (the Gaussian sketch of the far-field kernel
-                          matrix, ~1e10 FP64 FMAs, the column-pivoted QRs and the T
-                          assembly) on the CUDA device current at ncs_create when there is
-                          one, else on the host; 0: always on the host. The one-patch
-                          modal solves stay on the host */
+  int device_precompute;/* 1 (default): the precompute forms the one-patch modal
+                          collocation matrices (Section 8.2; the modal kernels at every
+                          quadrature node, ~1e5 nodes x ~500 theta nodes) and runs its
+                          interpolative decompositions (the Gaussian sketch of the
+                          far-field kernel matrix, ~1e10 FP64 FMAs, the column-pivoted QRs
+                          and the T assembly) on the CUDA device current at ncs_create
+                          when there is one, else on the host; 0: always on the host. The
+                          per-mode LUs and solves stay on the host */
 } ncs_params;
 
 /* Fills *p with the defaults listed above. */
@@ -162,7 +164,9 @@ int ncs_info(const ncs_ctx* ctx, int64_t* out, int n);
 
 /* Precompute timings in seconds: out[0] one-patch solve, out[1] ID; out[2] = 1 if the ID
  * ran on a CUDA device, else 0; parts of out[1]: out[3] sketch, out[4] CPQRs, out[5]
- * assembly of the T operators. */
+ * assembly of the T operators; out[6] = 1 if the modal collocation matrices were formed
+ * on a CUDA device, else 0; parts of out[0]: out[7] collocation matrices, out[8] LUs and
+ * modal solves. n < 9 fills the first n. */
 int ncs_timings(const ncs_ctx* ctx, double* out, int n);
 
 /*

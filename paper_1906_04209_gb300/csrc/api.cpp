@@ -493,6 +493,7 @@ int ncs_create(double eps, int mode, int K, const ncs_params* params, ncs_ctx** 
     o.threads = c->prm.threads;
     o.id_ladder_max = c->prm.id_ladder_max;
     o.device_sketch = c->prm.device_precompute != 0;
+    o.device_colloc = c->prm.device_precompute != 0;
     try {
       ncs::precompute(eps, mode, K, o, c->pc);
     } catch (const std::exception& e) {
@@ -644,6 +645,9 @@ int ncs_timings(const ncs_ctx* c, double* out, int n) {
   if (n > 3) out[3] = c->pc.seconds_sketch;
   if (n > 4) out[4] = c->pc.seconds_cpqr;
   if (n > 5) out[5] = c->pc.seconds_assemble;
+  if (n > 6) out[6] = c->pc.colloc_on_device ? 1.0 : 0.0;
+  if (n > 7) out[7] = c->pc.seconds_colloc;
+  if (n > 8) out[8] = c->pc.seconds_lu;
   return NCS_OK;
 }
 

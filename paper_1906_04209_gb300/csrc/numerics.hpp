@@ -227,23 +227,6 @@ struct LU {
   }
 };
 
-// Complete elliptic integrals K(k), E(k) given k^2 and k'^2 = 1 - k^2 (k' passed
-// separately for accuracy near k = 1); arithmetic-geometric mean method.
-inline void ellipke(double k2, double kp2, double* K, double* E) {
-  double a = 1.0, b = std::sqrt(kp2), c = std::sqrt(k2);
-  double sum = 0.5 * c * c, pw = 0.5;
-  for (int it = 0; it < 60; ++it) {
-    double an = 0.5 * (a + b), bn = std::sqrt(a * b), cn = 0.5 * (a - b);
-    a = an;
-    b = bn;
-    pw *= 2.0;
-    sum += pw * cn * cn;
-    if (std::fabs(cn) <= 1e-17 * a) break;
-  }
-  *K = kPi / (2.0 * a);
-  *E = *K * (1.0 - sum);
-}
-
 // Counter-based standard normal variates (splitmix64 + Box-Muller).
 inline uint64_t splitmix64(uint64_t x) {
   x += 0x9E3779B97F4A7C15ull;

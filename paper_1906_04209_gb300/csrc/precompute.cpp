@@ -23,7 +23,9 @@
 #include <cstdio>
 #include <stdexcept>
 
+#include "modal.hpp"
 #include "numerics.hpp"
+#include "onepatch.hpp"
 #ifdef _OPENMP
 #include <omp.h>
 #endif
@@ -176,61 +178,12 @@ void local_offset(double t, double th, double* o) {
 }
 
 void modal_coulomb(double t, double tp, int nmax, double* out) {
-  const double st = std::sin(t) * std::sin(tp);
-  const double sh = std::sin(0.5 * (t - tp));
-  const double chim1 = 2.0 * sh * sh / st;  // chi - 1, accurate for t ~ t'
-  const double chi = 1.0 + chim1;
-  const double k2 = 2.0 / (2.0 + chim1), kp2 = chim1 / (2.0 + chim1);
-  double K, E;
-  ellipke(k2, kp2, &K, &E);
-  const double k = std::sqrt(k2);
-  const double Q0 = k * K;  // Q_{-1/2}(chi)
-  const double pref = 2.0 / (kPi * std::sqrt(st));
-  out[0] = pref * Q0;
-  if (nmax == 0) return;
-  const double lnal = std::log(chi + std::sqrt(chim1 * (2.0 + chim1)));
-  if (2.0 * nmax * lnal < std::log(100.0)) {
-    // forward recurrence (at most two digits of growth)
-    double qm = Q0, q = chi * k * K - 2.0 * E / k;  // Q_{1/2}
-    out[1] = pref * q;
-    for (int n = 1; n < nmax; ++n) {
-      double qn = (2.0 * n * chi * q - (n - 0.5) * qm) / (n + 0.5);
-      qm = q;
-      q = qn;
-      out[n + 1] = pref * q;
-    }
-    return;
-  }
-  // Miller backward recurrence normalised by Q_{-1/2}
-  const int N = nmax + (int)std::ceil(18.5 / lnal) + 10;
-  double qp = 0.0, q = 1.0;
-  double tmp[512];
-  if (nmax >= 512) throw std::runtime_error("modal_coulomb: nmax too large");
-  for (int n = N; n >= 1; --n) {
-    double qm = (2.0 * n * chi * q - (n + 0.5) * qp) / (n - 0.5);
-    qp = q;
-    q = qm;
-    if (n - 1 <= nmax) tmp[n - 1] = q;
-    if (n <= nmax) tmp[n] = qp;
-    if (std::fabs(q) > 1e250) {
-      q *= 1e-250;
-      qp *= 1e-250;
-      for (int j = n - 1; j <= nmax; ++j) tmp[j] *= 1e-250;
-    }
-  }
-  const double scale = Q0 / tmp[0];
-  for (int n = 0; n <= nmax; ++n) out[n] = pref * tmp[n] * scale;
+  if (!modal::coulomb_modes<512>(t, tp, nmax, out)) throw std::runtime_error("modal_coulomb: nmax too large");
 }
 
 void modal_log(double t, double tp, int nmax, double* out) {
-  const double t1 = std::min(t, tp), t2 = std::max(t, tp);
-  out[0] = -std::log(std::cos(0.5 * t1) * std::sin(0.5 * t2));
-  const double ratio = std::tan(0.5 * t1) / std::tan(0.5 * t2);
-  double pw = 1.0;
-  for (int n = 1; n <= nmax; ++n) {
-    pw *= ratio;
-    out[n] = pw / (2.0 * n);
-  }
+  for (int n = 0; n <= nmax; ++n) out[n] = 0.0;
+  modal::log_modes_add(t, tp, nmax, 1.0, out);
 }
 
 void modal_log1p(double t, double tp, int nmax, double* out) {
@@ -331,51 +284,121 @@ void precompute(double eps, int mode, int K, const PrecomputeOptions& opt, Preco
   std::vector<double> nodes_gl(gx), nodes_gj(jx);
   const Lagrange lag_gl(nodes_gl), lag_gj(nodes_gj);
 
-  // ---- collocation matrices A_n (n = 0..mmax), row-major nr x nr each
-  std::vector<double> A((size_t)(mmax + 1) * nr * nr, 0.0);
+  // ---- collocation matrices A_n (n = 0..mmax), row-major nr x nr each. Row i against
+  // panel j integrates G_n(t_i, t') times the panel's Lagrange basis with a rule graded
+  // toward t' = t_i; on the Gauss-Jacobi panel the rule is taken in u = sqrt(eps - t').
+  auto colloc_rule = [&](int i, int j, std::vector<double>& xq, std::vector<double>& wq) {
+    const double a = edges[j], ti = tr[i];
+    if (j < npan - 1) {
+      singular_rule(a, edges[j + 1], ti, xq, wq);
+      return;
+    }
+    // t' = eps - u^2 on u in [0, sqrt(eps - a)]: (eps - t')^(-1/2) dt' = 2 du
+    const double U = std::sqrt(eps - a), su = std::sqrt(std::max(eps - ti, 0.0));
+    // dt'/du = -2u: keep t' >= ~30 ulp away from t_i near u = su
+    const double hu = su > 0.0 ? std::max(2e-13 * U, 2e-13 * eps / su) : 0.0;
+    singular_rule(0.0, U, su, xq, wq, hu);
+    for (size_t q = 0; q < xq.size(); ++q) {
+      double u = xq[q];
+      xq[q] = eps - u * u;
+      wq[q] *= 2.0;
+    }
+  };
+  // column factors: the Jacobi panel's unknowns are g(t_k) = sigma(t_k) sqrt(eps - t_k)
+  std::vector<double> colscale(nr, 1.0);
+  for (int k = 0; k < nord; ++k) colscale[(npan - 1) * nord + k] = std::sqrt(eps - tr[(npan - 1) * nord + k]);
+  const double tc0 = now_s();
+  std::vector<double> A;
+  out.colloc_on_device = false;
+  if (opt.device_colloc && nord <= kCollocMaxOrd && mmax < kCollocMaxModes) {
+    CollocProblem pr;
+    pr.nr = nr;
+    pr.npan = npan;
+    pr.nord = nord;
+    pr.nmodes = mmax + 1;
+    pr.mode = mode;
+    pr.tr = tr;
+    pr.colscale = colscale;
+    pr.lag_nodes = gx;
+    pr.lag_nodes.insert(pr.lag_nodes.end(), jx.begin(), jx.end());
+    pr.lag_bw = lag_gl.bw;
+    pr.lag_bw.insert(pr.lag_bw.end(), lag_gj.bw.begin(), lag_gj.bw.end());
+    // every (row, panel) rule, built per row in parallel and concatenated in (i, j) order
+    std::vector<std::vector<double>> rows(nr);
+    std::vector<int> cnt((size_t)nr * npan);
 #pragma omp parallel
-  {
-    std::vector<double> xq, wq, Gn(mmax + 1), L(nord);
-#pragma omp for schedule(dynamic, 1)
-    for (int i = 0; i < nr; ++i) {
-      const double ti = tr[i];
-      for (int j = 0; j < npan; ++j) {
-        const double a = edges[j], b = edges[j + 1];
-        const double mid = 0.5 * (a + b), half = 0.5 * (b - a);
-        const bool jac = (j == npan - 1);
-        if (!jac) {
-          singular_rule(a, b, ti, xq, wq);
-        } else {
-          // t' = eps - u^2 on u in [0, sqrt(eps - a)]: (eps - t')^(-1/2) dt' = 2 du
-          const double U = std::sqrt(eps - a), su = std::sqrt(std::max(eps - ti, 0.0));
-          // dt'/du = -2u: keep t' >= ~30 ulp away from t_i near u = su
-          const double hu = su > 0.0 ? std::max(2e-13 * U, 2e-13 * eps / su) : 0.0;
-          singular_rule(0.0, U, su, xq, wq, hu);
+    {
+      std::vector<double> xq, wq;
+#pragma omp for schedule(dynamic, 4)
+      for (int i = 0; i < nr; ++i) {
+        std::vector<double>& r = rows[i];
+        for (int j = 0; j < npan; ++j) {
+          colloc_rule(i, j, xq, wq);
+          const double mid = 0.5 * (edges[j] + edges[j + 1]), half = 0.5 * (edges[j + 1] - edges[j]);
           for (size_t q = 0; q < xq.size(); ++q) {
-            double u = xq[q];
-            xq[q] = eps - u * u;
-            wq[q] *= 2.0;
+            r.push_back(xq[q]);
+            r.push_back(2.0 * kPi * wq[q] * std::sin(xq[q]));
+            r.push_back((xq[q] - mid) / half);
           }
+          cnt[(size_t)i * npan + j] = (int)xq.size();
         }
-        for (size_t q = 0; q < xq.size(); ++q) {
-          const double tq = xq[q];
-          modal_kernels(ti, tq, mmax, mode, Gn.data());
-          (jac ? lag_gj : lag_gl).eval((tq - mid) / half, L.data());
-          const double wt = 2.0 * kPi * wq[q] * std::sin(tq);
-          for (int k = 0; k < nord; ++k) {
-            double lk = L[k];
-            if (jac) lk *= std::sqrt(eps - tr[j * nord + k]);  // g(t_k) = sigma(t_k) sqrt(eps - t_k)
-            const double c = wt * lk;
-            for (int n = 0; n <= mmax; ++n) A[((size_t)n * nr + i) * nr + j * nord + k] += c * Gn[n];
+      }
+    }
+    pr.qoff.assign((size_t)nr * npan + 1, 0);
+    for (size_t b = 0; b < cnt.size(); ++b) pr.qoff[b + 1] = pr.qoff[b] + cnt[b];
+    const size_t nq = (size_t)pr.qoff.back();
+    pr.tq.reserve(nq);
+    pr.wt.reserve(nq);
+    pr.ls.reserve(nq);
+    for (int i = 0; i < nr; ++i)
+      for (size_t q = 0; q < rows[i].size(); q += 3) {
+        pr.tq.push_back(rows[i][q]);
+        pr.wt.push_back(rows[i][q + 1]);
+        pr.ls.push_back(rows[i][q + 2]);
+      }
+    const ThetaRule& R = theta_rule(mmax);
+    pr.hs2 = R.half_sin2;
+    pr.cw.resize(R.th.size() * (size_t)(mmax + 1));
+    for (size_t it = 0; it < R.th.size(); ++it)
+      for (int n = 0; n <= mmax; ++n) pr.cw[it * (mmax + 1) + n] = R.cosn[it * (R.nmax + 1) + n];
+    std::string err;
+    const int rc = colloc_assemble_device(pr, A, &err);
+    if (rc < 0) throw std::runtime_error(err);
+    out.colloc_on_device = rc > 0;
+  }
+  if (!out.colloc_on_device) {
+    A.assign((size_t)(mmax + 1) * nr * nr, 0.0);
+#pragma omp parallel
+    {
+      std::vector<double> xq, wq, Gn(mmax + 1), L(nord);
+#pragma omp for schedule(dynamic, 1)
+      for (int i = 0; i < nr; ++i) {
+        const double ti = tr[i];
+        for (int j = 0; j < npan; ++j) {
+          const double mid = 0.5 * (edges[j] + edges[j + 1]), half = 0.5 * (edges[j + 1] - edges[j]);
+          const bool jac = (j == npan - 1);
+          colloc_rule(i, j, xq, wq);
+          for (size_t q = 0; q < xq.size(); ++q) {
+            const double tq = xq[q];
+            modal_kernels(ti, tq, mmax, mode, Gn.data());
+            (jac ? lag_gj : lag_gl).eval((tq - mid) / half, L.data());
+            const double wt = 2.0 * kPi * wq[q] * std::sin(tq);
+            for (int k = 0; k < nord; ++k) {
+              const double c = wt * (L[k] * colscale[j * nord + k]);
+              for (int n = 0; n <= mmax; ++n) A[((size_t)n * nr + i) * nr + j * nord + k] += c * Gn[n];
+            }
           }
         }
       }
     }
   }
+  const double tc1 = now_s();
+  out.seconds_colloc = tc1 - tc0;
 
   // ---- one LU per mode; beta_j solves the mode-m_j system with rhs c_j R(t/eps)
   if (opt.keep_collocation) out.colloc = A;
   std::vector<LU> lus(mmax + 1);
+#pragma omp parallel for schedule(dynamic, 1)
   for (int n = 0; n <= mmax; ++n) lus[n].factor(&A[(size_t)n * nr * nr], nr);
   out.nrad = nr;
   out.trad = tr;
@@ -389,6 +412,7 @@ void precompute(double eps, int mode, int K, const PrecomputeOptions& opt, Preco
       for (int i = 0; i < nr; ++i) out.beta[(size_t)i * K + j] = rhs[i];
     }
   }
+  out.seconds_lu = now_s() - tc1;
 
   // ---- fine grid, weights and I = w^T B
   int nth = opt.ntheta_fine > 0 ? opt.ntheta_fine : M + 40;

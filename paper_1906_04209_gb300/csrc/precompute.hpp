@@ -18,6 +18,7 @@ struct PrecomputeOptions {
   bool multilevel = true;   // also compress against farther regions (ladder x 2^(1/3))
   double id_ladder_max = 1.0;  // largest far-field radius of the ladder (radians)
   bool device_sketch = false;  // form the ID sketch on the current CUDA device when one exists
+  bool device_colloc = false;  // form the modal collocation matrices on the current CUDA device
   bool keep_collocation = false;  // keep the modal collocation matrices (diagnostics)
 };
 
@@ -45,12 +46,14 @@ struct Precomputed {
   std::vector<double> I;             // K
   std::vector<OutRep> reps;          // increasing rho_min; reps[0] equals (T, st, sth, sloc)
   bool sketch_on_device = false;     // the ID sketch was formed on a CUDA device
+  bool colloc_on_device = false;     // the collocation matrices were formed on a CUDA device
   std::vector<double> trad;          // radial collocation nodes
   std::vector<double> beta;          // nrad x K radial profiles
   std::vector<double> w;             // nf fine-grid weights
   std::vector<double> colloc;        // (mmax+1) x nrad x nrad when kept
   double seconds_onepatch = 0, seconds_id = 0;
   double seconds_sketch = 0, seconds_cpqr = 0, seconds_assemble = 0;  // parts of seconds_id
+  double seconds_colloc = 0, seconds_lu = 0;  // parts of seconds_onepatch: matrices, LUs + solves
 };
 
 // Basis ordering: n ascending, then m ascending, cos before sin; first K kept.

@@ -228,10 +228,11 @@ class Context:
         return dict(zip(keys, [int(v) for v in out]))
 
     def timings(self):
-        """[one-patch s, ID s, 1 if the ID sketch ran on the device, sketch s, CPQR s,
-        T assembly s]"""
-        out = np.zeros(6)
-        load().ncs_timings(self.h, _ptr(out), 6)
+        """[one-patch s, ID s, 1 if the ID ran on the device, sketch s, CPQR s,
+        T assembly s, 1 if the collocation matrices were formed on the device,
+        collocation s, LU + modal solves s]"""
+        out = np.zeros(9)
+        load().ncs_timings(self.h, _ptr(out), 9)
         return out
 
     def operator(self):

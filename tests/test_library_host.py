@@ -109,12 +109,15 @@ def test_set_patches_validation(libncs):
 
 
 def test_precompute_without_device_uses_host_sketch(libncs):
-    # without a CUDA device the ID sketch is formed on the host whatever the parameter says
+    # without a CUDA device the ID sketch and the collocation matrices are formed on the host
+    # whatever the parameter says
     torch = pytest.importorskip("torch")
     if torch.cuda.is_available():
         pytest.skip("a CUDA device is present")
     c = ncs.Context(0.05, INTERIOR, 10, npan=6, nord=10, ntheta_fine=24, device_precompute=1)
-    assert c.timings()[2] == 0.0
+    t = c.timings()
+    assert t[2] == 0.0 and t[6] == 0.0
+    assert t[7] > 0.0 and t[8] >= 0.0 and t[7] + t[8] <= t[0] + 1e-9
 
 
 def test_launch_count_without_gpu(libncs):
