@@ -147,4 +147,165 @@ __device__ __forceinline__ void pair_loop32(const float4* __restrict__ S, int ns
   }
 }
 
+// ---- packed pairs: sm_100+ f32x2 arithmetic -------------------------------------------
+// add/sub/mul/fma .rn.f32x2 perform two IEEE single-precision operations (one per 32-bit
+// half of a 64-bit register) in one instruction, each rounded exactly as the scalar
+// instruction would round it. The packed pair loop below evaluates the same operation
+// sequence as pair32 / pair32_poly for two sources at once, so a pair's value is unchanged
+// and the issue slots of its FP32 arithmetic are halved; that leaves room on the FMA pipe
+// for more logarithms by lg2_poly, the MUFU unit being the other bound.
+typedef unsigned long long f32x2;
+
+__device__ __forceinline__ f32x2 x2_pack(float lo, float hi) {
+  f32x2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void x2_unpack(f32x2 v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f32x2 x2_add(f32x2 a, f32x2 b) {
+  f32x2 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f32x2 x2_sub(f32x2 a, f32x2 b) {
+  f32x2 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f32x2 x2_mul(f32x2 a, f32x2 b) {
+  f32x2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f32x2 x2_fma(f32x2 a, f32x2 b, f32x2 c) {
+  f32x2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
+// The packed constants of a pair loop, formed once per call.
+struct PairX2Consts {
+  f32x2 one, nln2, bias, c[9];
+  __device__ __forceinline__ PairX2Consts() {
+    one = x2_pack(1.0f, 1.0f);
+    nln2 = x2_pack(-kLn2f, -kLn2f);
+    bias = x2_pack(12582912.0f, 12582912.0f);
+    const float cf[9] = {1.224903390e-01f,  -2.088673115e-01f, 2.178854942e-01f,
+                         -2.387827337e-01f, 2.876248062e-01f,  -3.607062101e-01f,
+                         4.809235036e-01f,  -7.213473916e-01f, 1.442694902e+00f};
+#pragma unroll
+    for (int k = 0; k < 9; ++k) c[k] = x2_pack(cf[k], cf[k]);
+  }
+};
+
+// lg2_poly on both halves: the same operations, the integer steps per half.
+__device__ __forceinline__ f32x2 lg2_poly_x2(f32x2 x, const PairX2Consts& k) {
+  float x0, x1;
+  x2_unpack(x, x0, x1);
+  const int i0 = __float_as_int(x0), i1 = __float_as_int(x1);
+  const int e0 = (i0 - 0x3f3504f3) >> 23, e1 = (i1 - 0x3f3504f3) >> 23;
+  const f32x2 f = x2_sub(x2_pack(__int_as_float(i0 - (e0 << 23)), __int_as_float(i1 - (e1 << 23))), k.one);
+  f32x2 p = k.c[0];
+#pragma unroll
+  for (int j = 1; j < 9; ++j) p = x2_fma(p, f, k.c[j]);
+  const f32x2 ef = x2_sub(x2_pack(__int_as_float(e0 + 0x4b400000), __int_as_float(e1 + 0x4b400000)), k.bias);
+  return x2_fma(f, p, ef);
+}
+
+// Two pairs (one target, the two sources of a staged pair) into the packed accumulator.
+// (X, Y) = (x pair, y pair), (Z, W) = (z pair, strength pair) of the sources.
+template <int MODE, bool POLY>
+__device__ __forceinline__ f32x2 pair32_x2(f32x2 ax, f32x2 ay, f32x2 az, const ulonglong2& XY,
+                                           const ulonglong2& ZW, f32x2 acc, const PairX2Consts& k) {
+  const f32x2 dx = x2_sub(ax, XY.x), dy = x2_sub(ay, XY.y), dz = x2_sub(az, ZW.x);
+  const f32x2 d2 = x2_fma(dx, dx, x2_fma(dy, dy, x2_mul(dz, dz)));
+  float d0, d1;
+  x2_unpack(d2, d0, d1);
+  const f32x2 rh = x2_pack(rsqrt_mufu(d0), rsqrt_mufu(d1));
+  const f32x2 arg = (MODE == 0) ? x2_add(k.one, rh) : x2_fma(d2, rh, d2);
+  f32x2 l;
+  if constexpr (POLY) {
+    l = lg2_poly_x2(arg, k);
+  } else {
+    float g0, g1;
+    x2_unpack(arg, g0, g1);
+    l = x2_pack(lg2_mufu(g0), lg2_mufu(g1));
+  }
+  return x2_fma(x2_fma(l, k.nln2, rh), ZW.y, acc);
+}
+
+// Staged sources in the paired layout of pair_loop32x2: sources 2k and 2k+1 share the 32
+// bytes S[2k], S[2k+1] = (x0, x1, y0, y1), (z0, z1, w0, w1).
+__device__ __forceinline__ void stage_source_x2(float4* S, int idx, float x, float y, float z, float w) {
+  float* f = reinterpret_cast<float*>(S) + 8 * (idx >> 1) + (idx & 1);
+  f[0] = x;
+  f[2] = y;
+  f[4] = z;
+  f[6] = w;
+}
+// An odd source count is padded with a zero-strength source far from every target
+// (half-scaled offsets have norm below 1.1; this one sits at distance > 2 from them).
+__device__ __forceinline__ void stage_pad_x2(float4* S, int ns) {
+  if (ns & 1) stage_source_x2(S, ns, 2.0f, 2.0f, 2.0f, 0.0f);
+}
+
+// NCS_PAIR_X2_POLY of every 16 two-pair chains (a target against a staged source pair)
+// take their logarithms with lg2_poly.
+#ifndef NCS_PAIR_X2_POLY
+#define NCS_PAIR_X2_POLY 6
+#endif
+
+// part[t] = sum over the ns staged sources (paired layout, padded to even) of G(a_t, s)
+// rho_s for the NT half-scaled targets: source pairs in groups of 8, the first
+// NCS_PAIR_X2_POLY of a group's 8 NT chains (scaled to NT) on lg2_poly.
+template <int MODE, int NT>
+__device__ __forceinline__ void pair_loop32x2(const float4* __restrict__ S, int ns, const float* ax, const float* ay,
+                                              const float* az, float* part) {
+  const PairX2Consts k;
+  const ulonglong2* S2 = reinterpret_cast<const ulonglong2*>(S);
+  f32x2 AX[NT], AY[NT], AZ[NT], P[NT];
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    AX[t] = x2_pack(ax[t], ax[t]);
+    AY[t] = x2_pack(ay[t], ay[t]);
+    AZ[t] = x2_pack(az[t], az[t]);
+    P[t] = x2_pack(0.0f, 0.0f);
+  }
+  constexpr int kPoly = NCS_PAIR_X2_POLY * NT / 2;  // poly chains per group of 8 * NT
+  const int np = (ns + 1) >> 1;
+  int s = 0;
+  for (; s + 8 <= np; s += 8) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const ulonglong2 XY = S2[2 * (s + u)], ZW = S2[2 * (s + u) + 1];
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        if (u * NT + t < kPoly)
+          P[t] = pair32_x2<MODE, true>(AX[t], AY[t], AZ[t], XY, ZW, P[t], k);
+        else
+          P[t] = pair32_x2<MODE, false>(AX[t], AY[t], AZ[t], XY, ZW, P[t], k);
+      }
+    }
+  }
+  for (; s < np; ++s) {
+    const ulonglong2 XY = S2[2 * s], ZW = S2[2 * s + 1];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) P[t] = pair32_x2<MODE, false>(AX[t], AY[t], AZ[t], XY, ZW, P[t], k);
+  }
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    float lo, hi;
+    x2_unpack(P[t], lo, hi);
+    part[t] = lo + hi;
+  }
+}
+
+// 1: the tree's FP32 pair kernels stage sources in the paired layout and run
+// pair_loop32x2; 0: float4 staging and pair_loop32.
+#ifndef NCS_PAIR_X2
+#define NCS_PAIR_X2 1
+#endif
+
 }  // namespace ncs

@@ -118,11 +118,18 @@ __global__ void __launch_bounds__(P2L_THREADS) p2l_kernel(
           v.x *= 0.5f;
           v.y *= 0.5f;
           v.z *= 0.5f;
+          if constexpr (NCS_PAIR_X2 != 0) {
+            stage_source_x2(reinterpret_cast<float4*>(S), idx, v.x, v.y, v.z, v.w);
+            continue;
+          }
         }
         S[idx] = v;
       }
-      __syncthreads();
       const int ns = nj * p;
+      if constexpr (sizeof(R) == 4 && NCS_PAIR_X2 != 0) {
+        if (threadIdx.x == 0) stage_pad_x2(reinterpret_cast<float4*>(S), ns);
+      }
+      __syncthreads();
       R part[P2L_NT];
 #pragma unroll
       for (int t = 0; t < P2L_NT; ++t) part[t] = 0;
@@ -130,10 +137,17 @@ __global__ void __launch_bounds__(P2L_THREADS) p2l_kernel(
       const int wbase = base + (threadIdx.x & ~31);
       const int nact = (wbase >= q) ? 0 : ((wbase + P2L_THREADS >= q) ? 1 : P2L_NT);
       if constexpr (sizeof(R) == 4) {
-        if (nact == P2L_NT)
-          pair_loop32<MODE, P2L_NT>(S, ns, ax, ay, az, part);
-        else if (nact == 1)
-          pair_loop32<MODE, 1>(S, ns, ax, ay, az, part);
+        if constexpr (NCS_PAIR_X2 != 0) {
+          if (nact == P2L_NT)
+            pair_loop32x2<MODE, P2L_NT>(S, ns, ax, ay, az, part);
+          else if (nact == 1)
+            pair_loop32x2<MODE, 1>(S, ns, ax, ay, az, part);
+        } else {
+          if (nact == P2L_NT)
+            pair_loop32<MODE, P2L_NT>(S, ns, ax, ay, az, part);
+          else if (nact == 1)
+            pair_loop32<MODE, 1>(S, ns, ax, ay, az, part);
+        }
       } else if (nact > 0) {
         for (int s = 0; s < ns; ++s) {
           const V4 v = S[s];
@@ -227,6 +241,9 @@ constexpr int DT_THREADS = 512 / DT_NT;
 constexpr int DTD_NT = 2;
 constexpr int DTD_THREADS = 256;
 constexpr int DT_JT = 8;
+// the paired staging pads an odd source count by one: even tile counts keep the padded
+// count within the tile's shared memory (an odd count only occurs in a partial tile)
+static_assert(P2L_JT % 2 == 0 && DT_JT % 2 == 0, "tile source counts must be even");
 
 template <typename R, int MODE>
 __global__ void __launch_bounds__(DT_THREADS) direct_list_kernel(
@@ -288,15 +305,25 @@ __global__ void __launch_bounds__(DT_THREADS) direct_list_kernel(
         v.x *= 0.5f;
         v.y *= 0.5f;
         v.z *= 0.5f;
+        if constexpr (NCS_PAIR_X2 != 0) {
+          stage_source_x2(reinterpret_cast<float4*>(S), idx, v.x, v.y, v.z, v.w);
+          continue;
+        }
       }
       S[idx] = v;
+    }
+    if constexpr (sizeof(R) == 4 && NCS_PAIR_X2 != 0) {
+      if (threadIdx.x == 0) stage_pad_x2(reinterpret_cast<float4*>(S), ns);
     }
     __syncthreads();
     R part[DT_NT];
 #pragma unroll
     for (int t = 0; t < DT_NT; ++t) part[t] = 0;
     if constexpr (sizeof(R) == 4) {
-      pair_loop32<MODE, DT_NT>(S, ns, ax, ay, az, part);
+      if constexpr (NCS_PAIR_X2 != 0)
+        pair_loop32x2<MODE, DT_NT>(S, ns, ax, ay, az, part);
+      else
+        pair_loop32<MODE, DT_NT>(S, ns, ax, ay, az, part);
     } else {
       for (int s = 0; s < ns; ++s) {
         const V4 v = S[s];
