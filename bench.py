@@ -36,10 +36,14 @@ WORKLOAD = "interior narrow escape, N=100000 patches, eps=0.001, K=136, jittered
 FLOPS_PER_PAIR = 20
 
 
-P2L_BYTES_PER_PAIR = 156.0e6 / 1.5108e10
+# DRAM bytes per pair of the FP32 P2L kernel: dram__bytes_read.sum + dram__bytes_write.sum
+# of one launch (170.2 + 15.5 MB) over its 1.5108e10 pairs, ncu capture of the packed pair
+# loop at N = 2e4 of the same layout family; the reads scale with the work items.
+P2L_BYTES_PER_PAIR = 185.7e6 / 1.5108e10
 # MUFU operations per FP32 pair in the P2L kernel: rsqrt always, log2 on the MUFU unit for
-# 15 pairs in 16 (the 16th takes a polynomial log2 on the FMA pipe)
-MUFU_PER_PAIR = 2.0 - 1.0 / 16.0
+# 12 pairs in 16 (the other 4 take a polynomial log2 on the FMA pipe; the packed pair
+# loop's default share)
+MUFU_PER_PAIR = 2.0 - 4.0 / 16.0
 
 
 def _dist():
@@ -242,8 +246,8 @@ def run_ours(args):
     peaks, src = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     # ALU roofline of the pair kernel: per pair the FP32 path issues MUFU_PER_PAIR MUFU
-    # ops (rsqrt, and log2 for all but one pair in 16) and ~11 other instructions;
-    # 152 SMs x 16 MUFU/clk cap it at 16 / MUFU_PER_PAIR pairs/clk/SM.
+    # ops (rsqrt, and log2 for 12 pairs in 16); 152 SMs x 16 MUFU/clk cap it at
+    # 16 / MUFU_PER_PAIR pairs/clk/SM.
     pair_peak = 152 * (16.0 / MUFU_PER_PAIR) * sm_max * 1e6 if prec == ncs.FP32 else None
     p2l_pairs = tstats["p2l_pairs"]
     achieved_pairs = p2l_pairs / (p2l_avg / 1000.0)

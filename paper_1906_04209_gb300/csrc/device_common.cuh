@@ -254,7 +254,7 @@ __device__ __forceinline__ void stage_pad_x2(float4* S, int ns) {
 // NCS_PAIR_X2_POLY of every 16 two-pair chains (a target against a staged source pair)
 // take their logarithms with lg2_poly.
 #ifndef NCS_PAIR_X2_POLY
-#define NCS_PAIR_X2_POLY 6
+#define NCS_PAIR_X2_POLY 4
 #endif
 
 // part[t] = sum over the ns staged sources (paired layout, padded to even) of G(a_t, s)
