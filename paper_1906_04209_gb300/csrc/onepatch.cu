@@ -173,11 +173,16 @@ int colloc_assemble_device(const CollocProblem& p, std::vector<double>& A, std::
   const size_t bytes = (nin + nA) * sizeof(double) + (size_t)(nb + 1) * sizeof(int);
   cudaStream_t s = nullptr;
   char* buf = nullptr;
-  cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaMalloc(&buf, bytes);
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess || cudaMalloc(&buf, bytes) != cudaSuccess) {
+    // no room or no usable device: the host loop forms the matrices, as for the ID sketch
+    if (s) cudaStreamDestroy(s);
+    cudaGetLastError();
+    return 0;
+  }
+  cudaError_t e = cudaSuccess;
   double* d = reinterpret_cast<double*>(buf);
   CollocArgs a{};
-  if (e == cudaSuccess) {
+  {
     size_t off = 0;
     auto put = [&](const std::vector<double>& v) -> const double* {
       double* dst = d + off;

@@ -33,8 +33,8 @@ constexpr int kCollocMaxOrd = 32;
 constexpr int kCollocMaxModes = 64;
 
 // Fills A (nmodes x nr x nr, row-major per mode) on the current CUDA device. Returns 1 on
-// success, 0 if no device is usable or the sizes exceed the kernel's limits (A untouched),
-// -1 on a CUDA error (message in *err).
+// success, 0 if no device is usable, its buffers cannot be allocated or the sizes exceed
+// the kernel's limits (A untouched), -1 on a CUDA error after that (message in *err).
 int colloc_assemble_device(const CollocProblem& p, std::vector<double>& A, std::string* err);
 
 }  // namespace ncs
