@@ -80,3 +80,20 @@ def test_device_collocation_beyond_kernel_limits_uses_host():
     c = ncs.Context(0.05, EXTERIOR, 10, npan=4, nord=33, ntheta_fine=24, method=ncs.METHOD_DIRECT,
                     id_ladder_max=0.0, device_precompute=1)
     assert c.timings()[6] == 0.0
+
+
+@pytest.mark.parametrize("mode", [EXTERIOR, INTERIOR])
+def test_device_onepatch_matches_oracle(mode):
+    """The one-patch solution with its collocation matrices formed on the device against the
+    oracle's modal solver (brute quadrature of the full Green's function in theta, scipy
+    rules): the same bar as the host path's CPU test."""
+    from oracle import onepatch
+    eps, K, npan, nord, nth = 0.05, 21, 7, 12, 30
+    c = ncs.Context(eps, mode, K, npan=npan, nord=nord, ntheta_fine=nth, device_precompute=1,
+                    method=ncs.METHOD_DIRECT)
+    assert c.timings()[6] == 1.0
+    tr, beta = c.onepatch()
+    op = onepatch.solve_one_patch(eps, mode, K, npan, nord, nth)
+    assert np.abs(tr - op.rad.t).max() < 1e-15
+    assert np.abs(beta - op.beta).max() < 1e-11 * np.abs(op.beta).max()
+    assert np.abs(c.operator()["I"] - op.I).max() < 1e-11 * np.abs(op.I).max()

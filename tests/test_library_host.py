@@ -38,6 +38,18 @@ def test_onepatch_matches_oracle(libncs, mode):
     assert np.abs(o["znode_r"] - r).max() < 1e-15 and np.abs(o["znode_theta"] - th).max() < 1e-15
 
 
+def test_precompute_independent_of_thread_count(libncs):
+    """The host precompute splits its loops over threads by rows, columns and modes, never
+    inside a sum: one thread and all threads give the same bits."""
+    kw = dict(npan=6, nord=10, ntheta_fine=24, device_precompute=0, id_ladder_max=0.2)
+    a = ncs.Context(0.05, INTERIOR, 21, threads=1, **kw)
+    b = ncs.Context(0.05, INTERIOR, 21, threads=0, **kw)
+    assert np.array_equal(a.onepatch()[1], b.onepatch()[1])
+    oa, ob = a.operator(), b.operator()
+    assert np.array_equal(oa["T"], ob["T"]) and np.array_equal(oa["I"], ob["I"])
+    assert np.array_equal(a.reps()[1], b.reps()[1])
+
+
 @pytest.mark.parametrize("mode", [EXTERIOR, INTERIOR])
 def test_library_outgoing_operator(libncs, mode):
     """The library's own ID (sketched CPQR) reproduces the far field of the oracle's
