@@ -245,11 +245,13 @@ void build_structure(const std::vector<double>& centres, const TreeOptions& opt,
     if (maxocc <= 1) break;
   }
   const int nl = (int)S.lv.size();
-  // neighbours
+  // neighbours (each group's list written by one thread; the box index is only read)
   for (int l = 0; l < nl; ++l) {
     Level& L = S.lv[l];
     L.nbrs.resize(L.keys.size());
-    for (size_t g = 0; g < L.keys.size(); ++g) {
+    const int64_t ng = (int64_t)L.keys.size();
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t g = 0; g < ng; ++g) {
       const uint64_t k = L.keys[g];
       const int f = (int)(k >> 48), ix = (int)((k >> 24) & 0xffffff), iy = (int)(k & 0xffffff);
       for (int dx = -1; dx <= 1; ++dx)
@@ -268,7 +270,9 @@ void build_structure(const std::vector<double>& centres, const TreeOptions& opt,
   for (int l = 0; l < nl; ++l) {
     Level& L = S.lv[l];
     L.il.resize(L.keys.size());
-    for (size_t g = 0; g < L.keys.size(); ++g) {
+    const int64_t ng = (int64_t)L.keys.size();
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t g = 0; g < ng; ++g) {
       std::vector<int> cand;
       if (l == 0) {
         for (size_t h = 0; h < L.keys.size(); ++h) cand.push_back((int)h);
@@ -346,7 +350,9 @@ void tree_build(const std::vector<double>& centres, const Precomputed& pc, const
     const Level& L = S.lv[l];
     gcirc[l].resize(3 * L.keys.size());
     grad[l].resize(L.keys.size());
-    for (size_t g = 0; g < L.keys.size(); ++g)
+    const int64_t ng = (int64_t)L.keys.size();
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t g = 0; g < ng; ++g)
       grad[l][g] = bounding_circle(centres, L.members[g], &gcirc[l][3 * g]) + eps * (1.0 + 1e-9);
   }
   for (int l = nl - 1; l >= 1; --l) {
@@ -361,18 +367,32 @@ void tree_build(const std::vector<double>& centres, const Precomputed& pc, const
       grad[l - 1][pg] = std::max(grad[l - 1][pg], need * (1.0 + 1e-12));
     }
   }
+  // Per level, every group's plan (its interaction-list sources by distance, grid or
+  // direct) is formed in parallel; the grid groups are then appended in group order, so
+  // the lists do not depend on the thread count. A patch is a member of one group per
+  // level, so the direct lists of a level's groups touch disjoint patches.
+  struct GroupPlan {
+    bool grid = false;
+    GridShape gs;
+    std::vector<int> srcs;     // sources sorted by distance from the circle centre
+    std::vector<double> dist;  // their distances
+  };
   for (int l = 0; l < nl; ++l) {
     const Level& L = S.lv[l];
-    for (size_t g = 0; g < L.keys.size(); ++g) {
+    const int64_t ng = (int64_t)L.keys.size();
+    std::vector<GroupPlan> plan(ng);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t g = 0; g < ng; ++g) {
       if (L.il[g].empty()) continue;
       const std::vector<int>& mem = L.members[g];
       std::vector<int> srcs;
       for (int h : L.il[g])
         for (int j : L.members[h]) srcs.push_back(j);
-      double c[3] = {gcirc[l][3 * g], gcirc[l][3 * g + 1], gcirc[l][3 * g + 2]};
+      const double* c = &gcirc[l][3 * g];
       const double R = grad[l][g];
       // sources sorted by distance, so that P2L work items hold similar distances
       std::vector<std::pair<double, int>> sd;
+      sd.reserve(srcs.size());
       for (int j : srcs) sd.push_back({geodesic(c, &centres[3 * j]), j});
       std::sort(sd.begin(), sd.end());
       for (size_t q = 0; q < sd.size(); ++q) srcs[q] = sd[q].second;
@@ -396,29 +416,43 @@ void tree_build(const std::vector<double>& centres, const Precomputed& pc, const
         for (int i : mem) direct[i].insert(direct[i].end(), srcs.begin(), srcs.end());
         continue;
       }
+      GroupPlan& P = plan[g];
+      P.grid = true;
+      P.gs = gs;
+      P.dist.resize(sd.size());
+      for (size_t q = 0; q < sd.size(); ++q) P.dist[q] = sd[q].first;
+      P.srcs = std::move(srcs);
+    }
+    for (int64_t g = 0; g < ng; ++g) {
+      GroupPlan& P = plan[g];
+      if (!P.grid) continue;
+      const GridShape gs = P.gs;
+      const double R = grad[l][g];
       const int gi = (int)t.gR.size();
-      t.gcen.insert(t.gcen.end(), c, c + 3);
+      t.gcen.insert(t.gcen.end(), &gcirc[l][3 * g], &gcirc[l][3 * g] + 3);
       t.gR.push_back(R);
       t.glevel.push_back(l);
       t.gshape.push_back(shape_index(gs));
       t.goff.push_back(t.total_grid_points);
       t.total_grid_points += gs.q();
-      for (size_t s = 0; s < srcs.size(); s += CH) {
-        const size_t e = std::min(srcs.size(), s + CH);
+      for (size_t s = 0; s < P.srcs.size(); s += CH) {
+        const size_t e = std::min(P.srcs.size(), s + CH);
         // grid points lie within R of the centre: every source of the item is at least
         // (its distance - R) away from them
-        const int k = select_rep(pc, sd[s].first - R);
+        const int k = select_rep(pc, P.dist[s] - R);
         t.witem_group.push_back(gi);
         t.witem_rep.push_back(k);
         t.witem_lo.push_back((int64_t)t.isrc.size() + (int64_t)s);
         t.witem_hi.push_back((int64_t)t.isrc.size() + (int64_t)e);
         t.p2l_pairs += (int64_t)(e - s) * rep_p(pc, k) * gs.q();
       }
-      t.isrc.insert(t.isrc.end(), srcs.begin(), srcs.end());
-      for (int i : mem) {
+      t.isrc.insert(t.isrc.end(), P.srcs.begin(), P.srcs.end());
+      for (int i : L.members[g]) {
         pgroups[i].push_back(gi);
         t.l2p_evals += (int64_t)pc.Kstar * gs.q();
       }
+      std::vector<int>().swap(P.srcs);
+      std::vector<double>().swap(P.dist);
     }
   }
   // leaf neighbours (Step 3), evaluated at the Zernike nodes
@@ -478,25 +512,30 @@ void tree_build(const std::vector<double>& centres, const Precomputed& pc, const
   }
   t.pd_off.assign(N + 1, 0);
   t.pg_off.assign(N + 1, 0);
+#pragma omp parallel for schedule(dynamic, 256)
+  for (int i = 0; i < N; ++i) std::sort(direct[i].begin(), direct[i].end());
   for (int i = 0; i < N; ++i) {
-    std::sort(direct[i].begin(), direct[i].end());
     t.pd_off[i + 1] = t.pd_off[i] + (int64_t)direct[i].size();
     t.pg_off[i + 1] = t.pg_off[i] + (int64_t)pgroups[i].size();
   }
-  t.pd.reserve(t.pd_off[N]);
-  t.pdk.reserve(t.pd_off[N]);
+  t.pd.resize(t.pd_off[N]);
+  t.pdk.resize(t.pd_off[N]);
   t.pg.reserve(t.pg_off[N]);
-  t.direct_pairs = 0;
+  int64_t dpairs = 0;
+#pragma omp parallel for schedule(dynamic, 256) reduction(+ : dpairs)
   for (int i = 0; i < N; ++i) {
+    int64_t o = t.pd_off[i];
     for (int j : direct[i]) {
       // the Zernike nodes of patch i lie within eps of its centre
       const int k = select_rep(pc, geodesic(&centres[3 * i], &centres[3 * j]) - eps);
-      t.pd.push_back(j);
-      t.pdk.push_back(k);
-      t.direct_pairs += (int64_t)rep_p(pc, k) * pc.Kstar;
+      t.pd[o] = j;
+      t.pdk[o] = k;
+      ++o;
+      dpairs += (int64_t)rep_p(pc, k) * pc.Kstar;
     }
-    t.pg.insert(t.pg.end(), pgroups[i].begin(), pgroups[i].end());
   }
+  t.direct_pairs = dpairs;
+  for (int i = 0; i < N; ++i) t.pg.insert(t.pg.end(), pgroups[i].begin(), pgroups[i].end());
   t.pairs_per_matvec = t.p2l_pairs + t.direct_pairs;
 }
 

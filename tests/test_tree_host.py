@@ -62,3 +62,18 @@ def test_tree_statistics(libncs):
     # every direct pair uses a representation no larger than the finest one
     assert 0 < s["direct_pairs"] <= s["direct_patch_pairs"] * info["p"] * info["Kstar"]
     assert s["p2l_pairs"] + s["direct_pairs"] < info["direct_pairs"]
+
+
+def test_tree_build_independent_of_thread_count(libncs):
+    """The tree's group plans are formed in parallel and merged in group order: one host
+    thread and all of them build the same lists (same counts of grid groups, work items,
+    pairs and transfers)."""
+    c, eps, mode, _ = L.workload(2)
+    stats = []
+    for threads in (1, 0):
+        ctx = ncs.Context(eps, mode, 3, npan=4, nord=6, ntheta_fine=8, threads=threads,
+                          method=ncs.METHOD_TREE)
+        ctx.set_patches(c)
+        stats.append(ctx.tree_stats())
+    assert stats[0] == stats[1]
+    assert stats[0]["grid_groups"] > 0 and stats[0]["p2l_items"] > 0
