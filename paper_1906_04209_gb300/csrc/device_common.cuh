@@ -106,7 +106,8 @@ __device__ __forceinline__ float pair32_poly(float d2h, float rho, float acc) {
   return fmaf(fmaf(l, -kLn2f, rh), rho, acc);
 }
 
-// NCS_PAIR_POLYLOG of every 16 FP32 pairs (0, 1 or 2) take their logarithm with
+// Scalar pair loop (the dense direct kernel, and the tree kernels of NCS_PAIR_X2 = 0
+// builds): NCS_PAIR_POLYLOG of every 16 FP32 pairs (0, 1 or 2) take their logarithm with
 // lg2_poly on the FMA pipe instead of the MUFU unit, which otherwise bounds the pair
 // rate (measured at N = 1e5: one in 16 shortens P2L by ~6 %, two in 16 by ~3 %).
 #ifndef NCS_PAIR_POLYLOG
