@@ -278,6 +278,22 @@ int ncs_solve(ncs_ctx* ctx, double tol, int precision, double* fhat, double* sca
 int ncs_eval(ncs_ctx* ctx, int64_t M, const double* targets, const double* fhat, double* out);
 
 /*
+ * Relative L2 residual of the multiple-scattering system on patch i (Section 9, eq.
+ * l2res, the error measure of the paper's large runs): the root mean square over Gamma_i
+ * of r = S sigma_i + sum_{j != i} S_ij sigma_j - 1. S sigma_i = sum_k fhat_ik q_k (each
+ * basis density solves the one-patch equation S b_k = q_k, Section 8); the other
+ * patches' potential comes from their finest skeleton representation (FP64 on the
+ * device; every point of Gamma_i is at least 2 eps from the other centres). The printed
+ * normalisation (the norm over |Gamma_i|) is read as the relative residual
+ * ||r|| / ||1|| = ||r|| / sqrt(|Gamma_i|). Quadrature: nt Gauss-Legendre nodes in the
+ * arclength t on [0, eps] (measure sin t dt) times nth equispaced angles; 0 selects
+ * M + 8 and 2M + 10. fhat: N*K host doubles (as from ncs_solve); rms: one double.
+ * Errors: NCS_E_INPUT (index out of range, grid above 4096 x 8192, NULL), NCS_E_STATE,
+ * NCS_E_OOM, NCS_E_CUDA.
+ */
+int ncs_patch_residual(ncs_ctx* ctx, int64_t i, const double* fhat, int nt, int nth, double* rms);
+
+/*
  * The projections of one GMRES Arnoldi step (Section 7, Step 3; classical Gram-Schmidt
  * on the device): out[j] = V_j . w for j < k, V_j = V + j*ld, all device FP64 arrays
  * (n entries each; out holds k), reduced deterministically in two stages (fixed

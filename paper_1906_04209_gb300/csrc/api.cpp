@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "internal.hpp"
+#include "numerics.hpp"
 
 using ncs::DeviceData;
 
@@ -997,6 +998,93 @@ int ncs_eval(ncs_ctx* c, int64_t M, const double* targets, const double* fhat, d
     return NCS_OK;
   } catch (const Fail& f) {
     return finish(c, f);
+  } catch (const std::exception& e) {
+    return finish(c, Fail{NCS_E_INPUT, e.what()});
+  }
+}
+
+int ncs_patch_residual(ncs_ctx* c, int64_t i, const double* fhat, int nt, int nth, double* rms) {
+  try {
+    if (!c || !fhat || !rms) throw Fail{NCS_E_INPUT, "bad residual arguments"};
+    check_ready(c);
+    if (i < 0 || i >= c->d.N) throw Fail{NCS_E_INPUT, "patch index out of range"};
+    const ncs::Precomputed& pc = c->pc;
+    if (nt <= 0) nt = pc.M + 8;
+    if (nth <= 0) nth = 2 * pc.M + 10;
+    if (nt > 4096 || nth > 8192) throw Fail{NCS_E_INPUT, "residual grid too large"};
+    const double eps = pc.eps;
+    const int K = pc.K;
+    // the patch's frame (the one of its Zernike nodes and skeletons): e1 = z x c / |z x c|
+    // (x at the poles), e2 = c x e1
+    const double* cc = &c->centres[3 * i];
+    double e1[3] = {-cc[1], cc[0], 0.0};
+    const double na2 = e1[0] * e1[0] + e1[1] * e1[1];
+    if (na2 >= 1e-24) {
+      const double inv = 1.0 / std::sqrt(na2);
+      e1[0] *= inv;
+      e1[1] *= inv;
+    } else {
+      e1[0] = 1.0;
+      e1[1] = 0.0;
+    }
+    const double e2[3] = {cc[1] * e1[2] - cc[2] * e1[1], cc[2] * e1[0] - cc[0] * e1[2],
+                          cc[0] * e1[1] - cc[1] * e1[0]};
+    std::vector<double> gx, gw;
+    ncs::gauss_legendre(nt, gx, gw);
+    const int64_t M = (int64_t)nt * nth;
+    std::vector<double> tg(3 * (size_t)M), dA(M), selfv(M);
+    const double* fi = fhat + (size_t)i * K;
+    for (int a = 0; a < nt; ++a) {
+      const double t = 0.5 * eps * (gx[a] + 1.0), wt = 0.5 * eps * gw[a];
+      const double st = std::sin(t), ct = std::cos(t);
+      std::vector<double> rad(K);
+      for (int k = 0; k < K; ++k) {
+        const double nn = (pc.bm[k] == 0 ? 2.0 : 1.0) * ncs::kPi / (2.0 * pc.bn[k] + 2.0);  // eq. zorthog
+        rad[k] = fi[k] * ncs::zernike_radial(pc.bn[k], pc.bm[k], t / eps) / std::sqrt(nn);
+      }
+      for (int b = 0; b < nth; ++b) {
+        const double th = 2.0 * ncs::kPi * b / nth, ch = std::cos(th), sh = std::sin(th);
+        const int64_t q = (int64_t)a * nth + b;
+        for (int k = 0; k < 3; ++k) tg[3 * q + k] = ct * cc[k] + st * (ch * e1[k] + sh * e2[k]);
+        dA[q] = wt * st * 2.0 * ncs::kPi / nth;
+        double v = 0.0;
+        for (int k = 0; k < K; ++k) v += rad[k] * (pc.bc[k] ? std::sin(pc.bm[k] * th) : std::cos(pc.bm[k] * th));
+        selfv[q] = v;
+      }
+    }
+    const int64_t n = c->d.N * c->d.K;
+    ensure_krylov(c, 1);
+    cudaStream_t s = c->stream;
+    double *dt = nullptr, *dout = nullptr;
+    std::vector<double> u(M);
+    try {
+      CU(cudaMalloc(&dt, 3 * (size_t)M * sizeof(double)));
+      CU(cudaMalloc(&dout, (size_t)M * sizeof(double)));
+      CU(cudaMemcpyAsync(c->work, fhat, n * sizeof(double), cudaMemcpyHostToDevice, s));
+      CU(cudaMemcpyAsync(dt, tg.data(), 3 * (size_t)M * sizeof(double), cudaMemcpyHostToDevice, s));
+      CU(ncs::launch_outgoing(c->d, c->work, NCS_FP64, s));
+      CU(ncs::launch_eval(c->d, pc.mode, M, dt, dout, s, i));  // patch i left out
+      CU(cudaMemcpyAsync(u.data(), dout, (size_t)M * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CU(cudaStreamSynchronize(s));
+    } catch (...) {
+      cudaFree(dt);
+      cudaFree(dout);
+      throw;
+    }
+    cudaFree(dt);
+    cudaFree(dout);
+    double num = 0.0, den = 0.0;
+    for (int64_t q = 0; q < M; ++q) {
+      const double r = selfv[q] + u[q] - 1.0;
+      num += dA[q] * r * r;
+      den += dA[q];
+    }
+    *rms = std::sqrt(num / den);
+    return NCS_OK;
+  } catch (const Fail& f) {
+    return finish(c, f);
+  } catch (const std::bad_alloc&) {
+    return finish(c, Fail{NCS_E_OOM, "out of host memory"});
   } catch (const std::exception& e) {
     return finish(c, Fail{NCS_E_INPUT, e.what()});
   }

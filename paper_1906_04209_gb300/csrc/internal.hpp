@@ -54,8 +54,10 @@ cudaError_t launch_skeleton_offsets(const DeviceData& d, cudaStream_t s);
 cudaError_t launch_outgoing(const DeviceData& d, const double* x, int prec, cudaStream_t s);
 cudaError_t launch_direct_field(const DeviceData& d, int mode, int prec, double eps, cudaStream_t s);
 cudaError_t launch_apply_P(const DeviceData& d, const double* x, double* y, int prec, cudaStream_t s);
+// Single-layer potential of every patch's finest skeleton representation at M targets
+// (off-surface Green's functions); patch `skip` (if >= 0) is left out of the sum.
 cudaError_t launch_eval(const DeviceData& d, int mode, int64_t M, const double* targets,
-                        double* out, cudaStream_t s);
+                        double* out, cudaStream_t s, int64_t skip = -1);
 
 // ---- tensor-core GEMMs (tc_gemm.cu)
 // Operands of the tensor-core GEMMs as TF32 hi/lo blocks in the shared-memory layout:

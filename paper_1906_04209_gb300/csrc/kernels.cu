@@ -442,7 +442,8 @@ cudaError_t launch_apply_P(const DeviceData& d, const double* x, double* y, int 
 template <int MODE>
 __global__ void __launch_bounds__(256) eval_kernel(int64_t N, int p, int pt, const double* __restrict__ centres,
                                                    const double* __restrict__ soff, const double* __restrict__ rho,
-                                                   const double* __restrict__ targets, double* __restrict__ out) {
+                                                   const double* __restrict__ targets, int64_t skip,
+                                                   double* __restrict__ out) {
   __shared__ double red[256];
   const int64_t t = blockIdx.x;
   const double x0 = targets[3 * t], x1 = targets[3 * t + 1], x2 = targets[3 * t + 2];
@@ -450,6 +451,7 @@ __global__ void __launch_bounds__(256) eval_kernel(int64_t N, int p, int pt, con
   double acc = 0.0;
   for (int64_t h = threadIdx.x; h < N * p; h += blockDim.x) {
     const int64_t j = h / p;
+    if (j == skip) continue;                 // a patch left out (its own points as targets)
     const int64_t g = j * pt + (h - j * p);  // representation 0 (the finest) of patch j
     const double s0 = centres[3 * j] + soff[3 * g], s1 = centres[3 * j + 1] + soff[3 * g + 1],
                  s2 = centres[3 * j + 2] + soff[3 * g + 2];
@@ -473,12 +475,14 @@ __global__ void __launch_bounds__(256) eval_kernel(int64_t N, int p, int pt, con
 }
 
 cudaError_t launch_eval(const DeviceData& d, int mode, int64_t M, const double* targets, double* out,
-                        cudaStream_t s) {
+                        cudaStream_t s, int64_t skip) {
   if (M == 0) return cudaSuccess;
   if (mode == 0)
-    count_launch(), eval_kernel<0><<<(unsigned)M, 256, 0, s>>>(d.N, d.p0, d.p, d.centres, d.soff64, d.rho64, targets, out);
+    count_launch(), eval_kernel<0><<<(unsigned)M, 256, 0, s>>>(d.N, d.p0, d.p, d.centres, d.soff64, d.rho64, targets,
+                                                               skip, out);
   else
-    count_launch(), eval_kernel<1><<<(unsigned)M, 256, 0, s>>>(d.N, d.p0, d.p, d.centres, d.soff64, d.rho64, targets, out);
+    count_launch(), eval_kernel<1><<<(unsigned)M, 256, 0, s>>>(d.N, d.p0, d.p, d.centres, d.soff64, d.rho64, targets,
+                                                               skip, out);
   return cudaGetLastError();
 }
 

@@ -31,7 +31,7 @@ EXPORTS = ["ncs_default_params", "ncs_create", "ncs_create_from_operator", "ncs_
            "ncs_matvec_dev", "ncs_field_dev", "ncs_solve", "ncs_eval", "ncs_last_error", "ncs_destroy",
            "ncs_tree_pairs", "ncs_tree_stats", "ncs_profile_matvec", "ncs_create_from_operators", "ncs_get_reps",
            "ncs_tc_gemm_f32", "ncs_batch_solve", "ncs_block_dots", "ncs_block_dots_noalloc",
-           "ncs_launch_count", "ncs_get_rep", "ncs_set_precision"]
+           "ncs_launch_count", "ncs_get_rep", "ncs_set_precision", "ncs_patch_residual"]
 
 
 class ncs_params(ctypes.Structure):
@@ -335,3 +335,10 @@ class Context:
         out = np.zeros(t.shape[0])
         self._check(load().ncs_eval(self.h, t.shape[0], _ptr(t), _ptr(f), _ptr(out)))
         return out
+
+    def patch_residual(self, i, fhat, nt=0, nth=0):
+        """Relative L2 residual of the system on patch i (eq. l2res)."""
+        f = _f64(fhat).ravel()
+        out = ctypes.c_double()
+        self._check(load().ncs_patch_residual(self.h, ctypes.c_int64(i), _ptr(f), nt, nth, ctypes.byref(out)))
+        return out.value
