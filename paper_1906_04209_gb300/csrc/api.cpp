@@ -411,7 +411,8 @@ void validate_centres(int64_t N, const double* cen, double eps) {
     return ((uint64_t)a << 42) ^ ((uint64_t)b << 21) ^ (uint64_t)cc;
   };
   for (int64_t i = 0; i < N; ++i) cells[key(cen[3 * i], cen[3 * i + 1], cen[3 * i + 2])].push_back(i);
-  for (int64_t i = 0; i < N; ++i) {
+  // the first patch i (in index order) with a later patch j too close, and that j
+  auto too_close = [&](int64_t i, int64_t* jout) {
     const double* c = cen + 3 * i;
     for (int dx = -1; dx <= 1; ++dx)
       for (int dy = -1; dy <= 1; ++dy)
@@ -423,11 +424,22 @@ void validate_centres(int64_t N, const double* cen, double eps) {
             const double* e = cen + 3 * j;
             const double d2 = (c[0] - e[0]) * (c[0] - e[0]) + (c[1] - e[1]) * (c[1] - e[1]) +
                               (c[2] - e[2]) * (c[2] - e[2]);
-            if (d2 < chord_min * chord_min)
-              throw Fail{NCS_E_INPUT, "patches " + std::to_string(i) + " and " + std::to_string(j) +
-                                          " are closer than 3 eps"};
+            if (d2 < chord_min * chord_min) {
+              if (jout) *jout = j;
+              return true;
+            }
           }
         }
+    return false;
+  };
+  int64_t bad = N;
+#pragma omp parallel for schedule(dynamic, 1024) reduction(min : bad)
+  for (int64_t i = 0; i < N; ++i)
+    if (i < bad && too_close(i, nullptr)) bad = i;
+  if (bad < N) {
+    int64_t j = -1;
+    too_close(bad, &j);
+    throw Fail{NCS_E_INPUT, "patches " + std::to_string(bad) + " and " + std::to_string(j) + " are closer than 3 eps"};
   }
 }
 

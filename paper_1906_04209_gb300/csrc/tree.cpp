@@ -88,9 +88,17 @@ bool neighbour_box(int face, int ix, int iy, int n, int dx, int dy, BoxId* out) 
 
 // Coarsest outgoing representation whose far field starts at or before `dist`.
 int select_rep(const Precomputed& pc, double dist) {
-  int k = 0;
-  while (k + 1 < (int)pc.reps.size() && pc.reps[k + 1].rho_min <= dist) ++k;
-  return k;
+  // the last representation whose far region starts at or before dist (radii increase
+  // along the ladder), else the first
+  int lo = 0, hi = (int)pc.reps.size() - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (pc.reps[mid].rho_min <= dist)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
 }
 
 int rep_p(const Precomputed& pc, int k) { return pc.reps.empty() ? pc.p : pc.reps[k].p; }
@@ -403,11 +411,10 @@ void tree_build(const std::vector<double>& centres, const Precomputed& pc, const
       GridShape gs;
       if ((int)mem.size() >= opt.grid_min_members && D > 1.15 * R) {
         gs = grid_size(R, D, opt.grid_tol);
-        double psum_grid = 0.0, psum_direct = 0.0;
-        for (size_t q = 0; q < sd.size(); ++q) {
-          psum_grid += rep_p(pc, select_rep(pc, sd[(q / CH) * CH].first - R));
-          psum_direct += rep_p(pc, select_rep(pc, sd[q].first - R));
-        }
+        double psum_grid = 0.0, psum_direct = 0.0;  // sums of integers: exact in any order
+        for (size_t s = 0; s < sd.size(); s += CH)
+          psum_grid += (double)(std::min(sd.size(), s + CH) - s) * rep_p(pc, select_rep(pc, sd[s].first - R));
+        for (size_t q = 0; q < sd.size(); ++q) psum_direct += rep_p(pc, select_rep(pc, sd[q].first - R));
         const double cost_grid = gs.q() * psum_grid + 0.1 * (double)mem.size() * pc.Kstar * gs.q();
         const double cost_direct = (double)mem.size() * pc.Kstar * psum_direct;
         use_grid = cost_grid < cost_direct;
