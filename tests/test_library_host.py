@@ -120,6 +120,29 @@ def test_set_patches_validation(libncs):
     assert e.value.code == ncs.NCS_E_INPUT
 
 
+def test_separation_check_names_the_first_pair(libncs):
+    # the check runs over all patches in parallel and reports the first offending patch in
+    # index order with its partner, as a serial scan would
+    from paper_1906_04209_gb300 import layouts as L
+    eps = 0.005
+    c = L.uniform(5000, eps, L.rng(77))
+    a, b = 1234, 3000
+    # move patch b to 2 eps (geodesic) from patch a, along a tangent direction of a
+    t = np.cross(c[a], [0.0, 0.0, 1.0])
+    t /= np.linalg.norm(t)
+    c[b] = np.cos(2 * eps) * c[a] + np.sin(2 * eps) * t
+    # keep the layout otherwise valid: drop patches that the move brought too close to b
+    d = np.arccos(np.clip(c @ c[b], -1, 1))
+    keep = [i for i in range(len(c)) if i in (a, b) or d[i] >= 3 * eps]
+    c = c[keep]
+    ia, ib = keep.index(a), keep.index(b)
+    ctx = ncs.Context(eps, 1, 3, npan=4, nord=6, ntheta_fine=8)
+    with pytest.raises(ncs.NcsError) as e:
+        ctx.set_patches(c)
+    assert e.value.code == ncs.NCS_E_INPUT
+    assert f"patches {min(ia, ib)} and {max(ia, ib)} are closer than 3 eps" in str(e.value)
+
+
 def test_precompute_without_device_uses_host_sketch(libncs):
     # without a CUDA device the ID sketch and the collocation matrices are formed on the host
     # whatever the parameter says
