@@ -1046,10 +1046,10 @@ int ncs_patch_residual(ncs_ctx* c, int64_t i, const double* fhat, int nt, int nt
     const int64_t M = (int64_t)nt * nth;
     std::vector<double> tg(3 * (size_t)M), dA(M), selfv(M);
     const double* fi = fhat + (size_t)i * K;
+    std::vector<double> rad(K);
     for (int a = 0; a < nt; ++a) {
       const double t = 0.5 * eps * (gx[a] + 1.0), wt = 0.5 * eps * gw[a];
       const double st = std::sin(t), ct = std::cos(t);
-      std::vector<double> rad(K);
       for (int k = 0; k < K; ++k) {
         const double nn = (pc.bm[k] == 0 ? 2.0 : 1.0) * ncs::kPi / (2.0 * pc.bn[k] + 2.0);  // eq. zorthog
         rad[k] = fi[k] * ncs::zernike_radial(pc.bn[k], pc.bm[k], t / eps) / std::sqrt(nn);
