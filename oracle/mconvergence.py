@@ -8,7 +8,6 @@ Test infrastructure only (see the package docstring). Run: python -m oracle.mcon
 """
 import time
 
-
 from . import operator as O
 from . import residual as R
 from . import solve as S
