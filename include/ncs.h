@@ -109,14 +109,18 @@ void ncs_default_params(ncs_params* p);
 /*
  * Creates a context for patch radius eps (0 < eps < 1), problem mode
  * (NCS_EXTERIOR / NCS_INTERIOR) and K Zernike functions per patch (1 <= K <= 2000),
- * and runs the one-patch precompute on the host (Section 7, Step 1): modal solves
- * giving B (Sections 5 and 8), I = w^T B (eq. getI), the interpolative decomposition
- * and T = Pi W B (Section 7.1, eq. Tmap), and the Zernike transform P (Section 4).
- * params may be NULL (defaults). This call and ncs_set_patches are host-only; the
- * CUDA device current at the first call that needs the GPU (a product, solve or
- * evaluation) is bound to the context for its lifetime and receives the uploads.
- * On success *out owns host and device memory that ncs_destroy releases.
- * Errors: NCS_E_INPUT, NCS_E_NUMERIC (precompute failure), NCS_E_OOM; *out is NULL.
+ * and runs the one-patch precompute (Section 7, Step 1): modal solves giving B
+ * (Sections 5 and 8), I = w^T B (eq. getI), the interpolative decompositions and
+ * T = Pi W B (Section 7.1, eq. Tmap), and the Zernike transform P (Section 4). With
+ * params->device_precompute (the default) its collocation matrices and interpolative
+ * decompositions run on the CUDA device current at this call, synchronously, with
+ * temporary device buffers freed before it returns (on the host if there is no device
+ * or no room). params may be NULL (defaults). The CUDA device current at the first
+ * call that needs the GPU for the context (a product, solve or evaluation) is bound to
+ * the context for its lifetime and receives the uploads. On success *out owns host and
+ * device memory that ncs_destroy releases.
+ * Errors: NCS_E_INPUT, NCS_E_NUMERIC (precompute failure, including a CUDA error in its
+ * device kernels), NCS_E_OOM; *out is NULL.
  */
 int ncs_create(double eps, int mode, int K, const ncs_params* params, ncs_ctx** out);
 
