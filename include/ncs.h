@@ -130,6 +130,8 @@ int ncs_create(double eps, int mode, int K, const ncs_params* params, ncs_ctx** 
  * skel_t, skel_theta (p each, t in [0, eps]) and I (K). P and the Zernike
  * sampling nodes are still formed by the library (Section 4). The arrays are
  * copied. Used to reuse a stored precompute.
+ * Errors: NCS_E_INPUT (sizes, NULL arrays, skeleton t outside [0, eps], non-finite T),
+ * NCS_E_OOM; *out is NULL.
  */
 int ncs_create_from_operator(double eps, int mode, int K, int p, const double* T,
                              const double* skel_t, const double* skel_theta, const double* I,
@@ -141,13 +143,16 @@ int ncs_create_from_operator(double eps, int mode, int K, int p, const double* T
  * skel_t, skel_theta concatenated in that order (sum(p) rows / entries). A source is
  * represented by the coarsest representation whose far field contains every target
  * it is summed onto (per-level recompression, Section 7 "Optimizations").
+ * Errors: as ncs_create_from_operator, and NCS_E_INPUT for radii that do not start at
+ * 2 eps or more and increase.
  */
 int ncs_create_from_operators(double eps, int mode, int K, int nrep, const double* rho_min, const int* p,
                               const double* T, const double* skel_t, const double* skel_theta,
                               const double* I, const ncs_params* params, ncs_ctx** out);
 
 /* Number of outgoing representations in *nrep; with rho_min and p non-NULL (and
- * *nrep at least that number on entry) also their far-field radii and ranks. */
+ * *nrep at least that number on entry) also their far-field radii and ranks, into caller
+ * arrays. Errors: NCS_E_INPUT (NULL ctx or nrep, *nrep too small). */
 int ncs_get_reps(const ncs_ctx* ctx, int* nrep, double* rho_min, int* p);
 
 /*
@@ -162,7 +167,8 @@ int ncs_get_rep(const ncs_ctx* ctx, int r, double* T, double* skel_t, double* sk
  * Writes context sizes into out[0..n): K, Kstar, p, M, nf (fine-grid points),
  * N (patches set, 0 if none), nrad (radial nodes), tree levels (0 if no tree),
  * grid points over all tree groups, pair evaluations per tree matvec (FP counts
- * of far-field kernel evaluations), direct pairs per matvec.
+ * of far-field kernel evaluations), direct pairs per matvec. out: n caller int64s.
+ * Errors: NCS_E_INPUT (NULL).
  */
 int ncs_info(const ncs_ctx* ctx, int64_t* out, int n);
 
@@ -177,7 +183,8 @@ int ncs_timings(const ncs_ctx* ctx, double* out, int n);
  * Copies the finest outgoing representation (far field beyond 2 eps) and the
  * rest of the precompute out (any pointer may be NULL to skip it): T (p x K),
  * skeleton (t, theta) (p each), I (K), P (K x Kstar), Zernike nodes on the unit
- * disk (r, theta) (Kstar each).
+ * disk (r, theta) (Kstar each), into caller arrays of those sizes.
+ * Errors: NCS_E_INPUT (NULL ctx).
  */
 int ncs_get_operator(const ncs_ctx* ctx, double* T, double* skel_t, double* skel_theta,
                      double* I, double* P, double* znode_r, double* znode_theta);
@@ -204,6 +211,7 @@ int ncs_set_patches(ncs_ctx* ctx, int64_t N, const double* centres);
  * interaction list, 2 = leaf-level neighbour; Step 3 note: each ordered pair of
  * distinct patches must appear exactly once). Call with target == NULL to get the
  * count in *count; then with buffers of at least *count ints each.
+ * Errors: NCS_E_INPUT (NULL, buffers smaller than the count), NCS_E_STATE (no patches).
  */
 int ncs_tree_pairs(ncs_ctx* ctx, int64_t* count, int* target, int* source, int* level, int* kind);
 
@@ -212,11 +220,12 @@ int ncs_tree_pairs(ncs_ctx* ctx, int64_t* count, int* target, int* source, int* 
  * P2L kernel evaluations, direct kernel evaluations, L2P node-grid products,
  * direct (target, source) patch pairs, distinct grid shapes, grid-to-grid links of
  * the downward pass, their point-grid products. Builds the host tree if needed
- * (host-only).
+ * (host-only). Errors: NCS_E_INPUT (NULL), NCS_E_STATE (no patches).
  */
 int ncs_tree_stats(ncs_ctx* ctx, int64_t* out, int n);
 
-/* Selects NCS_METHOD_AUTO / DIRECT / TREE for later products and solves. */
+/* Selects NCS_METHOD_AUTO / DIRECT / TREE for later products and solves (a tree is
+ * built on the host if needed). Errors: NCS_E_INPUT (NULL ctx, bad method). */
 int ncs_set_method(ncs_ctx* ctx, int method);
 
 /*
@@ -231,11 +240,15 @@ int ncs_set_precision(ncs_ctx* ctx, int precision);
  * y = A x for the system of eq. (opinteqnsdisc): y_i = x_i + P sum_{j != i} S_ij B x_j,
  * evaluated by the compressed representation (Section 7, Step 3). x, y: host,
  * N*K doubles. precision: NCS_FP64, NCS_DF64 or NCS_FP32 (FP32 kernels, FP64 in/out).
+ * x and y belong to the caller and are used only during the call (synchronous).
+ * Errors: NCS_E_INPUT (NULL, bad precision), NCS_E_STATE (no patches), NCS_E_OOM,
+ * NCS_E_CUDA, NCS_E_TIMEOUT (a bounded device wait of the tensor-core GEMM gave up).
  */
 int ncs_matvec(ncs_ctx* ctx, const double* x, double* y, int precision);
 
-/* As ncs_matvec with device pointers x, y (N*K doubles) on the given stream
- * (cudaStream_t, NULL = legacy default stream). Asynchronous. */
+/* As ncs_matvec with device pointers x, y (N*K doubles, caller-owned, not overlapping)
+ * on the given stream (cudaStream_t, NULL = legacy default stream). Asynchronous: errors
+ * of the enqueued work surface at a later synchronising call. Errors: as ncs_matvec. */
 int ncs_matvec_dev(ncs_ctx* ctx, const double* x, double* y, int precision, void* stream);
 
 /*
@@ -243,14 +256,16 @@ int ncs_matvec_dev(ncs_ctx* ctx, const double* x, double* y, int precision, void
  * of Step 3 written to ms[0..n): outgoing map (3.1), P2L onto incoming grids (3.2),
  * grid coefficients (first half of 3.4), direct sums at the Zernike nodes (3.3 and
  * small groups; the whole sum for the direct method), L2P interpolation (second half
- * of 3.4), apply P (3.5), total. Stages that do not run report 0.
+ * of 3.4), apply P (3.5), total. Stages that do not run report 0. ms: n caller doubles.
+ * Errors: as ncs_matvec.
  */
 int ncs_profile_matvec(ncs_ctx* ctx, const double* x, double* y, int precision, void* stream, double* ms, int n);
 
 /*
  * The multiple-scattering field before the transform P (Section 7, end of Step 4):
  * z_i(k) = sum_{j != i} [S_ij B x_j](k) at the Zernike sampling nodes, z: device,
- * N*Kstar doubles, patch-major. Asynchronous on `stream`.
+ * N*Kstar doubles, patch-major, caller-owned. Asynchronous on `stream`.
+ * Errors: as ncs_matvec_dev.
  */
 int ncs_field_dev(ncs_ctx* ctx, const double* x, double* z, int precision, void* stream);
 
