@@ -72,7 +72,7 @@ typedef struct ncs_params {
   int nord;            /* nodes per panel, default 20 */
   int ntheta_fine;     /* fine-grid azimuths; 0 = M + 40 rounded up to even */
   double id_tol;       /* interpolative-decomposition tolerance (Section 7.1), default 1e-11 */
-  int threads;         /* host threads for the precompute; 0 = all */
+  int threads;         /* host threads for the precompute and the tree set-up; 0 = all */
   double grid_tol;     /* incoming-grid tolerance (Section 7.3), default 1e-8 */
   int method;          /* NCS_METHOD_*, default AUTO */
   int tree_min_patches;/* AUTO switches to the tree at this N, default 2000 */
@@ -91,8 +91,8 @@ typedef struct ncs_params {
   double id_ladder_max;/* largest far-field radius (radians) for which an extra, smaller ID
                           representation is built (far fields beyond 2, 2.52, 3.17, 4, ... eps;
                           Section 7.1 recompression), default 1.0; 0: only the 2 eps one.
-                          Fewer representations shorten the host precompute (one CPQR of
-                          the sketch per representation) and lengthen the products */
+                          Fewer representations shorten the precompute (one CPQR of the
+                          sketch per representation) and lengthen the products */
   int device_precompute;/* 1 (default): the precompute forms the one-patch modal
                           collocation matrices (Section 8.2; the modal kernels at every
                           quadrature node, ~1e5 nodes x ~500 theta nodes) and runs its
