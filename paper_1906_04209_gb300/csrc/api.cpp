@@ -19,6 +19,9 @@
 
 #include "internal.hpp"
 #include "numerics.hpp"
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 using ncs::DeviceData;
 
@@ -243,6 +246,10 @@ bool use_tree(const ncs_ctx* c) {
 // host part of the tree (Step 2 of Section 7)
 void ensure_tree_host(ncs_ctx* c) {
   if (c->tree_built) return;
+#ifdef _OPENMP
+  // the thread count is an ICV of the calling host thread: the context's, on every build
+  omp_set_num_threads(c->prm.threads > 0 ? c->prm.threads : omp_get_num_procs());
+#endif
   ncs::TreeOptions to;
   to.grid_tol = c->prm.grid_tol;
   to.eps = c->pc.eps;
