@@ -7,8 +7,9 @@ K = 136 Zernike functions per patch (M = 15, 13.6 M unknowns), ID tolerance 1e-1
 incoming-grid tolerance 1e-8, cube-sphere tree. One step = one product y = A x of
 the second-kind system (outgoing map, P2L onto incoming grids, direct sums, L2P,
 Zernike transform) in the FP32 kernels that the mixed-precision solve iterates with.
-The line also reports the FP64 product rate and, with --solve, the mixed and FP64
-solve times to a 1e-8 relative residual.
+The line also reports the FP64 and float-float product rates, the metric's solves to a
+1e-8 relative residual (mixed, float-float and plain FP64, each with its recomputed true
+residual and the density error against the FP64 solution) and the 256-sphere batch.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
     torchrun --nproc-per-node N bench.py --gpus N ...   (independent replicas)
@@ -231,25 +232,9 @@ def run_ours(args):
 
     solve = None
     if args.solve:
-        solve = {}
-        # mixed: FP32 inner GMRES + float-float residual; df64: every product in float-float
-        # (FP64-accurate on the FP32 pipes); fp64: every product on the FP64 pipe (slow on
-        # this part, only with --solve-fp64)
-        for name, p in (("mixed", ncs.MIXED), ("df64", ncs.DF64), ("fp64", ncs.FP64)):
-            if name == "fp64" and not args.solve_fp64:
-                continue
-            t0 = time.time()
-            r = ctx.solve(tol=1e-8, precision=p, want_fhat=False, allow_noconv=True)
-            solve[name] = {"seconds": round(time.time() - t0, 3), "iterations": r["iterations"],
-                           "relres": r["relres"], "mu": r["scalar"], "rc": r["rc"]}
-        # the paper's error measure for its large runs (eq. l2res): the relative L2 residual
-        # of the mixed solution on a seeded random patch, the other patches' potential in
-        # FP64 from their skeletons (untimed; a second mixed solve returns the densities)
-        r = ctx.solve(tol=1e-8, precision=ncs.MIXED, want_fhat=True, allow_noconv=True)
-        ip = int(np.random.default_rng(1906).integers(N))
-        t0 = time.time()
-        l2 = ctx.patch_residual(ip, r["fhat"])
-        solve["mixed"]["patch_residual"] = {"patch": ip, "l2": l2, "seconds": round(time.time() - t0, 3)}
+        solve = solve_legs(args, ctx, N, K, sp)
+
+    batch = batch_leg(args) if (args.batch and rank == 0) else None
 
     peaks, src = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
@@ -299,11 +284,86 @@ def run_ours(args):
         "pairs_per_step": tstats["p2l_pairs"] + tstats["direct_pairs"],
         "pair_rate_per_s": round((tstats["p2l_pairs"] + tstats["direct_pairs"]) * 1000.0 / ms_step, 1),
         "solve": solve,
+        "batch": batch,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def solve_legs(args, ctx, N, K, sp):
+    """The metric's solves of the same workload to a relative residual of args.solve_tol:
+    mixed (FP32 inner GMRES + float-float refinement residuals), float-float (every
+    product FP64-accurate on the FP32 pipes) and plain FP64 (every product on the FP64
+    pipe). Each is timed around the ncs_solve call (densities copied back included); its
+    true residual b - A x is then recomputed with one float-float product, outside the
+    timed region, and the densities are compared with the FP64 solve's."""
+    import torch
+
+    from paper_1906_04209_gb300 import ncs
+
+    P = ctx.operator()["P"]
+    b = torch.tensor(np.tile(P.sum(axis=1), N), dtype=torch.float64, device="cuda")
+    bn = float(torch.linalg.norm(b))
+    legs = [("mixed", ncs.MIXED), ("df64", ncs.DF64)]
+    if args.solve_fp64:
+        legs.append(("fp64", ncs.FP64))
+    out, fh = {}, {}
+    for name, p in legs:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = ctx.solve(tol=args.solve_tol, precision=p, want_fhat=True, allow_noconv=True)
+        sec = time.perf_counter() - t0
+        st = ctx.solve_stats()
+        xd = torch.from_numpy(r["fhat"]).to("cuda")
+        yd = torch.empty_like(xd)
+        ctx.matvec_dev(xd.data_ptr(), yd.data_ptr(), ncs.DF64, sp)
+        torch.cuda.synchronize()
+        true = float(torch.linalg.norm(b - yd)) / bn
+        out[name] = {"seconds": round(sec, 3), "iterations": r["iterations"],
+                     "gmres_steps": int(st["gmres_steps"]), "residual_products": int(st["residual_products"]),
+                     "residual_updates": int(st["residual_updates"]), "graph_replays": int(st["graph_replays"]),
+                     "mu": r["scalar"], "relres_reported": r["relres"], "relres_true": true, "rc": r["rc"]}
+        fh[name] = r["fhat"]
+        del xd, yd
+    ref = "fp64" if "fp64" in fh else "df64"
+    fr = fh[ref]
+    for name in fh:
+        if name != ref:
+            out[name]["density_err_vs_" + ref] = float(np.abs(fh[name] - fr).max() / np.abs(fr).max())
+            out[name]["mu_relerr_vs_" + ref] = abs(out[name]["mu"] - out[ref]["mu"]) / abs(out[ref]["mu"])
+    if "fp64" in out:
+        out["speedup_mixed_over_fp64"] = round(out["fp64"]["seconds"] / out["mixed"]["seconds"], 2)
+        out["speedup_df64_over_fp64"] = round(out["fp64"]["seconds"] / out["df64"]["seconds"], 2)
+    out["speedup_mixed_over_df64"] = round(out["df64"]["seconds"] / out["mixed"]["seconds"], 2)
+    out["tol"] = args.solve_tol
+    # the paper's error measure for its large runs (eq. l2res): the relative L2 residual of
+    # the mixed solution on a seeded random patch (untimed)
+    ip = int(np.random.default_rng(1906).integers(N))
+    t0 = time.time()
+    l2 = ctx.patch_residual(ip, fh["mixed"])
+    out["mixed"]["patch_residual"] = {"patch": ip, "l2": l2, "seconds": round(time.time() - t0, 3)}
+    return out
+
+
+def batch_leg(args):
+    """The batch workload: 256 independent spheres (N log-uniform in [50, 5000], eps in
+    [0.005, 0.02], half interior, K = 128), each solved to args.solve_tol in mixed
+    precision with its own precompute and tree; wall time and aggregate products/s."""
+    from paper_1906_04209_gb300 import layouts as L, ncs
+    work = L.batch_workload(args.batch_size)
+    inst = [(c, e, m) for c, e, m, _ in work]
+    K = work[0][3]
+    t0 = time.perf_counter()
+    out = ncs.batch_solve(inst, K, tol=args.solve_tol, precision=ncs.MIXED)
+    wall = time.perf_counter() - t0
+    prods = int(np.sum(out["iterations"]))
+    return {"instances": len(inst), "patches": int(sum(len(c) for c, _, _ in inst)), "K": K,
+            "wall_s": round(wall, 3), "setup_s_summed": round(float(out["seconds"][0]), 3),
+            "solve_s_summed": round(float(out["seconds"][1]), 3), "products": prods,
+            "products_per_s": round(prods / wall, 2), "max_relres": float(np.max(out["relres"])),
+            "all_converged": bool(np.all(out["status"] == 0))}
 
 
 def cpu_baseline(args, centres, eps, mode, K, seconds=None):
@@ -364,11 +424,14 @@ def main():
     ap.add_argument("--grid-tol", type=float, default=1e-8)
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--df64-steps", type=int, default=2)
-    ap.add_argument("--solve", action="store_true")
+    ap.add_argument("--no-solve", dest="solve", action="store_false")
+    ap.add_argument("--solve-tol", type=float, default=1e-8)
+    ap.add_argument("--no-batch", dest="batch", action="store_false")
+    ap.add_argument("--batch-size", type=int, default=256)
     # a smaller layout of the same family (profiler captures only; the line names its N)
     ap.add_argument("--patches", type=int, default=None)
     ap.add_argument("--tensor-cores", type=int, default=1, choices=[0, 1])
-    ap.add_argument("--solve-fp64", action="store_true")
+    ap.add_argument("--no-solve-fp64", dest="solve_fp64", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=10.0)

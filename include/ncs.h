@@ -101,6 +101,10 @@ typedef struct ncs_params {
                           and the T assembly) on the CUDA device current at ncs_create
                           when there is one, else on the host; 0: always on the host. The
                           per-mode LUs and solves stay on the host */
+  int cuda_graphs;     /* 1 (default): ncs_solve captures one GMRES step (the product, the
+                          orthogonalisation and the Givens update, all reading the step
+                          index from device memory) as a CUDA graph on its first use and
+                          replays it; 0: the same kernels launched one by one */
 } ncs_params;
 
 /* Fills *p with the defaults listed above. */
@@ -286,6 +290,17 @@ int ncs_solve(ncs_ctx* ctx, double tol, int precision, double* fhat, double* sca
               double* Isigma, int* iterations, double* relres);
 
 /*
+ * Counters of the last ncs_solve on ctx, into out[0..n): [0] GMRES steps (products at the
+ * inner precision), [1] residuals recomputed as b - A x (products at the residual
+ * precision: NCS_MIXED's mixed_residual, else the solve's), [2] FP32 residual updates
+ * r - A corr, [3] refinement steps (NCS_MIXED), [4] the final relative residual, [5] steps
+ * run as a replay of the captured CUDA graph, [6] wall seconds of the solve, [7] 1 if the
+ * final residual was recomputed as b - A x (always, unless the solve stopped early on an
+ * error). Errors: NCS_E_INPUT (NULL).
+ */
+int ncs_solve_stats(const ncs_ctx* ctx, double* out, int n);
+
+/*
  * Single-layer potential at M off-patch targets (Section 2, eqs. urep and
  * intBVPansatz, off-surface Green's functions eqs. Gextoffsurface /
  * Gintoffsurface): u(x) = sum_j sum_m G(x, s_jm) rho_jm with rho_j = T fhat_j.
@@ -329,10 +344,13 @@ int ncs_block_dots(int64_t n, int k, const double* V, int64_t ld, const double* 
  * counterpart: this is a property of the library, not of the method. The partial sums
  * live in a fixed device array inside the library (room for k <= 1024 vectors, 512 KiB,
  * held by every GPU that loads the library until the process exits); the first call on
- * a device looks its address up with that device current, so make that first call
- * before any stream capture. Asynchronous on `stream`; calls that overlap on the GPU
- * share the array and race, so serialise them. Nothing is allocated or freed.
- * Errors: NCS_E_INPUT (k > 1024, bad sizes or NULL), NCS_E_CUDA.
+ * a device looks its address up with that device current (which may load the library's
+ * device code on that device), so make that first call before any stream capture.
+ * Asynchronous on `stream`; calls that overlap on the GPU share the array and race, so
+ * serialise them. Nothing is allocated or freed.
+ * Errors: NCS_E_INPUT (k > 1024, bad sizes or NULL), NCS_E_CUDA (also when an earlier,
+ * unrelated CUDA error is pending on the calling thread: it is reported, and cleared,
+ * before anything is launched).
  */
 int ncs_block_dots_noalloc(int64_t n, int k, const double* V, int64_t ld, const double* w, double* out,
                            void* stream);

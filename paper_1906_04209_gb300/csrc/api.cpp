@@ -75,6 +75,30 @@ T* dev_alloc(size_t n) {
   return p;
 }
 
+// The captured Arnoldi steps hold the layout's, the workspace's and the product path's
+// pointers: dropped whenever one of them changes.
+void invalidate_graphs(ncs_ctx* c) {
+  for (int p = 0; p < 4; ++p)
+    if (c->step_graph[p]) {
+      cudaGraphExecDestroy(c->step_graph[p]);
+      c->step_graph[p] = nullptr;
+      c->step_graph_kernels[p] = 0;
+    }
+}
+
+void free_krylov(ncs_ctx* c) {
+  invalidate_graphs(c);
+  dev_free(c->V);
+  dev_free(c->work);
+  dev_free(c->partial);
+  dev_free(c->hdev);
+  dev_free(c->gmem);
+  c->gd = ncs::GmresDev();
+  if (c->st_host) cudaFreeHost(c->st_host);
+  c->st_host = nullptr;
+  c->Vcap = 0;
+}
+
 void free_layout(ncs_ctx* c) {
   DeviceData& d = c->d;
   dev_free(d.centres);
@@ -84,11 +108,7 @@ void free_layout(ncs_ctx* c) {
   dev_free(d.rho32);
   dev_free(d.z);
   dev_free(d.Apack);
-  dev_free(c->V);
-  dev_free(c->work);
-  dev_free(c->partial);
-  dev_free(c->hdev);
-  c->Vcap = 0;
+  free_krylov(c);
   ncs::tree_free(c->tdev);
   c->tree_built = false;
   c->tree_uploaded = false;
@@ -319,6 +339,7 @@ double dev_dot(ncs_ctx* c, const double* a, const double* b, cudaStream_t s) {
 void ensure_krylov(ncs_ctx* c, int maxit) {
   const int64_t n = c->d.N * c->d.K;
   if (c->Vcap < maxit + 1) {
+    invalidate_graphs(c);
     dev_free(c->V);
     c->V = dev_alloc<double>((size_t)(maxit + 1) * n);
     c->Vcap = maxit + 1;
@@ -326,76 +347,124 @@ void ensure_krylov(ncs_ctx* c, int maxit) {
     dev_free(c->hdev);
     c->partial = dev_alloc<double>((size_t)ncs::kDotChunks * (maxit + 2));
     c->hdev = dev_alloc<double>(maxit + 2);
+    // device GMRES state and arrays, one allocation
+    dev_free(c->gmem);
+    const size_t m1 = (size_t)maxit + 1, nb = (size_t)ncs::gmres_update_blocks(n);
+    const size_t st_words = (sizeof(ncs::GmresState) + 7) / 8;
+    const size_t words = st_words + m1 * maxit + 2 * (size_t)maxit + m1 + maxit + 2 * m1 + ncs::kDotChunks * m1 +
+                         nb + (size_t)n;
+    c->gmem = dev_alloc<double>(words);
+    ncs::GmresDev& g = c->gd;
+    double* q = c->gmem;
+    g.maxit = maxit;
+    g.st = reinterpret_cast<ncs::GmresState*>(q);
+    q += st_words;
+    g.H = q, q += m1 * maxit;
+    g.cs = q, q += maxit;
+    g.sn = q, q += maxit;
+    g.g = q, q += m1;
+    g.y = q, q += maxit;
+    g.h1 = q, q += m1;
+    g.h2 = q, q += m1;
+    g.partial = q, q += ncs::kDotChunks * m1;
+    g.pnorm = q, q += nb;
+    g.vk = q;
   }
   if (!c->work) c->work = dev_alloc<double>(5 * (size_t)n);
+  if (!c->st_host) CU(cudaHostAlloc((void**)&c->st_host, sizeof(ncs::GmresState), cudaHostAllocDefault));
 }
 
-// GMRES (x0 = 0, no restart, CGS2 orthogonalisation on the device, Givens on the host)
-// for A e = r with products at precision `prec`. Returns the number of products and
-// the estimated relative residual; e receives the iterate.
+// One Arnoldi step: w = A vk, two Gram-Schmidt passes, the Givens update, the next basis
+// vector, and a copy of the device state into pinned host memory. Every argument is fixed
+// for a given workspace and layout; the step's column index is read on the device.
+void arnoldi_step(ncs_ctx* c, int prec, cudaStream_t s) {
+  const int64_t n = c->d.N * c->d.K;
+  double* w = c->work + 3 * n;
+  matvec(c, c->gd.vk, w, prec, s);
+  CU(ncs::launch_arnoldi_orthogonalize(n, c->V, w, c->gd, s));
+  CU(cudaMemcpyAsync(c->st_host, c->gd.st, sizeof(ncs::GmresState), cudaMemcpyDeviceToHost, s));
+}
+
+// Captures arnoldi_step as a CUDA graph (once per precision and workspace). On any failure
+// the context keeps launching the step directly (the same kernels) and says why.
+void capture_step(ncs_ctx* c, int prec, cudaStream_t s) {
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    c->graphs_off = true;
+    return;
+  }
+  const long long n0 = ncs::g_launches.load();
+  bool ok = true;
+  try {
+    arnoldi_step(c, prec, s);
+  } catch (const Fail& f) {
+    ok = false;
+    c->graph_note = f.msg;
+  }
+  const long long n1 = ncs::g_launches.load();
+  ncs::g_launches.fetch_sub(n1 - n0);  // captured, not launched
+  const cudaError_t e = cudaStreamEndCapture(s, &g);
+  cudaGraphExec_t ge = nullptr;
+  if (ok && e == cudaSuccess && g && cudaGraphInstantiate(&ge, g, 0) == cudaSuccess) {
+    c->step_graph[prec] = ge;
+    c->step_graph_kernels[prec] = n1 - n0;
+  } else {
+    cudaGetLastError();
+    if (ok) c->graph_note = std::string("graph capture: ") + cudaGetErrorString(e);
+    c->graphs_off = true;
+  }
+  if (g) cudaGraphDestroy(g);
+}
+
+// GMRES (x0 = 0, no restart) for A e = r with products at precision `prec`, its whole
+// state on the device: CGS2 orthogonalisation, Givens rotations, residual estimate and
+// back substitution in FP64 kernels. The host launches one step (a replay of the captured
+// graph after the first) and reads the 48-byte state back. Returns the number of products;
+// *est receives the estimated relative residual, e the iterate.
 int gmres(ncs_ctx* c, const double* r, double* e, double tol, int prec, int maxit, double* est,
           cudaStream_t s) {
   const int64_t n = c->d.N * c->d.K;
-  double* w = c->work + 3 * n;
   const double beta = std::sqrt(dev_dot(c, r, r, s));
   CU(cudaMemsetAsync(e, 0, n * sizeof(double), s));
+  if (!std::isfinite(beta)) throw Fail{NCS_E_NUMERIC, "GMRES: non-finite right-hand side"};
   if (!(beta > 0.0)) {
-    if (!std::isfinite(beta)) throw Fail{NCS_E_NUMERIC, "GMRES: non-finite right-hand side"};
     *est = 0.0;
     return 0;
   }
-  double* V = c->V;
-  CU(ncs::launch_scale_copy(n, r, 1.0 / beta, V, s));
-  std::vector<double> H((size_t)(maxit + 1) * maxit, 0.0), cs(maxit), sn(maxit), g(maxit + 1, 0.0);
-  std::vector<double> h(maxit + 2), h2(maxit + 2);
-  g[0] = beta;
-  int k = 0, m = 0;
-  double res = 1.0;
-  for (k = 0; k < maxit; ++k) {
-    matvec(c, V + (size_t)k * n, w, prec, s);
-    // classical Gram-Schmidt, twice
-    CU(ncs::launch_dots(n, k + 1, V, n, w, c->partial, c->hdev, s));
-    CU(cudaMemcpyAsync(h.data(), c->hdev, (k + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
-    CU(ncs::launch_sub_combination(n, k + 1, V, n, c->hdev, w, -1.0, s));
-    CU(ncs::launch_dots(n, k + 1, V, n, w, c->partial, c->hdev, s));
-    CU(cudaMemcpyAsync(h2.data(), c->hdev, (k + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
-    CU(ncs::launch_sub_combination(n, k + 1, V, n, c->hdev, w, -1.0, s));
-    const double hn = std::sqrt(dev_dot(c, w, w, s));  // synchronises the stream
-    for (int j = 0; j <= k; ++j) H[(size_t)j * maxit + k] = h[j] + h2[j];
-    H[(size_t)(k + 1) * maxit + k] = hn;
-    if (!std::isfinite(hn)) throw Fail{NCS_E_NUMERIC, "GMRES: non-finite Arnoldi vector"};
-    for (int j = 0; j < k; ++j) {
-      const double a = H[(size_t)j * maxit + k], b = H[(size_t)(j + 1) * maxit + k];
-      H[(size_t)j * maxit + k] = cs[j] * a + sn[j] * b;
-      H[(size_t)(j + 1) * maxit + k] = -sn[j] * a + cs[j] * b;
+  ncs::GmresDev& gd = c->gd;
+  maxit = std::min(maxit, gd.maxit);
+  *c->st_host = ncs::GmresState{0, 0, ncs::kGmresRunning, maxit, beta, tol, 1.0, 0.0};
+  CU(cudaMemcpyAsync(gd.st, c->st_host, sizeof(ncs::GmresState), cudaMemcpyHostToDevice, s));
+  CU(ncs::launch_scale_copy(n, r, 1.0 / beta, c->V, s));
+  CU(cudaMemcpyAsync(gd.vk, c->V, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  int steps = 0;
+  while (steps < maxit) {
+    if (steps > 0 && c->prm.cuda_graphs && !c->graphs_off && !c->step_graph[prec]) capture_step(c, prec, s);
+    if (steps > 0 && c->step_graph[prec]) {
+      CU(cudaGraphLaunch(c->step_graph[prec], s));
+      ncs::g_launches.fetch_add(c->step_graph_kernels[prec]);
+      c->solve_stats[5] += 1.0;
+    } else {
+      arnoldi_step(c, prec, s);
     }
-    const double a = H[(size_t)k * maxit + k], b = H[(size_t)(k + 1) * maxit + k];
-    const double rr = std::hypot(a, b);
-    if (!(rr > 0.0)) throw Fail{NCS_E_NUMERIC, "GMRES: breakdown (zero Hessenberg column)"};
-    cs[k] = a / rr;
-    sn[k] = b / rr;
-    H[(size_t)k * maxit + k] = rr;
-    H[(size_t)(k + 1) * maxit + k] = 0.0;
-    g[k + 1] = -sn[k] * g[k];
-    g[k] = cs[k] * g[k];
-    res = std::fabs(g[k + 1]) / beta;
-    m = k + 1;
-    if (log_level() > 1) std::fprintf(stderr, "ncs: gmres it %d est %.3e\n", m, res);
-    if (res <= tol || hn == 0.0) break;
-    CU(ncs::launch_scale_copy(n, w, 1.0 / hn, V + (size_t)(k + 1) * n, s));
+    CU(cudaStreamSynchronize(s));
+    ++steps;
+    const ncs::GmresState h = *c->st_host;
+    if (log_level() > 1) std::fprintf(stderr, "ncs: gmres it %d est %.3e\n", h.m, h.res);
+    if (h.done) break;
   }
-  // y = H^-1 g, e = V y
-  std::vector<double> y(m);
-  for (int i = m - 1; i >= 0; --i) {
-    double t = g[i];
-    for (int j = i + 1; j < m; ++j) t -= H[(size_t)i * maxit + j] * y[j];
-    y[i] = t / H[(size_t)i * maxit + i];
+  const ncs::GmresState h = *c->st_host;
+  if (h.flag == ncs::kGmresNonFinite) throw Fail{NCS_E_NUMERIC, "GMRES: non-finite Arnoldi vector"};
+  if (h.flag == ncs::kGmresBreakdown && h.m == 0) throw Fail{NCS_E_NUMERIC, "GMRES: breakdown (zero Hessenberg column)"};
+  if (h.m > 0) {
+    CU(ncs::launch_gmres_backsolve(gd, s));
+    CU(ncs::launch_sub_combination(n, h.m, c->V, n, gd.y, e, 1.0, s));
   }
-  CU(cudaMemcpyAsync(c->hdev, y.data(), m * sizeof(double), cudaMemcpyHostToDevice, s));
-  CU(ncs::launch_sub_combination(n, m, V, n, c->hdev, e, 1.0, s));
   CU(cudaStreamSynchronize(s));
-  *est = res;
-  return m;
+  *est = h.flag == ncs::kGmresBreakdown ? 1.0 : h.res;
+  c->solve_stats[0] += steps;
+  return steps;
 }
 
 void validate_centres(int64_t N, const double* cen, double eps) {
@@ -493,6 +562,7 @@ void ncs_default_params(ncs_params* p) {
   p->residual_update = 1;
   p->id_ladder_max = 1.0;
   p->device_precompute = 1;
+  p->cuda_graphs = 1;
 }
 
 int ncs_create(double eps, int mode, int K, const ncs_params* params, ncs_ctx** out) {
@@ -758,6 +828,7 @@ int ncs_tree_stats(ncs_ctx* c, int64_t* out, int n) {
 int ncs_set_method(ncs_ctx* c, int method) {
   if (!c) return NCS_E_INPUT;
   if (method < 0 || method > 2) return finish(c, Fail{NCS_E_INPUT, "bad method"});
+  if (method != c->method) invalidate_graphs(c);
   c->method = method;
   if (!c->centres.empty() && use_tree(c)) {
     try {
@@ -881,6 +952,8 @@ int ncs_solve(ncs_ctx* c, double tol, int precision, double* fhat, double* scala
     if (precision != NCS_FP64 && precision != NCS_FP32 && precision != NCS_MIXED && precision != NCS_DF64)
       throw Fail{NCS_E_INPUT, "bad precision"};
     check_ready(c);
+    const auto t_start = std::chrono::steady_clock::now();
+    for (double& v : c->solve_stats) v = 0.0;
     const int maxit = c->prm.gmres_maxit;
     ensure_krylov(c, maxit);
     const int64_t n = c->d.N * c->d.K;
@@ -909,30 +982,53 @@ int ncs_solve(ncs_ctx* c, double tol, int precision, double* fhat, double* scala
       CU(ncs::launch_axpby(n, 1.0, b, -1.0, r, s));
       rel = std::sqrt(dev_dot(c, r, r, s)) / bnorm;
       ++total;
-      converged = est <= tol;
+      c->solve_stats[1] += 1.0;
+      c->solve_stats[7] = 1.0;
+      // both the GMRES estimate and the recomputed residual must meet the tolerance (an
+      // FP32 product's estimate can fall below it while b - A x stays near 1e-6)
+      converged = est <= tol && rel <= tol;
     } else {
       // iterative refinement: FP32 inner GMRES, FP64-accurate residuals. Once the
       // residual is small, the correction is small as well and the new residual is
       // updated as r - A corr with the FP32 product: its error (about 1e-6 |A corr|,
       // |A corr| ~ |r|) is then below kUpdateRel * 1e-6 of |b|, far under the tolerance.
+      // An updated residual that meets the tolerance is checked by recomputing b - A x at
+      // the residual precision before the solve reports convergence.
       constexpr double kUpdateRel = 1e-4;
       double* corr = c->work + 4 * n;
       CU(cudaMemsetAsync(x, 0, n * sizeof(double), s));
       CU(cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
       rel = 1.0;
+      bool updated = false;  // r was formed by the FP32 update, not recomputed
       for (int outer = 0; outer < 20; ++outer) {
-        if (rel <= tol) break;
+        if (rel <= tol) {
+          if (!updated) break;
+          matvec(c, x, r, c->prm.mixed_residual, s);
+          CU(ncs::launch_axpby(n, 1.0, b, -1.0, r, s));
+          ++total;
+          c->solve_stats[1] += 1.0;
+          updated = false;
+          rel = std::sqrt(dev_dot(c, r, r, s)) / bnorm;
+          if (log_level() > 0) std::fprintf(stderr, "ncs: refinement check relres %.3e\n", rel);
+          if (!std::isfinite(rel)) throw Fail{NCS_E_NUMERIC, "refinement: non-finite residual"};
+          if (rel <= tol) break;
+        }
         const double inner_tol = std::max(0.3 * tol / rel, 3e-6);
         double inner_est = 1.0;
         total += gmres(c, r, corr, std::min(inner_tol, 0.5), NCS_FP32, maxit, &inner_est, s);
+        c->solve_stats[3] += 1.0;
         CU(ncs::launch_axpby(n, 1.0, corr, 1.0, x, s));
         if (rel <= kUpdateRel && c->prm.residual_update) {
           double* Ac = c->work + 3 * n;
           matvec(c, corr, Ac, NCS_FP32, s);
           CU(ncs::launch_axpby(n, -1.0, Ac, 1.0, r, s));
+          c->solve_stats[2] += 1.0;
+          updated = true;
         } else {
           matvec(c, x, r, c->prm.mixed_residual, s);
           CU(ncs::launch_axpby(n, 1.0, b, -1.0, r, s));
+          c->solve_stats[1] += 1.0;
+          updated = false;
         }
         ++total;
         const double newrel = std::sqrt(dev_dot(c, r, r, s)) / bnorm;
@@ -940,10 +1036,12 @@ int ncs_solve(ncs_ctx* c, double tol, int precision, double* fhat, double* scala
         if (!std::isfinite(newrel)) throw Fail{NCS_E_NUMERIC, "refinement: non-finite residual"};
         const bool stalled = newrel > 0.9 * rel && outer > 0;
         rel = newrel;
-        if (stalled) break;
+        if (stalled && !(rel <= tol && updated)) break;
       }
-      converged = rel <= tol;
+      converged = rel <= tol && !updated;
+      c->solve_stats[7] = updated ? 0.0 : 1.0;
     }
+    c->solve_stats[4] = rel;
     // I_sigma = I . sum_i f_i (eq. getI), then mu or C
     CU(ncs::launch_periodic_dot(n, c->d.K, x, c->d.I, c->partial, c->hdev, s));
     double Is = 0.0;
@@ -951,6 +1049,7 @@ int ncs_solve(ncs_ctx* c, double tol, int precision, double* fhat, double* scala
     if (fhat) CU(cudaMemcpyAsync(fhat, x, n * sizeof(double), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
     check_tc(c);
+    c->solve_stats[6] = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
     if (Isigma) *Isigma = Is;
     if (scalar) *scalar = (c->pc.mode == NCS_INTERIOR) ? 1.0 / (3.0 * Is) - 0.6 : 4.0 * M_PI * Is;
     if (iterations) *iterations = total;
@@ -1216,6 +1315,12 @@ int ncs_batch_solve(int B, const double* eps, const int* mode, const int64_t* N,
   if (status)
     for (int b = 0; b < B; ++b)
       if (status[b] != NCS_OK) return status[b];
+  return NCS_OK;
+}
+
+int ncs_solve_stats(const ncs_ctx* c, double* out, int n) {
+  if (!c || !out) return NCS_E_INPUT;
+  for (int i = 0; i < n && i < 8; ++i) out[i] = c->solve_stats[i];
   return NCS_OK;
 }
 

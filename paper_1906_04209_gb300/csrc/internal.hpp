@@ -84,6 +84,42 @@ cudaError_t launch_periodic_dot(int64_t n, int K, const double* x, const double*
                                 double* out, cudaStream_t s);
 constexpr int kDotChunks = 64;
 
+// ---- GMRES state on the device (blas.cu). The column in progress is m; a step reads it,
+// so the same launches (and one captured CUDA graph) serve every iteration.
+constexpr int kGmresRunning = 0, kGmresConverged = 1, kGmresHappy = 2, kGmresBreakdown = 3, kGmresNonFinite = 4;
+struct GmresState {
+  int m;       // Arnoldi columns completed (= index of the column in progress)
+  int done;    // 1: no further step (flag says why; flag 0 with done = iteration cap)
+  int flag;    // kGmres*
+  int maxit;   // iteration cap
+  double beta; // |r0|
+  double tol;  // relative tolerance of the estimate |g_m| / beta
+  double res;  // current estimate
+  double hn;   // norm of the newest (orthogonalised) vector
+};
+// Device pointers of one context's GMRES workspace.
+struct GmresDev {
+  int maxit = 0;
+  GmresState* st = nullptr;
+  double* H = nullptr;        // (maxit + 1) x maxit, column-major
+  double* cs = nullptr;       // maxit
+  double* sn = nullptr;       // maxit
+  double* g = nullptr;        // maxit + 1
+  double* y = nullptr;        // maxit
+  double* h1 = nullptr;       // maxit + 1: first Gram-Schmidt pass
+  double* h2 = nullptr;       // maxit + 1: second pass
+  double* partial = nullptr;  // kDotChunks x (maxit + 1)
+  double* pnorm = nullptr;    // gmres_update_blocks(n)
+  double* vk = nullptr;       // n: copy of the newest basis vector (the product's input)
+};
+int gmres_update_blocks(int64_t n);
+// Two Gram-Schmidt passes of w against V_0..V_m, the Givens update of column m and
+// V_{m+1} = vk = w / |w| (every launch a no-op once st->done).
+cudaError_t launch_arnoldi_orthogonalize(int64_t n, const double* V, double* w, const GmresDev& gd,
+                                         cudaStream_t s);
+// y = R^-1 g (m from the device state).
+cudaError_t launch_gmres_backsolve(const GmresDev& gd, cudaStream_t s);
+
 }  // namespace ncs
 
 // The opaque context of the C ABI.
@@ -107,7 +143,16 @@ struct ncs_ctx {
   // GMRES workspace
   double* V = nullptr;
   int Vcap = 0;
-  double* work = nullptr;      // 4 vectors of N*K
+  double* work = nullptr;      // 5 vectors of N*K
   double* partial = nullptr;   // kDotChunks * (maxit+2)
   double* hdev = nullptr;      // maxit+2
+  double* gmem = nullptr;      // backing store of gd
+  ncs::GmresDev gd;
+  ncs::GmresState* st_host = nullptr;  // pinned copy of *gd.st, read after each step
+  // one captured Arnoldi step (product + orthogonalisation + state copy) per precision
+  cudaGraphExec_t step_graph[4] = {nullptr, nullptr, nullptr, nullptr};
+  long long step_graph_kernels[4] = {0, 0, 0, 0};
+  bool graphs_off = false;      // capture failed once: steps are launched directly
+  std::string graph_note;       // why
+  double solve_stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // see ncs_solve_stats
 };

@@ -59,6 +59,9 @@ extern "C" int ncs_block_dots_noalloc(int64_t n, int k, const double* V, int64_t
   if (n < 0 || k < 0 || ld < n || (k > 0 && (!V || !w || !out))) return NCS_E_INPUT;
   if (k > ncs::kNoAllocMaxVectors) return NCS_E_INPUT;  // beyond the fixed scratch
   if (k == 0) return NCS_OK;
+  // an error left by earlier, unrelated work on this thread would otherwise surface
+  // after this call's launch as if the launch had failed: report it before launching
+  if (cudaGetLastError() != cudaSuccess) return NCS_E_CUDA;
   int rc = NCS_OK;
   double* partial = ncs::scratch_for_current_device(&rc);
   if (!partial) return rc;

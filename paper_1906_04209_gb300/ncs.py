@@ -31,7 +31,7 @@ EXPORTS = ["ncs_default_params", "ncs_create", "ncs_create_from_operator", "ncs_
            "ncs_matvec_dev", "ncs_field_dev", "ncs_solve", "ncs_eval", "ncs_last_error", "ncs_destroy",
            "ncs_tree_pairs", "ncs_tree_stats", "ncs_profile_matvec", "ncs_create_from_operators", "ncs_get_reps",
            "ncs_tc_gemm_f32", "ncs_batch_solve", "ncs_block_dots", "ncs_block_dots_noalloc",
-           "ncs_launch_count", "ncs_get_rep", "ncs_set_precision", "ncs_patch_residual"]
+           "ncs_launch_count", "ncs_get_rep", "ncs_set_precision", "ncs_patch_residual", "ncs_solve_stats"]
 
 
 class ncs_params(ctypes.Structure):
@@ -40,7 +40,7 @@ class ncs_params(ctypes.Structure):
                 ("method", ctypes.c_int), ("tree_min_patches", ctypes.c_int), ("gmres_maxit", ctypes.c_int),
                 ("verbose", ctypes.c_int), ("mixed_residual", ctypes.c_int), ("tensor_cores", ctypes.c_int),
                 ("residual_update", ctypes.c_int), ("id_ladder_max", ctypes.c_double),
-                ("device_precompute", ctypes.c_int)]
+                ("device_precompute", ctypes.c_int), ("cuda_graphs", ctypes.c_int)]
 
 
 class NcsError(RuntimeError):
@@ -98,6 +98,7 @@ def load(path: str = LIB_PATH):
     lib.ncs_block_dots_noalloc.argtypes = [ctypes.c_int64, ctypes.c_int, VP, ctypes.c_int64, VP, VP, VP]
     lib.ncs_get_rep.argtypes = [VP, ctypes.c_int, D, D, D]
     lib.ncs_set_precision.argtypes = [VP, ctypes.c_int]
+    lib.ncs_solve_stats.argtypes = [VP, D, ctypes.c_int]
     lib.ncs_launch_count.argtypes = []
     lib.ncs_launch_count.restype = ctypes.c_int64
     lib.ncs_destroy.argtypes = [VP]
@@ -328,6 +329,14 @@ class Context:
         if rc != NCS_OK and not (allow_noconv and rc == NCS_E_NOCONV):
             self._check(rc)
         return dict(fhat=fhat, scalar=sc.value, Isigma=Is.value, iterations=it.value, relres=rr.value, rc=rc)
+
+    def solve_stats(self) -> dict:
+        """Counters of the last solve (see ncs_solve_stats)."""
+        out = np.zeros(8)
+        self._check(load().ncs_solve_stats(self.h, _ptr(out), 8))
+        keys = ["gmres_steps", "residual_products", "residual_updates", "refinement_steps", "relres",
+                "graph_replays", "seconds", "recomputed"]
+        return dict(zip(keys, out.tolist()))
 
     def eval(self, targets, fhat):
         t = _f64(targets).reshape(-1, 3)
