@@ -17,6 +17,7 @@ residual and the density error against the FP64 solution) and the 256-sphere bat
 from __future__ import annotations
 
 import argparse
+import faulthandler
 import json
 import math
 import os
@@ -45,6 +46,14 @@ P2L_BYTES_PER_PAIR = 185.7e6 / 1.5108e10
 # 12 pairs in 16 (the other 4 take a polynomial log2 on the FMA pipe; the packed pair
 # loop's default share)
 MUFU_PER_PAIR = 2.0 - 4.0 / 16.0
+
+
+_T0 = time.time()
+
+
+def _progress(msg):
+    """One line per leg on stderr (the JSON line stays alone on stdout)."""
+    print(f"[bench +{time.time() - _T0:.1f}s] {msg}", file=sys.stderr, flush=True)
 
 
 def _dist():
@@ -230,6 +239,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         df64 = 1000.0 * args.df64_steps / e0.elapsed_time(e1)
 
+    _progress("products done")
     solve = None
     if args.solve:
         solve = solve_legs(args, ctx, N, K, sp)
@@ -311,6 +321,7 @@ def solve_legs(args, ctx, N, K, sp):
         legs.append(("fp64", ncs.FP64))
     out, fh = {}, {}
     for name, p in legs:
+        _progress(f"solve {name}")
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         r = ctx.solve(tol=args.solve_tol, precision=p, want_fhat=True, allow_noconv=True)
@@ -341,6 +352,7 @@ def solve_legs(args, ctx, N, K, sp):
     # the paper's error measure for its large runs (eq. l2res): the relative L2 residual of
     # the mixed solution on a seeded random patch (untimed)
     ip = int(np.random.default_rng(1906).integers(N))
+    _progress("patch residual")
     t0 = time.time()
     l2 = ctx.patch_residual(ip, fh["mixed"])
     out["mixed"]["patch_residual"] = {"patch": ip, "l2": l2, "seconds": round(time.time() - t0, 3)}
@@ -352,9 +364,11 @@ def batch_leg(args):
     [0.005, 0.02], half interior, K = 128), each solved to args.solve_tol in mixed
     precision with its own precompute and tree; wall time and aggregate products/s."""
     from paper_1906_04209_gb300 import layouts as L, ncs
+    _progress("batch workload")
     work = L.batch_workload(args.batch_size)
     inst = [(c, e, m) for c, e, m, _ in work]
     K = work[0][3]
+    _progress("batch solve")
     t0 = time.perf_counter()
     out = ncs.batch_solve(inst, K, tol=args.solve_tol, precision=ncs.MIXED)
     wall = time.perf_counter() - t0
@@ -414,6 +428,7 @@ def run_reference(args):
 
 
 def main():
+    faulthandler.enable()  # a crash in native code prints the Python stack to stderr
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)

@@ -111,6 +111,25 @@ typedef struct ncs_params {
 void ncs_default_params(ncs_params* p);
 
 /*
+ * Launch configuration of the tree product's FP32 path, chosen per workload by ncs_tune
+ * (no counterpart in the paper, whose Section 7 "Optimizations and parallelization"
+ * leaves such choices to the implementation). Every setting gives the same product up to
+ * the FP32 rounding of its pair sums; none changes the accuracy of the FP64 or
+ * float-float products.
+ */
+typedef struct ncs_tuning {
+  int p2l_tile;       /* interaction-list patches per shared-memory tile of a P2L block: 8, 16 */
+  int p2l_poly;       /* of every 16 packed pair chains in the P2L kernel, how many take
+                         their logarithm on the FMA pipe instead of the MUFU unit: 0, 2, 4, 6 */
+  int direct_poly;    /* the same for the direct lists at the Zernike nodes: 0, 2, 4, 6 */
+  int item_patches;   /* interaction-list patches per P2L work item (one block): 8..64, a
+                         multiple of p2l_tile; changing it rebuilds the host tree */
+  double l2p_weight;  /* cost of one L2P node-grid product in pair evaluations, weighed when
+                         a group chooses its incoming grid or direct evaluation (Step 3):
+                         0.01..1; changing it rebuilds the host tree */
+} ncs_tuning;
+
+/*
  * Creates a context for patch radius eps (0 < eps < 1), problem mode
  * (NCS_EXTERIOR / NCS_INTERIOR) and K Zernike functions per patch (1 <= K <= 2000),
  * and runs the one-patch precompute (Section 7, Step 1): modal solves giving B
@@ -288,6 +307,32 @@ int ncs_field_dev(ncs_ctx* ctx, const double* x, double* z, int precision, void*
  */
 int ncs_solve(ncs_ctx* ctx, double tol, int precision, double* fhat, double* scalar,
               double* Isigma, int* iterations, double* relres);
+
+/*
+ * Autotuner of the tree product. Times FP32 tree products of the context's layout under
+ * candidate launch configurations (flags & 1: the pair-kernel variants, each stage timed
+ * with CUDA events; flags & 2: the work-item size and the grid-or-direct weight, each
+ * candidate on a rebuilt tree), keeps a candidate only if its product matches the
+ * float-float product of the same input to 2e-5 of the largest entry, and applies the
+ * fastest to ctx (products and solves that follow use it). With cache_path non-NULL the
+ * choice is looked up first in, and then appended to, that text file, keyed by mode, K,
+ * eps, N and the default tree's shape (levels, share of direct pairs); a hit costs no
+ * trial products. out (may be NULL) receives the chosen configuration; report (may be
+ * NULL, n entries) receives [0] default product ms, [1] tuned product ms, [2] trial
+ * products, [3] the chosen product's error against float-float (relative to max |z|),
+ * [4] seconds spent, [5] 1 if the choice came from the cache. Uses the device, the
+ * context's stream and one temporary device buffer (2 N K* doubles).
+ * Errors: NCS_E_INPUT (flags), NCS_E_STATE (no patches, or not the tree method),
+ * NCS_E_OOM, NCS_E_CUDA.
+ */
+int ncs_tune(ncs_ctx* ctx, int flags, const char* cache_path, ncs_tuning* out, double* report, int n);
+
+/* Applies a launch configuration (as from ncs_tune) to ctx. Errors: NCS_E_INPUT (a value
+ * outside the ranges of ncs_tuning). */
+int ncs_set_tuning(ncs_ctx* ctx, const ncs_tuning* t);
+
+/* The context's current launch configuration. Errors: NCS_E_INPUT (NULL). */
+int ncs_get_tuning(const ncs_ctx* ctx, ncs_tuning* t);
 
 /*
  * Counters of the last ncs_solve on ctx, into out[0..n): [0] GMRES steps (products at the

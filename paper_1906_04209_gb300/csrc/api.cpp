@@ -263,6 +263,15 @@ bool use_tree(const ncs_ctx* c) {
   return (int64_t)(c->centres.size() / 3) >= c->prm.tree_min_patches;
 }
 
+ncs::TreeOptions tree_options(const ncs_ctx* c) {
+  ncs::TreeOptions to;
+  to.grid_tol = c->prm.grid_tol;
+  to.eps = c->pc.eps;
+  to.item_patches = c->tune.item_patches;
+  to.l2p_weight = c->tune.l2p_weight;
+  return to;
+}
+
 // host part of the tree (Step 2 of Section 7)
 void ensure_tree_host(ncs_ctx* c) {
   if (c->tree_built) return;
@@ -270,10 +279,7 @@ void ensure_tree_host(ncs_ctx* c) {
   // the thread count is an ICV of the calling host thread: the context's, on every build
   omp_set_num_threads(c->prm.threads > 0 ? c->prm.threads : omp_get_num_procs());
 #endif
-  ncs::TreeOptions to;
-  to.grid_tol = c->prm.grid_tol;
-  to.eps = c->pc.eps;
-  ncs::tree_build(c->centres, c->pc, to, c->tree);
+  ncs::tree_build(c->centres, c->pc, tree_options(c), c->tree);
   c->tree_built = true;
 }
 
@@ -283,6 +289,9 @@ void ensure_tree(ncs_ctx* c) {
     ncs::tree_upload(c->tree, c->pc, c->tdev);
     c->tree_uploaded = true;
   }
+  c->tdev.cfg.p2l_tile = c->tune.p2l_tile;
+  c->tdev.cfg.p2l_poly = c->tune.p2l_poly;
+  c->tdev.cfg.direct_poly = c->tune.direct_poly;
 }
 
 void outgoing(ncs_ctx* c, const double* x, int prec, cudaStream_t s) {
@@ -541,6 +550,66 @@ void validate_params(const ncs_params& p) {
     throw Fail{NCS_E_INPUT, "mixed_residual must be NCS_FP64 or NCS_DF64"};
 }
 
+bool tuning_valid(const ncs_tuning& t) {
+  const auto poly_ok = [](int p) { return p == 0 || p == 2 || p == 4 || p == 6; };
+  return (t.p2l_tile == 8 || t.p2l_tile == 16) && poly_ok(t.p2l_poly) && poly_ok(t.direct_poly) &&
+         t.item_patches >= 8 && t.item_patches <= 64 && t.item_patches % t.p2l_tile == 0 &&
+         t.l2p_weight >= 0.01 && t.l2p_weight <= 1.0;
+}
+
+// Applies a launch configuration; a change of the tree knobs drops the tree (rebuilt on
+// the host, and uploaded, at the next product).
+void apply_tuning(ncs_ctx* c, const ncs_tuning& t) {
+  const bool rebuild = t.item_patches != c->tune.item_patches || t.l2p_weight != c->tune.l2p_weight;
+  c->tune = t;
+  invalidate_graphs(c);
+  if (rebuild && c->tree_built) {
+    ncs::tree_free(c->tdev);
+    c->tree_built = false;
+    c->tree_uploaded = false;
+    c->tree = ncs::TreeHost();
+  }
+}
+
+// Cache key of a workload: mode, K, eps, N (in half-octaves) and the shape of its tree
+// (levels, per-mille of pair evaluations in the direct lists).
+std::string tune_key(const ncs_ctx* c) {
+  const ncs::TreeHost& t = c->tree;
+  const int64_t N = (int64_t)(c->centres.size() / 3);
+  const double share = (double)t.direct_pairs / std::max<double>(1.0, (double)(t.direct_pairs + t.p2l_pairs));
+  char buf[160];
+  std::snprintf(buf, sizeof buf, "m%d_K%d_e%.4g_N%d_L%d_d%d_g%.0e", c->pc.mode, c->pc.K, c->pc.eps,
+                (int)std::lround(2.0 * std::log2((double)N)), t.levels, (int)std::lround(1000.0 * share),
+                c->prm.grid_tol);
+  return buf;
+}
+
+bool tune_cache_lookup(const char* path, const std::string& key, ncs_tuning* t) {
+  FILE* f = std::fopen(path, "r");
+  if (!f) return false;
+  char line[512], k[256];
+  bool hit = false;
+  ncs_tuning v{};
+  while (std::fgets(line, sizeof line, f)) {
+    if (std::sscanf(line, "ncs-tune-v1 %255s %d %d %d %d %lf", k, &v.p2l_tile, &v.p2l_poly, &v.direct_poly,
+                    &v.item_patches, &v.l2p_weight) == 6 &&
+        key == k && tuning_valid(v)) {
+      *t = v;
+      hit = true;  // the last entry for a key wins
+    }
+  }
+  std::fclose(f);
+  return hit;
+}
+
+void tune_cache_store(const char* path, const std::string& key, const ncs_tuning& t) {
+  FILE* f = std::fopen(path, "a");
+  if (!f) throw Fail{NCS_E_INPUT, std::string("tune cache: cannot append to ") + path};
+  std::fprintf(f, "ncs-tune-v1 %s %d %d %d %d %.17g\n", key.c_str(), t.p2l_tile, t.p2l_poly, t.direct_poly,
+               t.item_patches, t.l2p_weight);
+  std::fclose(f);
+}
+
 }  // namespace
 
 extern "C" {
@@ -787,10 +856,7 @@ int ncs_tree_pairs(ncs_ctx* c, int64_t* count, int* target, int* source, int* le
   try {
     if (c->centres.empty()) throw Fail{NCS_E_STATE, "no patches: call ncs_set_patches first"};
     std::vector<int> t, s, l, k;
-    ncs::TreeOptions to;
-    to.grid_tol = c->prm.grid_tol;
-    to.eps = c->pc.eps;
-    ncs::tree_pairs(c->centres, c->pc, to, t, s, l, k);
+    ncs::tree_pairs(c->centres, c->pc, tree_options(c), t, s, l, k);
     if (target && source && level && kind) {
       if (*count < (int64_t)t.size()) throw Fail{NCS_E_INPUT, "pair buffers too small"};
       std::memcpy(target, t.data(), t.size() * sizeof(int));
@@ -1316,6 +1382,169 @@ int ncs_batch_solve(int B, const double* eps, const int* mode, const int64_t* N,
     for (int b = 0; b < B; ++b)
       if (status[b] != NCS_OK) return status[b];
   return NCS_OK;
+}
+
+int ncs_set_tuning(ncs_ctx* c, const ncs_tuning* t) {
+  if (!c || !t) return NCS_E_INPUT;
+  if (!tuning_valid(*t)) return finish(c, Fail{NCS_E_INPUT, "ncs_set_tuning: value out of range"});
+  if (c->device_ready) cudaSetDevice(c->device);
+  apply_tuning(c, *t);
+  return NCS_OK;
+}
+
+int ncs_get_tuning(const ncs_ctx* c, ncs_tuning* t) {
+  if (!c || !t) return NCS_E_INPUT;
+  *t = c->tune;
+  return NCS_OK;
+}
+
+int ncs_tune(ncs_ctx* c, int flags, const char* cache_path, ncs_tuning* out, double* report, int nrep) {
+  double* buf = nullptr;
+  cudaEvent_t ev[6] = {};
+  int rc = NCS_OK;
+  try {
+    if (!c) throw Fail{NCS_E_INPUT, "null context"};
+    if (flags < 1 || flags > 3) throw Fail{NCS_E_INPUT, "ncs_tune: flags must be 1, 2 or 3"};
+    check_ready(c);
+    if (!use_tree(c)) throw Fail{NCS_E_STATE, "ncs_tune: the context does not use the tree method"};
+    ensure_tree(c);
+    const auto t_start = std::chrono::steady_clock::now();
+    cudaStream_t s = c->stream;
+    double rep[6] = {0, 0, 0, 0, 0, 0};
+    const std::string key = tune_key(c);
+    ncs_tuning best = c->tune;
+    if (cache_path && tune_cache_lookup(cache_path, key, &best)) {
+      apply_tuning(c, best);
+      rep[5] = 1.0;
+    } else {
+      const int64_t n = c->d.N * c->d.K, nz = c->d.N * c->d.Kstar;
+      buf = dev_alloc<double>((size_t)(n + 2 * nz + 2));
+      double *x = buf, *zref = buf + n, *zt = buf + n + nz, *md = buf + n + 2 * nz;
+      {
+        // a fixed pseudo-random input (splitmix64 to [-1, 1))
+        std::vector<double> xh((size_t)n);
+        uint64_t st = 0x9e3779b97f4a7c15ull;
+        for (auto& v : xh) {
+          uint64_t z = (st += 0x9e3779b97f4a7c15ull);
+          z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+          z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+          z ^= z >> 31;
+          v = 2.0 * (double)(z >> 11) * (1.0 / 9007199254740992.0) - 1.0;
+        }
+        CU(cudaMemcpyAsync(x, xh.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
+        field(c, x, NCS_DF64, s);
+        CU(cudaMemcpyAsync(zref, c->d.z, nz * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        CU(cudaStreamSynchronize(s));
+      }
+      for (auto& e : ev) CU(cudaEventCreate(&e));
+      int trials = 0;
+      // FP32 field of x under the current configuration: min over reps of the P2L and
+      // direct-list stage times and of the whole field, and its error against zref
+      struct Meas {
+        double p2l, direct, total, err;
+      };
+      auto measure = [&](int reps) {
+        ensure_tree(c);
+        Meas m{1e300, 1e300, 1e300, 0.0};
+        for (int r = 0; r <= reps; ++r) {
+          CU(cudaEventRecord(ev[5], s));
+          outgoing(c, x, NCS_FP32, s);
+          CU(ncs::launch_tree_field(c->d, c->tdev, c->pc.mode, NCS_FP32, s, ev));
+          CU(cudaEventSynchronize(ev[4]));
+          ++trials;
+          if (r == 0) continue;  // warm-up
+          float a = 0, b = 0, t = 0;
+          CU(cudaEventElapsedTime(&a, ev[0], ev[1]));
+          CU(cudaEventElapsedTime(&b, ev[2], ev[3]));
+          CU(cudaEventElapsedTime(&t, ev[5], ev[4]));
+          m.p2l = std::min(m.p2l, (double)a);
+          m.direct = std::min(m.direct, (double)b);
+          m.total = std::min(m.total, (double)t);
+        }
+        CU(ncs::launch_maxabs_diff(nz, c->d.z, zref, md, s));
+        double h[2];
+        CU(cudaMemcpyAsync(h, md, sizeof h, cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        check_tc(c);
+        m.err = h[0] / std::max(h[1], 1e-300);
+        return m;
+      };
+      constexpr double kTol = 2e-5;  // the FP32 product's accuracy bar
+      constexpr int kReps = 3;
+      const ncs_tuning start = c->tune;
+      const Meas m0 = measure(kReps);
+      rep[0] = m0.total;
+      double best_total = m0.err <= kTol ? m0.total : 1e300;
+      double best_err = m0.err;
+      if (flags & 1) {
+        // P2L variants (the direct lists are timed as a separate stage of the same runs)
+        double bp = m0.err <= kTol ? m0.p2l : 1e300;
+        ncs_tuning bt = start;
+        for (int jt : {8, 16})
+          for (int poly : {0, 2, 4, 6}) {
+            ncs_tuning t = start;
+            t.p2l_tile = jt;
+            t.p2l_poly = poly;
+            if (!tuning_valid(t) || (jt == start.p2l_tile && poly == start.p2l_poly)) continue;
+            apply_tuning(c, t);
+            const Meas m = measure(kReps);
+            if (m.err <= kTol && m.p2l < bp) bp = m.p2l, bt = t;
+          }
+        double bd = m0.err <= kTol ? m0.direct : 1e300;
+        for (int poly : {0, 2, 4, 6}) {
+          ncs_tuning t = bt;
+          t.direct_poly = poly;
+          if (poly == start.direct_poly) continue;
+          apply_tuning(c, t);
+          const Meas m = measure(kReps);
+          if (m.err <= kTol && m.direct < bd) bd = m.direct, bt.direct_poly = poly;
+        }
+        apply_tuning(c, bt);
+        const Meas m = measure(kReps);
+        best = bt;
+        best_total = m.err <= kTol ? m.total : 1e300;
+        best_err = m.err;
+        if (!(m.err <= kTol)) {  // keep the starting configuration
+          best = start;
+          best_total = m0.total;
+          best_err = m0.err;
+        }
+        apply_tuning(c, best);
+      }
+      if (flags & 2) {
+        // work-item size and grid-or-direct weight: each candidate on its own tree
+        const ncs_tuning base = best;
+        for (int ip : {16, 32})
+          for (double w : {0.05, 0.1, 0.2}) {
+            ncs_tuning t = base;
+            t.item_patches = ip;
+            t.l2p_weight = w;
+            if (!tuning_valid(t) || (ip == base.item_patches && w == base.l2p_weight)) continue;
+            apply_tuning(c, t);
+            const Meas m = measure(kReps);
+            if (m.err <= kTol && m.total < best_total) best_total = m.total, best = t, best_err = m.err;
+          }
+        apply_tuning(c, best);
+      }
+      rep[1] = best_total;
+      rep[2] = trials;
+      rep[3] = best_err;
+      if (cache_path) tune_cache_store(cache_path, key, best);
+    }
+    rep[4] = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    if (out) *out = c->tune;
+    for (int i = 0; report && i < nrep && i < 6; ++i) report[i] = rep[i];
+  } catch (const Fail& f) {
+    rc = finish(c, f);
+  } catch (const std::bad_alloc&) {
+    rc = finish(c, Fail{NCS_E_OOM, "out of host memory"});
+  } catch (const std::exception& e) {
+    rc = finish(c, Fail{NCS_E_INPUT, e.what()});
+  }
+  for (auto& e : ev)
+    if (e) cudaEventDestroy(e);
+  if (buf) cudaFree(buf);
+  return rc;
 }
 
 int ncs_solve_stats(const ncs_ctx* c, double* out, int n) {

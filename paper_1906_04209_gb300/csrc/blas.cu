@@ -93,6 +93,34 @@ __global__ void nonfinite_kernel(int64_t n, const double* __restrict__ x, int* _
   if (bad) atomicOr(out, 1);
 }
 
+// Non-negative doubles order like their bit patterns, so atomicMax on the bits is a max.
+__global__ void maxabs_diff_kernel(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
+                                   unsigned long long* __restrict__ out) {
+  double d = 0.0, m = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    d = fmax(d, fabs(a[i] - b[i]));
+    m = fmax(m, fabs(b[i]));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    d = fmax(d, __shfl_down_sync(0xffffffffu, d, o));
+    m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    // a NaN difference is reported as +Inf (the largest bit pattern atomicMax keeps)
+    atomicMax(out, (unsigned long long)__double_as_longlong(d == d ? d : INFINITY));
+    atomicMax(out + 1, (unsigned long long)__double_as_longlong(m));
+  }
+}
+
+cudaError_t launch_maxabs_diff(int64_t n, const double* a, const double* b, double* out, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(out, 0, 2 * sizeof(double), s);
+  if (e != cudaSuccess) return e;
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 4);
+  count_launch(), maxabs_diff_kernel<<<(unsigned)std::max<int64_t>(1, blocks), 256, 0, s>>>(
+      n, a, b, reinterpret_cast<unsigned long long*>(out));
+  return cudaGetLastError();
+}
+
 cudaError_t launch_nonfinite_count(int64_t n, const double* x, int* out, cudaStream_t s) {
   const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 4);
   count_launch(), nonfinite_kernel<<<(unsigned)blocks, 256, 0, s>>>(n, x, out);

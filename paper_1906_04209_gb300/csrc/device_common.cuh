@@ -259,9 +259,11 @@ __device__ __forceinline__ void stage_pad_x2(float4* S, int ns) {
 #endif
 
 // part[t] = sum over the ns staged sources (paired layout, padded to even) of G(a_t, s)
-// rho_s for the NT half-scaled targets: source pairs in groups of 8, the first
-// NCS_PAIR_X2_POLY of a group's 8 NT chains (scaled to NT) on lg2_poly.
-template <int MODE, int NT>
+// rho_s for the NT half-scaled targets: source pairs in groups of 8, the first POLY16
+// of every 16 two-pair chains (scaled to a group's 8 NT chains) on lg2_poly. POLY16 is
+// a run-time choice of the kernels' launch configuration (set by ncs_tune), with
+// NCS_PAIR_X2_POLY as the default.
+template <int MODE, int NT, int POLY16 = NCS_PAIR_X2_POLY>
 __device__ __forceinline__ void pair_loop32x2(const float4* __restrict__ S, int ns, const float* ax, const float* ay,
                                               const float* az, float* part) {
   const PairX2Consts k;
@@ -274,7 +276,7 @@ __device__ __forceinline__ void pair_loop32x2(const float4* __restrict__ S, int 
     AZ[t] = x2_pack(az[t], az[t]);
     P[t] = x2_pack(0.0f, 0.0f);
   }
-  constexpr int kPoly = NCS_PAIR_X2_POLY * NT / 2;  // poly chains per group of 8 * NT
+  constexpr int kPoly = POLY16 * NT / 2;  // poly chains per group of 8 * NT
   const int np = (ns + 1) >> 1;
   int s = 0;
   for (; s + 8 <= np; s += 8) {

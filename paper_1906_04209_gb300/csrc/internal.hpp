@@ -80,6 +80,8 @@ cudaError_t launch_sub_combination(int64_t n, int k, const double* V, int64_t ld
 cudaError_t launch_scale_copy(int64_t n, const double* w, double a, double* v, cudaStream_t s);
 cudaError_t launch_axpby(int64_t n, double a, const double* x, double b, double* y, cudaStream_t s);
 cudaError_t launch_nonfinite_count(int64_t n, const double* x, int* out, cudaStream_t s);
+// out[0] = max |a_i - b_i|, out[1] = max |b_i| over n entries (out: 2 device doubles, zeroed here)
+cudaError_t launch_maxabs_diff(int64_t n, const double* a, const double* b, double* out, cudaStream_t s);
 cudaError_t launch_periodic_dot(int64_t n, int K, const double* x, const double* I, double* partial,
                                 double* out, cudaStream_t s);
 constexpr int kDotChunks = 64;
@@ -152,6 +154,7 @@ struct ncs_ctx {
   // one captured Arnoldi step (product + orthogonalisation + state copy) per precision
   cudaGraphExec_t step_graph[4] = {nullptr, nullptr, nullptr, nullptr};
   long long step_graph_kernels[4] = {0, 0, 0, 0};
+  ncs_tuning tune{16, 4, 4, 16, 0.1};  // tree product launch configuration (ncs_tune)
   bool graphs_off = false;      // capture failed once: steps are launched directly
   std::string graph_note;       // why
   double solve_stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // see ncs_solve_stats

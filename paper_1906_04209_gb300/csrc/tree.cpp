@@ -348,7 +348,7 @@ void tree_build(const std::vector<double>& centres, const Precomputed& pc, const
     t.shapes.push_back(s);
     return (int)t.shapes.size() - 1;
   };
-  const int CH = 16;  // source patches per P2L work item
+  const int CH = std::max(1, opt.item_patches);  // source patches per P2L work item
   // Bounding circles (Section 7.3) of every group: smallest enclosing circle of the
   // members' centres in the gnomonic plane at their mean direction, radius + eps; then,
   // bottom-up, each radius grows until the disk contains the disks of its children that
@@ -415,7 +415,7 @@ void tree_build(const std::vector<double>& centres, const Precomputed& pc, const
         for (size_t s = 0; s < sd.size(); s += CH)
           psum_grid += (double)(std::min(sd.size(), s + CH) - s) * rep_p(pc, select_rep(pc, sd[s].first - R));
         for (size_t q = 0; q < sd.size(); ++q) psum_direct += rep_p(pc, select_rep(pc, sd[q].first - R));
-        const double cost_grid = gs.q() * psum_grid + 0.1 * (double)mem.size() * pc.Kstar * gs.q();
+        const double cost_grid = gs.q() * psum_grid + opt.l2p_weight * (double)mem.size() * pc.Kstar * gs.q();
         const double cost_direct = (double)mem.size() * pc.Kstar * psum_direct;
         use_grid = cost_grid < cost_direct;
       }

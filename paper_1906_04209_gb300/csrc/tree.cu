@@ -59,8 +59,10 @@ constexpr int P2L_JT = NCS_P2L_JT;
 // memory (43 KB at p = 169) at the FP32 kernel's, and its blocks per SM with it
 constexpr int P2L_DF_JT = 8;
 
-// One block per work item (grid group g, a slice of its interaction-list patches).
-template <typename R, int MODE>
+// One block per work item (grid group g, a slice of its interaction-list patches). JT
+// source patches per shared-memory tile, POLY of every 16 packed pair chains with the
+// logarithm on the FMA pipe (FP32 only): both chosen at run time (KernelConfig).
+template <typename R, int MODE, int JT = P2L_JT, int POLY = NCS_PAIR_X2_POLY>
 __global__ void __launch_bounds__(P2L_THREADS) p2l_kernel(
     const int* __restrict__ witem_group, const int* __restrict__ witem_rep, const int* __restrict__ rep_p,
     const int* __restrict__ rep_off, int pt, const int64_t* __restrict__ witem_lo, const int64_t* __restrict__ witem_hi,
@@ -70,7 +72,7 @@ __global__ void __launch_bounds__(P2L_THREADS) p2l_kernel(
     const R* __restrict__ rho, double* __restrict__ grid) {
   using V4 = typename V4T<R>::type;
   extern __shared__ unsigned char p2l_smem[];
-  __shared__ double D[P2L_JT][3];
+  __shared__ double D[JT][3];
   const int item = blockIdx.x;
   const int g = witem_group[item];
   const int rk = witem_rep[item];
@@ -97,8 +99,8 @@ __global__ void __launch_bounds__(P2L_THREADS) p2l_kernel(
       }
       acc[t] = 0.0;
     }
-    for (int64_t s0 = lo; s0 < hi; s0 += P2L_JT) {
-      const int nj = (int)min((int64_t)P2L_JT, hi - s0);
+    for (int64_t s0 = lo; s0 < hi; s0 += JT) {
+      const int nj = (int)min((int64_t)JT, hi - s0);
       __syncthreads();
       if (threadIdx.x < nj * 3) {
         const int jj = threadIdx.x / 3, c = threadIdx.x - 3 * jj;
@@ -139,9 +141,9 @@ __global__ void __launch_bounds__(P2L_THREADS) p2l_kernel(
       if constexpr (sizeof(R) == 4) {
         if constexpr (NCS_PAIR_X2 != 0) {
           if (nact == P2L_NT)
-            pair_loop32x2<MODE, P2L_NT>(S, ns, ax, ay, az, part);
+            pair_loop32x2<MODE, P2L_NT, POLY>(S, ns, ax, ay, az, part);
           else if (nact == 1)
-            pair_loop32x2<MODE, 1>(S, ns, ax, ay, az, part);
+            pair_loop32x2<MODE, 1, POLY>(S, ns, ax, ay, az, part);
         } else {
           if (nact == P2L_NT)
             pair_loop32<MODE, P2L_NT>(S, ns, ax, ay, az, part);
@@ -245,7 +247,7 @@ constexpr int DT_JT = 8;
 // count within the tile's shared memory (an odd count only occurs in a partial tile)
 static_assert(P2L_JT % 2 == 0 && DT_JT % 2 == 0, "tile source counts must be even");
 
-template <typename R, int MODE>
+template <typename R, int MODE, int POLY = NCS_PAIR_X2_POLY>
 __global__ void __launch_bounds__(DT_THREADS) direct_list_kernel(
     int pt, int Kstar, int pmax, const int* __restrict__ rep_p, const int* __restrict__ rep_off,
     const int64_t* __restrict__ pd_off, const int* __restrict__ pd, const int* __restrict__ pdk,
@@ -321,7 +323,7 @@ __global__ void __launch_bounds__(DT_THREADS) direct_list_kernel(
     for (int t = 0; t < DT_NT; ++t) part[t] = 0;
     if constexpr (sizeof(R) == 4) {
       if constexpr (NCS_PAIR_X2 != 0)
-        pair_loop32x2<MODE, DT_NT>(S, ns, ax, ay, az, part);
+        pair_loop32x2<MODE, DT_NT, POLY>(S, ns, ax, ay, az, part);
       else
         pair_loop32<MODE, DT_NT>(S, ns, ax, ay, az, part);
     } else {
@@ -1090,6 +1092,43 @@ static cudaError_t downward(const TreeDevice& t, cudaStream_t s) {
   return cudaSuccess;
 }
 
+// The FP32 pair kernels' run-time variants (KernelConfig): source patches per P2L tile
+// and the share of logarithms taken on the FMA pipe. Every variant has the same
+// parameters, so one pointer type serves them all.
+template <int MODE, int JT>
+static auto p2l32_variant(int poly) -> decltype(&p2l_kernel<float, MODE, JT, 0>) {
+  switch (poly) {
+    case 0: return &p2l_kernel<float, MODE, JT, 0>;
+    case 2: return &p2l_kernel<float, MODE, JT, 2>;
+    case 4: return &p2l_kernel<float, MODE, JT, 4>;
+    case 6: return &p2l_kernel<float, MODE, JT, 6>;
+    default: return nullptr;
+  }
+}
+
+template <int MODE>
+static auto p2l32_variant(int jt, int poly) -> decltype(&p2l_kernel<float, MODE, 16, 0>) {
+  if (jt == 8) return p2l32_variant<MODE, 8>(poly);
+  if (jt == 16) return p2l32_variant<MODE, 16>(poly);
+  return nullptr;
+}
+
+template <int MODE>
+static auto direct32_variant(int poly) -> decltype(&direct_list_kernel<float, MODE, 0>) {
+  switch (poly) {
+    case 0: return &direct_list_kernel<float, MODE, 0>;
+    case 2: return &direct_list_kernel<float, MODE, 2>;
+    case 4: return &direct_list_kernel<float, MODE, 4>;
+    case 6: return &direct_list_kernel<float, MODE, 6>;
+    default: return nullptr;
+  }
+}
+
+bool kernel_config_valid(const KernelConfig& k) {
+  const auto poly_ok = [](int p) { return p == 0 || p == 2 || p == 4 || p == 6; };
+  return (k.p2l_tile == 8 || k.p2l_tile == 16) && poly_ok(k.p2l_poly) && poly_ok(k.direct_poly);
+}
+
 template <typename R, int MODE>
 static cudaError_t tree_field_impl(const DeviceData& dd, const TreeDevice& t, cudaStream_t s, cudaEvent_t* ev) {
   const R* soff = (sizeof(R) == 8) ? (const R*)dd.soff64 : (const R*)dd.soff32;
@@ -1101,9 +1140,16 @@ static cudaError_t tree_field_impl(const DeviceData& dd, const TreeDevice& t, cu
   if (t.nitems > 0) {
     e = cudaMemsetAsync(t.grid, 0, t.ngrid * sizeof(double), s);
     if (e != cudaSuccess) return e;
-    const size_t smem = (size_t)P2L_JT * dd.pmax * sizeof(V4);
-    if ((e = allow_smem(p2l_kernel<R, MODE>, smem)) != cudaSuccess) return e;
-    count_launch(), p2l_kernel<R, MODE><<<t.nitems, P2L_THREADS, smem, s>>>(t.witem_group, t.witem_rep, dd.rep_p, dd.rep_off, dd.p,
+    auto kern = &p2l_kernel<R, MODE>;
+    int jt = P2L_JT;
+    if constexpr (std::is_same<R, float>::value) {
+      kern = p2l32_variant<MODE>(t.cfg.p2l_tile, t.cfg.p2l_poly);
+      jt = t.cfg.p2l_tile;
+      if (!kern) return cudaErrorInvalidValue;
+    }
+    const size_t smem = (size_t)jt * dd.pmax * sizeof(V4);
+    if ((e = allow_smem(kern, smem)) != cudaSuccess) return e;
+    count_launch(), kern<<<t.nitems, P2L_THREADS, smem, s>>>(t.witem_group, t.witem_rep, dd.rep_p, dd.rep_off, dd.p,
                                                              t.witem_lo, t.witem_hi, t.isrc, t.gcen, t.gshape, t.goff,
                                                              t.shape_nr, t.shape_nth, gpos, dd.centres, soff, rho,
                                                              t.grid);
@@ -1115,10 +1161,15 @@ static cudaError_t tree_field_impl(const DeviceData& dd, const TreeDevice& t, cu
   }
   if (ev) cudaEventRecord(ev[2], s);
   {
+    auto kern = &direct_list_kernel<R, MODE>;
+    if constexpr (std::is_same<R, float>::value) {
+      kern = direct32_variant<MODE>(t.cfg.direct_poly);
+      if (!kern) return cudaErrorInvalidValue;
+    }
     const size_t smem = (size_t)DT_JT * dd.pmax * sizeof(V4);
-    if ((e = allow_smem(direct_list_kernel<R, MODE>, smem)) != cudaSuccess) return e;
+    if ((e = allow_smem(kern, smem)) != cudaSuccess) return e;
     dim3 grid((unsigned)dd.N, (unsigned)((dd.Kstar + DT_THREADS * DT_NT - 1) / (DT_THREADS * DT_NT)));
-    count_launch(), direct_list_kernel<R, MODE><<<grid, DT_THREADS, smem, s>>>(dd.p, dd.Kstar, dd.pmax, dd.rep_p, dd.rep_off, t.pd_off, t.pd,
+    count_launch(), kern<<<grid, DT_THREADS, smem, s>>>(dd.p, dd.Kstar, dd.pmax, dd.rep_p, dd.rep_off, t.pd_off, t.pd,
                                                                 t.pdk, dd.centres, dd.zloc, soff, rho, dd.z);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }

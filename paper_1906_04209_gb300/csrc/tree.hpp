@@ -17,7 +17,21 @@ struct TreeOptions {
   double grid_tol = 1e-8;  // incoming-grid tolerance
   int max_level = 24;
   int grid_min_members = 2;  // groups with fewer patches evaluate directly at the Zernike nodes
+  int item_patches = 16;     // interaction-list source patches per P2L work item
+  double l2p_weight = 0.1;   // cost of one L2P node-grid product in kernel evaluations, used
+                             // when a group chooses between a grid and direct evaluation
 };
+
+// Launch configuration of the FP32 pair kernels of the tree product (results differ only
+// by the order of FP32 sums and by the logarithm's approximation, both within the FP32
+// product's accuracy). Chosen per workload by ncs_tune.
+struct KernelConfig {
+  int p2l_tile = 16;    // source patches per shared-memory tile of a P2L work item: 8 or 16
+  int p2l_poly = 4;     // of every 16 packed pair chains, how many take lg2 on the FMA pipe:
+                        // 0, 2, 4 or 6 (the rest on the MUFU unit)
+  int direct_poly = 4;  // the same for the direct lists
+};
+bool kernel_config_valid(const KernelConfig& k);
 
 // One incoming-grid shape: n_r parity-restricted Chebyshev radii x n_theta angles.
 struct GridShape {
@@ -89,6 +103,7 @@ struct TreeDevice {
   double* grid = nullptr;        // ngrid values (FP64 accumulation for both precisions)
   double* coef = nullptr;        // ngrid coefficients
   int max_q = 0, max_nr = 0, max_nth = 0;
+  KernelConfig cfg;              // FP32 pair-kernel variants
 };
 
 void tree_build(const std::vector<double>& centres, const Precomputed& pc, const TreeOptions& opt, TreeHost& t);

@@ -31,7 +31,8 @@ EXPORTS = ["ncs_default_params", "ncs_create", "ncs_create_from_operator", "ncs_
            "ncs_matvec_dev", "ncs_field_dev", "ncs_solve", "ncs_eval", "ncs_last_error", "ncs_destroy",
            "ncs_tree_pairs", "ncs_tree_stats", "ncs_profile_matvec", "ncs_create_from_operators", "ncs_get_reps",
            "ncs_tc_gemm_f32", "ncs_batch_solve", "ncs_block_dots", "ncs_block_dots_noalloc",
-           "ncs_launch_count", "ncs_get_rep", "ncs_set_precision", "ncs_patch_residual", "ncs_solve_stats"]
+           "ncs_launch_count", "ncs_get_rep", "ncs_set_precision", "ncs_patch_residual", "ncs_solve_stats", "ncs_tune", "ncs_set_tuning",
+           "ncs_get_tuning"]
 
 
 class ncs_params(ctypes.Structure):
@@ -41,6 +42,14 @@ class ncs_params(ctypes.Structure):
                 ("verbose", ctypes.c_int), ("mixed_residual", ctypes.c_int), ("tensor_cores", ctypes.c_int),
                 ("residual_update", ctypes.c_int), ("id_ladder_max", ctypes.c_double),
                 ("device_precompute", ctypes.c_int), ("cuda_graphs", ctypes.c_int)]
+
+
+class ncs_tuning(ctypes.Structure):
+    _fields_ = [("p2l_tile", ctypes.c_int), ("p2l_poly", ctypes.c_int), ("direct_poly", ctypes.c_int),
+                ("item_patches", ctypes.c_int), ("l2p_weight", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class NcsError(RuntimeError):
@@ -99,6 +108,9 @@ def load(path: str = LIB_PATH):
     lib.ncs_get_rep.argtypes = [VP, ctypes.c_int, D, D, D]
     lib.ncs_set_precision.argtypes = [VP, ctypes.c_int]
     lib.ncs_solve_stats.argtypes = [VP, D, ctypes.c_int]
+    lib.ncs_tune.argtypes = [VP, ctypes.c_int, ctypes.c_char_p, ctypes.POINTER(ncs_tuning), D, ctypes.c_int]
+    lib.ncs_set_tuning.argtypes = [VP, ctypes.POINTER(ncs_tuning)]
+    lib.ncs_get_tuning.argtypes = [VP, ctypes.POINTER(ncs_tuning)]
     lib.ncs_launch_count.argtypes = []
     lib.ncs_launch_count.restype = ctypes.c_int64
     lib.ncs_destroy.argtypes = [VP]
@@ -329,6 +341,28 @@ class Context:
         if rc != NCS_OK and not (allow_noconv and rc == NCS_E_NOCONV):
             self._check(rc)
         return dict(fhat=fhat, scalar=sc.value, Isigma=Is.value, iterations=it.value, relres=rr.value, rc=rc)
+
+    def tune(self, flags=3, cache_path=None):
+        """Picks the tree product's launch configuration for this layout (see ncs_tune).
+        Returns (configuration dict, report dict)."""
+        t = ncs_tuning()
+        rep = np.zeros(6)
+        cp = None if cache_path is None else os.fsencode(cache_path)
+        self._check(load().ncs_tune(self.h, flags, cp, ctypes.byref(t), _ptr(rep), 6))
+        keys = ["default_ms", "tuned_ms", "trial_products", "error", "seconds", "from_cache"]
+        return t.as_dict(), dict(zip(keys, rep.tolist()))
+
+    def set_tuning(self, **kw):
+        t = ncs_tuning()
+        self._check(load().ncs_get_tuning(self.h, ctypes.byref(t)))
+        for k, v in kw.items():
+            setattr(t, k, v)
+        self._check(load().ncs_set_tuning(self.h, ctypes.byref(t)))
+
+    def get_tuning(self) -> dict:
+        t = ncs_tuning()
+        self._check(load().ncs_get_tuning(self.h, ctypes.byref(t)))
+        return t.as_dict()
 
     def solve_stats(self) -> dict:
         """Counters of the last solve (see ncs_solve_stats)."""

@@ -22,9 +22,10 @@ def _cuda(libncs):
     torch.cuda.set_device(0)
 
 
-def _ctx(pre, T_scale=1.0, **kw):
+def _ctx(pre, T_max=None, **kw):
+    T = pre.idr.T if T_max is None else (pre.idr.T / np.abs(pre.idr.T).max()) * T_max
     return ncs.Context(pre.eps, pre.mode, pre.K,
-                       operator=(pre.idr.T * T_scale, pre.idr.t_skel, pre.idr.th_skel, pre.op.I), **kw)
+                       operator=(T, pre.idr.t_skel, pre.idr.th_skel, pre.op.I), **kw)
 
 
 @pytest.mark.parametrize("mode", [EXTERIOR, INTERIOR])
@@ -53,7 +54,9 @@ def test_graph_step_equals_direct_launches(small_pre, mode):
 
 def test_graph_step_tree_mixed(small_pre):
     """The mixed solve on the tree replays its FP32 step graph across refinement steps
-    and gives the same answer as direct launches; its reported residual is recomputed."""
+    and gives the same answer as direct launches (to rounding: the P2L kernel adds its
+    partial sums into the grids atomically, so two runs differ in the last bits); its
+    reported residual is recomputed."""
     eps = 0.01
     pre = small_pre(INTERIOR, eps=eps)
     N = 2500
@@ -67,7 +70,8 @@ def test_graph_step_tree_mixed(small_pre):
         assert r["relres"] <= 1e-9 and st["recomputed"] == 1.0
         assert st["refinement_steps"] >= 1
         res[graphs] = (r, st)
-    assert np.array_equal(res[0][0]["fhat"], res[1][0]["fhat"])
+    f0, f1 = res[0][0]["fhat"], res[1][0]["fhat"]
+    assert np.abs(f0 - f1).max() <= 1e-9 * np.abs(f0).max()
     assert res[1][1]["graph_replays"] > 0 and res[0][1]["graph_replays"] == 0
 
 
@@ -107,7 +111,8 @@ def test_overflowing_operator_returns_numeric(small_pre):
     pre = small_pre(INTERIOR)
     N = 12
     c = L.uniform(N, pre.eps, L.rng(97, 1))
-    ctx = _ctx(pre, T_scale=1e307 / np.abs(pre.idr.T).max(), method=ncs.METHOD_DIRECT)
+    assert np.all(np.isfinite((pre.idr.T / np.abs(pre.idr.T).max()) * 1e307))
+    ctx = _ctx(pre, T_max=1e307, method=ncs.METHOD_DIRECT)
     ctx.set_patches(c)
     with pytest.raises(ncs.NcsError) as e:
         ctx.solve(tol=1e-10, precision=ncs.FP64)
