@@ -40,12 +40,9 @@ FLOPS_PER_PAIR = 20
 
 # DRAM bytes per pair of the FP32 P2L kernel: dram__bytes_read.sum + dram__bytes_write.sum
 # of one launch (170.2 + 15.5 MB) over its 1.5108e10 pairs, ncu capture of the packed pair
-# loop at N = 2e4 of the same layout family; the reads scale with the work items.
-P2L_BYTES_PER_PAIR = 185.7e6 / 1.5108e10
-# MUFU operations per FP32 pair in the P2L kernel: rsqrt always, log2 on the MUFU unit for
-# 12 pairs in 16 (the other 4 take a polynomial log2 on the FMA pipe; the packed pair
-# loop's default share)
-MUFU_PER_PAIR = 2.0 - 4.0 / 16.0
+# loop at N = 2e4 of the same layout family; the reads scale with the work items. Valid for
+# the launch configuration that was captured (reported as null for any other).
+P2L_CAPTURE = {"p2l_tile": 16, "p2l_poly": 4, "bytes_per_pair": 185.7e6 / 1.5108e10}
 
 
 _T0 = time.time()
@@ -155,6 +152,13 @@ def run_ours(args):
     ctx = ncs.Context(eps, mode, K, method=ncs.METHOD_TREE, grid_tol=args.grid_tol, tensor_cores=args.tensor_cores)
     ctx.set_patches(centres)
     setup_s = time.time() - t0
+    tuning = None
+    if args.tune:
+        _progress("tune")
+        cfg, rep = ctx.tune(flags=3)
+        tuning = {"config": cfg, "default_ms": round(rep["default_ms"], 3), "tuned_ms": round(rep["tuned_ms"], 3),
+                  "trial_products": int(rep["trial_products"]), "error_vs_df64": rep["error"],
+                  "seconds": round(rep["seconds"], 2)}
     info, tstats = ctx.info(), ctx.tree_stats()
     n = N * K
     g = torch.Generator(device="cuda").manual_seed(1234 + rank)
@@ -248,10 +252,17 @@ def run_ours(args):
 
     peaks, src = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    # ALU roofline of the pair kernel: per pair the FP32 path issues MUFU_PER_PAIR MUFU
-    # ops (rsqrt, and log2 for 12 pairs in 16); 152 SMs x 16 MUFU/clk cap it at
-    # 16 / MUFU_PER_PAIR pairs/clk/SM.
-    pair_peak = 152 * (16.0 / MUFU_PER_PAIR) * sm_max * 1e6 if prec == ncs.FP32 else None
+    # ALU roofline of the pair kernel: per pair the FP32 path issues mufu_per_pair MUFU
+    # ops (rsqrt, and log2 for the pairs whose logarithm is not taken on the FMA pipe);
+    # 152 SMs x 16 MUFU/clk cap it at 16 / mufu_per_pair pairs/clk/SM. Two fixed bounds are
+    # reported beside it: the joint MUFU + FMA-pipe bound over every share s of polynomial
+    # logarithms (9 FP32 operations per pair plus 11 per polynomial log2 on 128 FMA lanes:
+    # 16 / (2 - s) = 128 / (9 + 11 s) at s = 112/304, 9.80 pairs/clk/SM), and the FP32 pipe
+    # at the nominal 20 flops per pair (128 lanes x 2 flops per clock).
+    tuned_cfg = ctx.get_tuning()
+    poly = tuned_cfg["p2l_poly"]
+    mufu_per_pair = 2.0 - poly / 16.0
+    pair_peak = 152 * (16.0 / mufu_per_pair) * sm_max * 1e6 if prec == ncs.FP32 else None
     p2l_pairs = tstats["p2l_pairs"]
     achieved_pairs = p2l_pairs / (p2l_avg / 1000.0)
     roof = {
@@ -264,12 +275,18 @@ def run_ours(args):
         # DRAM bytes per launch: an ncu capture of this kernel on the N = 2e4 layout of the
         # same family measured 156.0 MB for 1.5108e10 pairs; the P2L reads scale with its
         # work items, so it is scaled by the pair ratio (null for other precisions)
-        "traffic": round(P2L_BYTES_PER_PAIR * p2l_pairs) if prec == ncs.FP32 else None,
+        "traffic": (round(P2L_CAPTURE["bytes_per_pair"] * p2l_pairs)
+                    if prec == ncs.FP32 and all(tuned_cfg[k] == P2L_CAPTURE[k] for k in ("p2l_tile", "p2l_poly"))
+                    else None),
         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum at N=2e4, scaled by pairs",
         "pairs_per_launch": p2l_pairs,
         "ms_per_launch": round(p2l_avg, 3),
         "peak_source": "derived: 152 SMs x 16 MUFU/clk / %g MUFU per pair x %g MHz (%s clocks)" % (
-            MUFU_PER_PAIR, sm_max, src),
+            mufu_per_pair, sm_max, src),
+        "frac_joint_mufu_fma": (round(achieved_pairs / (152 * (16.0 / (2.0 - 112.0 / 304.0)) * sm_max * 1e6), 4)
+                                if prec == ncs.FP32 else None),
+        "frac_fp32_pipe": (round(achieved_pairs * FLOPS_PER_PAIR / (152 * 256 * sm_max * 1e6), 4)
+                           if prec == ncs.FP32 else None),
     }
     cpu = cpu_baseline(args, centres, eps, mode, K) if (rank == 0 and args.cpu_baseline) else None
     line = {
@@ -293,6 +310,7 @@ def run_ours(args):
         "df64_matvecs_per_s": round(df64, 4) if df64 else None,
         "pairs_per_step": tstats["p2l_pairs"] + tstats["direct_pairs"],
         "pair_rate_per_s": round((tstats["p2l_pairs"] + tstats["direct_pairs"]) * 1000.0 / ms_step, 1),
+        "tuning": tuning,
         "solve": solve,
         "batch": batch,
     }
@@ -344,6 +362,18 @@ def solve_legs(args, ctx, N, K, sp):
         if name != ref:
             out[name]["density_err_vs_" + ref] = float(np.abs(fh[name] - fr).max() / np.abs(fr).max())
             out[name]["mu_relerr_vs_" + ref] = abs(out[name]["mu"] - out[ref]["mu"]) / abs(out[ref]["mu"])
+    # every solution against a tight FP64-accurate one (float-float products to 1e-11,
+    # untimed): two iterates that each meet 1e-8 differ by up to cond(A) x 1e-8, so the
+    # error of each against the tight solution shows what the tolerance, not the precision,
+    # leaves
+    _progress("tight reference solve")
+    rt = ctx.solve(tol=args.solve_tol * 1e-3, precision=ncs.DF64, want_fhat=True, allow_noconv=True)
+    ft = rt["fhat"]
+    out["tight_reference"] = {"precision": "df64", "tol": args.solve_tol * 1e-3, "relres": rt["relres"],
+                              "iterations": rt["iterations"], "mu": rt["scalar"]}
+    for name in fh:
+        out[name]["density_err_vs_tight"] = float(np.abs(fh[name] - ft).max() / np.abs(ft).max())
+        out[name]["mu_relerr_vs_tight"] = abs(out[name]["mu"] - rt["scalar"]) / abs(rt["scalar"])
     if "fp64" in out:
         out["speedup_mixed_over_fp64"] = round(out["fp64"]["seconds"] / out["mixed"]["seconds"], 2)
         out["speedup_df64_over_fp64"] = round(out["fp64"]["seconds"] / out["df64"]["seconds"], 2)
@@ -442,6 +472,7 @@ def main():
     ap.add_argument("--no-solve", dest="solve", action="store_false")
     ap.add_argument("--solve-tol", type=float, default=1e-8)
     ap.add_argument("--no-batch", dest="batch", action="store_false")
+    ap.add_argument("--no-tune", dest="tune", action="store_false")
     ap.add_argument("--batch-size", type=int, default=256)
     # a smaller layout of the same family (profiler captures only; the line names its N)
     ap.add_argument("--patches", type=int, default=None)

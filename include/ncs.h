@@ -104,7 +104,10 @@ typedef struct ncs_params {
   int cuda_graphs;     /* 1 (default): ncs_solve captures one GMRES step (the product, the
                           orthogonalisation and the Givens update, all reading the step
                           index from device memory) as a CUDA graph on its first use and
-                          replays it; 0: the same kernels launched one by one */
+                          replays it; 0: the same kernels launched one by one. While a
+                          capture runs, no other host thread may synchronise the whole
+                          device (cudaDeviceSynchronize, or calls that imply it): with
+                          contexts driven from several threads set 0 (ncs_batch_solve does) */
 } ncs_params;
 
 /* Fills *p with the defaults listed above. */
@@ -346,13 +349,20 @@ int ncs_get_tuning(const ncs_ctx* ctx, ncs_tuning* t);
 int ncs_solve_stats(const ncs_ctx* ctx, double* out, int n);
 
 /*
- * Single-layer potential at M off-patch targets (Section 2, eqs. urep and
- * intBVPansatz, off-surface Green's functions eqs. Gextoffsurface /
- * Gintoffsurface): u(x) = sum_j sum_m G(x, s_jm) rho_jm with rho_j = T fhat_j.
- * targets: M x 3 host (|x| >= 1 exterior, |x| <= 1 interior; each at least 2 eps
- * in arclength of its radial projection from every patch centre); fhat: N*K host.
- * out (M): exterior ubar = 1 - u; interior vbar = (v - 1)/(3D) + (1 - |x|^2)/6 with
- * D = -I_sigma (eq. vtilde). Errors: NCS_E_INPUT for targets too close.
+ * Single-layer potential at M targets off the patches (Section 2, eqs. urep and
+ * intBVPansatz, off-surface Green's functions eqs. Gextoffsurface / Gintoffsurface):
+ * u(x) = sum_j S sigma_j(x). A patch whose centre lies farther than 2.5 eps (geodesic, from
+ * the target's radial projection) is summed from its skeletons, rho_j = T fhat_j; a nearer
+ * patch is integrated directly against its density sigma_j = sum_k fhat_jk b_k (the
+ * one-patch solution, Section 8) with radial and angular rules graded toward the target
+ * (FP64 on the device), which serves targets close to the sphere such as the paper's maps
+ * at |x| = 1 - eps/5 (Section 9.2). targets: M x 3 host (|x| >= 1 exterior, |x| <= 1
+ * interior); fhat: N*K host. out (M): exterior ubar = 1 - u; interior
+ * vbar = (v - 1)/(3D) + (1 - |x|^2)/6 with D = -I_sigma (eq. vtilde).
+ * Errors: NCS_E_INPUT (a target on the sphere inside a patch, where u is the boundary data;
+ * targets within 2.5 eps of a patch on a context made from an operator, which has no
+ * one-patch data; a near target with Zernike degree M > 31; a target so close that its
+ * radial rule would exceed 2048 nodes), NCS_E_STATE, NCS_E_CUDA.
  */
 int ncs_eval(ncs_ctx* ctx, int64_t M, const double* targets, const double* fhat, double* out);
 

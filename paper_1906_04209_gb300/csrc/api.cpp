@@ -133,6 +133,9 @@ void free_all(ncs_ctx* c) {
   dev_free(d.Tpack);
   dev_free(d.Ppack);
   dev_free(d.tc_err);
+  dev_free(c->near_d);
+  dev_free(c->near_i);
+  c->near_ready = false;
   if (c->stream) cudaStreamDestroy(c->stream);
   c->stream = nullptr;
 }
@@ -179,9 +182,11 @@ void upload_operator(ncs_ctx* c) {
     float* P32d = dev_upload(P32);
     d.Tpack = dev_alloc<uint32_t>((size_t)ncs::tc_pack_words(pt, pc.K, ncs::tc_block_cols(pt)));
     d.Ppack = dev_alloc<uint32_t>((size_t)ncs::tc_pack_words(pc.K, pc.Kstar, ncs::tc_block_cols(pc.K)));
-    CU(ncs::launch_tc_pack_b(T32d, pt, pc.K, d.Tpack, 0));
-    CU(ncs::launch_tc_pack_b(P32d, pc.K, pc.Kstar, d.Ppack, 0));
-    CU(cudaDeviceSynchronize());
+    // on the context's stream: a device-wide synchronisation here would fail while another
+    // host thread captures a CUDA graph (which a batch of contexts can do concurrently)
+    CU(ncs::launch_tc_pack_b(T32d, pt, pc.K, d.Tpack, c->stream));
+    CU(ncs::launch_tc_pack_b(P32d, pc.K, pc.Kstar, d.Ppack, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
     dev_free(T32d);
     dev_free(P32d);
   }
@@ -1129,41 +1134,171 @@ int ncs_solve(ncs_ctx* c, double tol, int precision, double* fhat, double* scala
   }
 }
 
+// Device copies of the one-patch data that the near-patch quadrature needs (uploaded at
+// the first evaluation with a target near a patch).
+void ensure_near_data(ncs_ctx* c) {
+  if (c->near_ready) return;
+  const ncs::Precomputed& pc = c->pc;
+  const int npan = c->prm.npan, nord = c->prm.nord, nrad = npan * nord;
+  if ((int)pc.trad.size() != nrad) throw Fail{NCS_E_STATE, "near-patch evaluation: no one-patch data"};
+  const double eps = pc.eps;
+  std::vector<double> edges(npan + 1);
+  edges[0] = 0.0;
+  for (int j = 1; j < npan; ++j) edges[j] = (1.0 - std::ldexp(1.0, -j)) * eps;
+  edges[npan] = eps;
+  std::vector<double> xn(nrad), bw(nrad), gap(nrad);
+  for (int p = 0; p < npan; ++p) {
+    const double mid = 0.5 * (edges[p] + edges[p + 1]), half = 0.5 * (edges[p + 1] - edges[p]);
+    for (int l = 0; l < nord; ++l) xn[p * nord + l] = (pc.trad[p * nord + l] - mid) / half;
+    for (int l = 0; l < nord; ++l) {
+      double prod = 1.0;
+      for (int m = 0; m < nord; ++m)
+        if (m != l) prod *= xn[p * nord + l] - xn[p * nord + m];
+      bw[p * nord + l] = 1.0 / prod;
+      gap[p * nord + l] = std::sqrt(std::max(0.0, eps - pc.trad[p * nord + l]));
+    }
+  }
+  std::vector<double> g10, w10, g20, w20, tab;
+  std::vector<int> off;
+  ncs::gauss_legendre(10, g10, w10);
+  ncs::gauss_legendre(20, g20, w20);
+  ncs::near_phi_tables(tab, off);
+  std::vector<double> all;
+  auto put = [&all](const std::vector<double>& v) {
+    const size_t o = all.size();
+    all.insert(all.end(), v.begin(), v.end());
+    return o;
+  };
+  const size_t o_edges = put(edges), o_xn = put(xn), o_bw = put(bw), o_tr = put(pc.trad), o_gap = put(gap),
+               o_beta = put(pc.beta), o_g10 = put(g10), o_w10 = put(w10), o_g20 = put(g20), o_w20 = put(w20),
+               o_tab = put(tab);
+  std::vector<int> ia;
+  ia.insert(ia.end(), pc.bm.begin(), pc.bm.end());
+  ia.insert(ia.end(), pc.bc.begin(), pc.bc.end());
+  ia.insert(ia.end(), off.begin(), off.end());
+  ia.push_back(0);  // error flag
+  c->near_d = dev_upload(all);
+  c->near_i = dev_upload(ia);
+  ncs::NearEvalArgs& a = c->near_args;
+  const double* b = c->near_d;
+  a.K = pc.K;
+  a.M = pc.M;
+  a.npan = npan;
+  a.nord = nord;
+  a.eps = eps;
+  a.edges = b + o_edges;
+  a.xnode = b + o_xn;
+  a.bary = b + o_bw;
+  a.trad = b + o_tr;
+  a.sqrt_gap = b + o_gap;
+  a.beta = b + o_beta;
+  a.g10 = b + o_g10;
+  a.w10 = b + o_w10;
+  a.g20 = b + o_g20;
+  a.w20 = b + o_w20;
+  a.phi_tab = b + o_tab;
+  a.bm = c->near_i;
+  a.bc = c->near_i + pc.K;
+  a.phi_off = c->near_i + 2 * pc.K;
+  a.err = c->near_i + 2 * pc.K + (int)off.size();
+  c->near_ready = true;
+}
+
 int ncs_eval(ncs_ctx* c, int64_t M, const double* targets, const double* fhat, double* out) {
   try {
     check_ready(c);
     if (M < 0 || (M > 0 && (!targets || !out)) || !fhat) throw Fail{NCS_E_INPUT, "bad eval arguments"};
     const double eps = c->pc.eps;
-    // every target's radial projection must be >= 2 eps from each centre (far region of Section 7.1)
+    const int64_t N = c->d.N;
+    // patches whose projected geodesic distance from a target is below kNear eps are
+    // integrated directly (near-patch quadrature); the others by their skeletons
+    constexpr double kNear = 2.5;
+    const double h = 2.0 * std::sin(0.5 * kNear * eps);  // chord of kNear eps
+    std::unordered_map<uint64_t, std::vector<int>> cells;
+    auto key = [h](double x, double y, double z) {
+      const int64_t a = (int64_t)std::floor(x / h) + (1 << 20), b = (int64_t)std::floor(y / h) + (1 << 20),
+                    cc = (int64_t)std::floor(z / h) + (1 << 20);
+      return ((uint64_t)a << 42) ^ ((uint64_t)b << 21) ^ (uint64_t)cc;
+    };
+    for (int64_t j = 0; j < N; ++j) cells[key(c->centres[3 * j], c->centres[3 * j + 1], c->centres[3 * j + 2])].push_back((int)j);
+    std::vector<int64_t> skip_off(M + 1, 0), pair_t;
+    std::vector<int> skip_idx;
     for (int64_t t = 0; t < M; ++t) {
       const double* x = targets + 3 * t;
       const double r = std::sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
       if (!(r > 0.0) || !std::isfinite(r)) throw Fail{NCS_E_INPUT, "bad target"};
       if (c->pc.mode == NCS_EXTERIOR && r < 1.0 - 1e-12) throw Fail{NCS_E_INPUT, "exterior target inside the sphere"};
       if (c->pc.mode == NCS_INTERIOR && r > 1.0 + 1e-12) throw Fail{NCS_E_INPUT, "interior target outside the sphere"};
-      for (int64_t j = 0; j < c->d.N; ++j) {
-        const double* cc = &c->centres[3 * j];
-        const double dot = (x[0] * cc[0] + x[1] * cc[1] + x[2] * cc[2]) / r;
-        if (std::acos(std::max(-1.0, std::min(1.0, dot))) < 2.0 * eps)
-          throw Fail{NCS_E_INPUT, "target " + std::to_string(t) + " within 2 eps of patch " + std::to_string(j)};
-      }
+      const double u[3] = {x[0] / r, x[1] / r, x[2] / r};
+      for (int dx = -1; dx <= 1; ++dx)
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dz = -1; dz <= 1; ++dz) {
+            auto it = cells.find(key(u[0] + dx * h, u[1] + dy * h, u[2] + dz * h));
+            if (it == cells.end()) continue;
+            for (int j : it->second) {
+              const double* cc = &c->centres[3 * j];
+              const double cr[3] = {u[1] * cc[2] - u[2] * cc[1], u[2] * cc[0] - u[0] * cc[2], u[0] * cc[1] - u[1] * cc[0]};
+              const double g = std::atan2(std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]),
+                                          u[0] * cc[0] + u[1] * cc[1] + u[2] * cc[2]);
+              if (g >= kNear * eps) continue;
+              if (std::fabs(r - 1.0) < 1e-12 && g <= eps * (1.0 + 1e-12))
+                throw Fail{NCS_E_INPUT, "target " + std::to_string(t) + " lies on patch " + std::to_string(j) +
+                                            " (the potential there is the boundary data)"};
+              skip_idx.push_back(j);
+              pair_t.push_back(t);
+            }
+          }
+      skip_off[t + 1] = (int64_t)skip_idx.size();
+    }
+    const int64_t npairs = (int64_t)skip_idx.size();
+    if (npairs > 0) {
+      if (c->from_operator) throw Fail{NCS_E_INPUT, "targets within 2.5 eps of a patch need the one-patch data (a context from ncs_create)"};
+      if (c->pc.M > 31) throw Fail{NCS_E_INPUT, "near-patch evaluation supports Zernike degrees M <= 31"};
+      ensure_near_data(c);
     }
     const int64_t n = c->d.N * c->d.K;
     ensure_krylov(c, 1);
     cudaStream_t s = c->stream;
     double *dt = nullptr, *dout = nullptr;
-    CU(cudaMalloc(&dt, std::max<int64_t>(1, 3 * M) * sizeof(double)));
-    CU(cudaMalloc(&dout, std::max<int64_t>(1, M) * sizeof(double)));
+    int64_t* dso = nullptr;
+    int64_t* dpt = nullptr;
+    int* dsi = nullptr;
+    auto release = [&]() {
+      cudaFree(dt);
+      cudaFree(dout);
+      cudaFree(dso);
+      cudaFree(dpt);
+      cudaFree(dsi);
+    };
     try {
+      dt = dev_alloc<double>(std::max<int64_t>(1, 3 * M));
+      dout = dev_alloc<double>(std::max<int64_t>(1, M));
+      dso = dev_upload(skip_off);
+      dpt = dev_upload(pair_t);
+      dsi = dev_upload(skip_idx);
       CU(cudaMemcpyAsync(c->work, fhat, n * sizeof(double), cudaMemcpyHostToDevice, s));
       if (M) CU(cudaMemcpyAsync(dt, targets, 3 * M * sizeof(double), cudaMemcpyHostToDevice, s));
       CU(ncs::launch_outgoing(c->d, c->work, NCS_FP64, s));
-      CU(ncs::launch_eval(c->d, c->pc.mode, M, dt, dout, s));
+      CU(ncs::launch_eval_skip(c->d, c->pc.mode, M, dt, dout, npairs ? dso : nullptr, npairs ? dsi : nullptr, s));
+      int nerr = 0;
+      if (npairs > 0) {
+        ncs::NearEvalArgs a = c->near_args;
+        a.pair_target = dpt;
+        a.pair_patch = dsi;
+        a.targets = dt;
+        a.centres = c->d.centres;
+        a.fhat = c->work;
+        a.out = dout;
+        CU(cudaMemsetAsync(a.err, 0, sizeof(int), s));
+        CU(ncs::launch_near_eval(a, c->pc.mode, npairs, s));
+        CU(cudaMemcpyAsync(&nerr, a.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+      }
       CU(ncs::launch_periodic_dot(n, c->d.K, c->work, c->d.I, c->partial, c->hdev, s));
       double Is = 0.0;
       CU(cudaMemcpyAsync(&Is, c->hdev, sizeof(double), cudaMemcpyDeviceToHost, s));
       if (M) CU(cudaMemcpyAsync(out, dout, M * sizeof(double), cudaMemcpyDeviceToHost, s));
       CU(cudaStreamSynchronize(s));
+      if (nerr) throw Fail{NCS_E_INPUT, "near-patch evaluation: a target too close to a patch for the radial rule"};
       for (int64_t t = 0; t < M; ++t) {
         const double* x = targets + 3 * t;
         const double r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
@@ -1173,12 +1308,10 @@ int ncs_eval(ncs_ctx* c, int64_t M, const double* targets, const double* fhat, d
           out[t] = (out[t] - 1.0) / (3.0 * (-Is)) + (1.0 - r2) / 6.0;  // eq. (vtilde), D = -I_sigma
       }
     } catch (...) {
-      cudaFree(dt);
-      cudaFree(dout);
+      release();
       throw;
     }
-    cudaFree(dt);
-    cudaFree(dout);
+    release();
     return NCS_OK;
   } catch (const Fail& f) {
     return finish(c, f);
@@ -1333,6 +1466,10 @@ int ncs_batch_solve(int B, const double* eps, const int* mode, const int64_t* N,
   else
     ncs_default_params(&prm);
   prm.threads = 1;  // one host thread per instance; instances run concurrently
+  // no CUDA-graph capture: a capture on one worker's stream makes device-wide
+  // synchronisation (which allocation, freeing and the precompute of the other workers may
+  // imply) invalid until it ends; the instances' steps are launched directly
+  prm.cuda_graphs = 0;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return NCS_E_CUDA;
   unsigned hw = std::thread::hardware_concurrency();

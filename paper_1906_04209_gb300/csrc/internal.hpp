@@ -59,6 +59,36 @@ cudaError_t launch_apply_P(const DeviceData& d, const double* x, double* y, int 
 cudaError_t launch_eval(const DeviceData& d, int mode, int64_t M, const double* targets,
                         double* out, cudaStream_t s, int64_t skip = -1);
 
+// ---- near-patch evaluation (neareval.cu)
+constexpr int kNearMaxLevels = 50;
+struct NearEvalArgs {
+  const int64_t* pair_target;  // npairs: target of each (target, near patch) pair
+  const int* pair_patch;       // npairs: the patch
+  const double* targets;       // M x 3
+  const double* centres;       // N x 3
+  const double* fhat;          // N x K densities
+  int K = 0, M = 0, npan = 0, nord = 0;
+  double eps = 0.0;
+  const double* edges;         // npan + 1 radial panel edges
+  const double* xnode;         // npan * nord nodes, normalised to [-1, 1] on their panel
+  const double* bary;          // npan * nord barycentric weights of those nodes
+  const double* trad;          // npan * nord radial nodes t
+  const double* sqrt_gap;      // npan * nord: sqrt(eps - t)
+  const double* beta;          // (npan * nord) x K radial profiles
+  const int* bm;               // K angular orders
+  const int* bc;               // K: 1 for sin, 0 for cos
+  const double *g10, *w10, *g20, *w20;  // Gauss-Legendre rules on [-1, 1]
+  const double* phi_tab;       // (weight, sin^2(phi/2), cos phi) per node
+  const int* phi_off;          // kNearMaxLevels + 2 node offsets
+  double* out;                 // M: the pair's potential is added atomically
+  int* err;                    // set when a radial rule would exceed its shared-memory room
+};
+void near_phi_tables(std::vector<double>& tab, std::vector<int>& off);
+cudaError_t launch_near_eval(const NearEvalArgs& a, int mode, int64_t npairs, cudaStream_t s);
+// launch_eval with a per-target list of patches left out (CSR: skip_off[M + 1], skip_idx)
+cudaError_t launch_eval_skip(const DeviceData& d, int mode, int64_t M, const double* targets, double* out,
+                             const int64_t* skip_off, const int* skip_idx, cudaStream_t s);
+
 // ---- tensor-core GEMMs (tc_gemm.cu)
 // Operands of the tensor-core GEMMs as TF32 hi/lo blocks in the shared-memory layout:
 // tc_pack_words 32-bit words for nrows x Kd in row tiles of H; B operands (the constant
@@ -155,6 +185,11 @@ struct ncs_ctx {
   cudaGraphExec_t step_graph[4] = {nullptr, nullptr, nullptr, nullptr};
   long long step_graph_kernels[4] = {0, 0, 0, 0};
   ncs_tuning tune{16, 4, 4, 16, 0.1};  // tree product launch configuration (ncs_tune)
+  // one-patch data of the near-patch quadrature (ncs_eval), uploaded on first use
+  bool near_ready = false;
+  double* near_d = nullptr;
+  int* near_i = nullptr;
+  ncs::NearEvalArgs near_args{};
   bool graphs_off = false;      // capture failed once: steps are launched directly
   std::string graph_note;       // why
   double solve_stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // see ncs_solve_stats

@@ -443,15 +443,21 @@ template <int MODE>
 __global__ void __launch_bounds__(256) eval_kernel(int64_t N, int p, int pt, const double* __restrict__ centres,
                                                    const double* __restrict__ soff, const double* __restrict__ rho,
                                                    const double* __restrict__ targets, int64_t skip,
-                                                   double* __restrict__ out) {
+                                                   const int64_t* __restrict__ skip_off,
+                                                   const int* __restrict__ skip_idx, double* __restrict__ out) {
   __shared__ double red[256];
   const int64_t t = blockIdx.x;
   const double x0 = targets[3 * t], x1 = targets[3 * t + 1], x2 = targets[3 * t + 2];
   const double rx = sqrt(x0 * x0 + x1 * x1 + x2 * x2);
+  // patches left out for this target: those evaluated by the near-patch quadrature
+  const int64_t s0 = skip_off ? skip_off[t] : 0, s1 = skip_off ? skip_off[t + 1] : 0;
   double acc = 0.0;
   for (int64_t h = threadIdx.x; h < N * p; h += blockDim.x) {
     const int64_t j = h / p;
     if (j == skip) continue;                 // a patch left out (its own points as targets)
+    bool near = false;
+    for (int64_t q = s0; q < s1; ++q) near |= (skip_idx[q] == j);
+    if (near) continue;
     const int64_t g = j * pt + (h - j * p);  // representation 0 (the finest) of patch j
     const double s0 = centres[3 * j] + soff[3 * g], s1 = centres[3 * j + 1] + soff[3 * g + 1],
                  s2 = centres[3 * j + 2] + soff[3 * g + 2];
@@ -479,10 +485,22 @@ cudaError_t launch_eval(const DeviceData& d, int mode, int64_t M, const double* 
   if (M == 0) return cudaSuccess;
   if (mode == 0)
     count_launch(), eval_kernel<0><<<(unsigned)M, 256, 0, s>>>(d.N, d.p0, d.p, d.centres, d.soff64, d.rho64, targets,
-                                                               skip, out);
+                                                               skip, nullptr, nullptr, out);
   else
     count_launch(), eval_kernel<1><<<(unsigned)M, 256, 0, s>>>(d.N, d.p0, d.p, d.centres, d.soff64, d.rho64, targets,
-                                                               skip, out);
+                                                               skip, nullptr, nullptr, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eval_skip(const DeviceData& d, int mode, int64_t M, const double* targets, double* out,
+                             const int64_t* skip_off, const int* skip_idx, cudaStream_t s) {
+  if (M == 0) return cudaSuccess;
+  if (mode == 0)
+    count_launch(), eval_kernel<0><<<(unsigned)M, 256, 0, s>>>(d.N, d.p0, d.p, d.centres, d.soff64, d.rho64, targets,
+                                                               -1, skip_off, skip_idx, out);
+  else
+    count_launch(), eval_kernel<1><<<(unsigned)M, 256, 0, s>>>(d.N, d.p0, d.p, d.centres, d.soff64, d.rho64, targets,
+                                                               -1, skip_off, skip_idx, out);
   return cudaGetLastError();
 }
 
