@@ -153,7 +153,10 @@ def run_ours(args):
     ctx.set_patches(centres)
     setup_s = time.time() - t0
     tuning = None
-    if args.tune:
+    if args.set_tuning:
+        ctx.set_tuning(**json.loads(args.set_tuning))
+        tuning = {"config": ctx.get_tuning(), "set": True}
+    elif args.tune:
         _progress("tune")
         cfg, rep = ctx.tune(flags=3)
         tuning = {"config": cfg, "default_ms": round(rep["default_ms"], 3), "tuned_ms": round(rep["tuned_ms"], 3),
@@ -221,6 +224,8 @@ def run_ours(args):
     e2e_s = max_over_ranks((time.perf_counter() - t0) / ee, device="cuda")
 
     # FP64 product rate (fewer steps: the FP64 pipe is the bottleneck on this part)
+    fma_peaks = {"fp64_tflops": round(ncs.fma_peak(ncs.FP64), 2), "fp32_tflops": round(ncs.fma_peak(ncs.FP32), 2),
+                 "source": "ncs_fma_peak microkernel (independent FMA chains, best of 3 launches)"}
     fp64 = None
     if args.fp64_steps > 0:
         step(ncs.FP64)
@@ -306,6 +311,7 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "clocks": clk,
         "stages_ms": {k: round(v, 3) for k, v in stages32.items()},
+        "fma_peaks": fma_peaks,
         "fp64_matvecs_per_s": round(fp64, 4) if fp64 else None,
         "df64_matvecs_per_s": round(df64, 4) if df64 else None,
         "pairs_per_step": tstats["p2l_pairs"] + tstats["direct_pairs"],
@@ -473,6 +479,8 @@ def main():
     ap.add_argument("--solve-tol", type=float, default=1e-8)
     ap.add_argument("--no-batch", dest="batch", action="store_false")
     ap.add_argument("--no-tune", dest="tune", action="store_false")
+    # a fixed launch configuration instead of tuning (profiler captures of a chosen variant)
+    ap.add_argument("--set-tuning", default=None, help='JSON, e.g. {"p2l_poly": 2, "direct_poly": 2}')
     ap.add_argument("--batch-size", type=int, default=256)
     # a smaller layout of the same family (profiler captures only; the line names its N)
     ap.add_argument("--patches", type=int, default=None)

@@ -436,6 +436,15 @@ int ncs_batch_solve(int B, const double* eps, const int* mode, const int64_t* N,
                     int K, double tol, int precision, const ncs_params* params, int workers, double* scalar,
                     double* Isigma, int* iterations, double* relres, int* status, double* seconds);
 
+/*
+ * Peak FMA throughput of the current device at precision NCS_FP64 or NCS_FP32, measured by
+ * the library's own microkernel (independent FMA chains on every SM, CUDA-event timed, best
+ * of three launches after a warm-up), in TFLOP/s (2 flops per FMA) into *tflops: the
+ * denominator of the pair kernels' pipe fractions. No counterpart in the paper.
+ * Synchronous; about 0.1 s. Errors: NCS_E_INPUT, NCS_E_CUDA.
+ */
+int ncs_fma_peak(int precision, double* tflops);
+
 /* Message of the last failure on ctx (static string if ctx is NULL). */
 const char* ncs_last_error(const ncs_ctx* ctx);
 

@@ -163,4 +163,136 @@ __device__ __forceinline__ void pair_f2_acc(const f2* a, float4 sh, float4 sl, c
   acc.lo += t.lo + g.lo;
 }
 
+// ---- packed float-float: two independent float-float values per f32x2 register pair --
+// The same error-free transformations as above on add/sub/mul/fma.rn.f32x2, which round
+// each 32-bit half exactly as the scalar instruction does; a thread evaluates its two
+// targets' pairs with one packed instruction where the scalar code issues two. Integer
+// steps (exponent and table index of the logarithm), the MUFU reciprocal square root and
+// the table loads stay per half.
+struct f2x2 {
+  f32x2 hi, lo;
+};
+
+__device__ __forceinline__ f32x2 x2_neg(f32x2 a) { return a ^ 0x8000000080000000ull; }
+__device__ __forceinline__ f32x2 x2_splat(float v) { return x2_pack(v, v); }
+
+__device__ __forceinline__ f2x2 two_sum_x2(f32x2 a, f32x2 b) {
+  const f32x2 s = x2_add(a, b);
+  const f32x2 bb = x2_sub(s, a);
+  return {s, x2_add(x2_sub(a, x2_sub(s, bb)), x2_sub(b, bb))};
+}
+
+__device__ __forceinline__ f2x2 fast_two_sum_x2(f32x2 a, f32x2 b) {
+  const f32x2 s = x2_add(a, b);
+  return {s, x2_sub(b, x2_sub(s, a))};
+}
+
+__device__ __forceinline__ f2x2 two_prod_x2(f32x2 a, f32x2 b) {
+  const f32x2 p = x2_mul(a, b);
+  return {p, x2_fma(a, b, x2_neg(p))};
+}
+
+__device__ __forceinline__ f2x2 f2_mul_x2(f2x2 a, f2x2 b) {
+  f2x2 p = two_prod_x2(a.hi, b.hi);
+  p.lo = x2_fma(a.hi, b.lo, x2_fma(a.lo, b.hi, p.lo));
+  return fast_two_sum_x2(p.hi, p.lo);
+}
+
+__device__ __forceinline__ f2x2 f2_add_sloppy_x2(f2x2 a, f2x2 b) {
+  const f2x2 s = two_sum_x2(a.hi, b.hi);
+  return fast_two_sum_x2(s.hi, x2_add(s.lo, x2_add(a.lo, b.lo)));
+}
+
+// f2_log_pow2 on both halves (see there).
+__device__ __forceinline__ f2x2 f2_log_pow2_x2(f2x2 v, int k, const float4* __restrict__ tab) {
+  float vh[2], vlo[2];
+  x2_unpack(v.hi, vh[0], vh[1]);
+  x2_unpack(v.lo, vlo[0], vlo[1]);
+  float m[2], ci[2], sc[2], ef[2];
+  float4 t[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int ib = __float_as_int(vh[h]);
+    const int e = (ib >> 23) - 127;
+    m[h] = __int_as_float((ib & 0x007fffff) | 0x3f800000);
+    sc[h] = __int_as_float((127 - e) << 23);
+    const int i = (ib >> 17) & (kLogTable - 1);
+    ci[h] = __int_as_float(0x3f800000 | (i << 17) | (1 << 16));
+    t[h] = tab[i];
+    ef[h] = (float)(e - k);
+  }
+  const f32x2 vl = x2_mul(x2_pack(vlo[0], vlo[1]), x2_pack(sc[0], sc[1]));  // v.lo / 2^e, exact
+  const f32x2 tx = x2_pack(t[0].x, t[1].x), ty = x2_pack(t[0].y, t[1].y), tz = x2_pack(t[0].z, t[1].z),
+              tw = x2_pack(t[0].w, t[1].w);
+  const f32x2 nh = x2_sub(x2_pack(m[0], m[1]), x2_pack(ci[0], ci[1]));
+  const f32x2 dh = x2_mul(nh, tz);
+  const f2x2 d = fast_two_sum_x2(dh, x2_fma(nh, tw, x2_fma(vl, tz, x2_fma(nh, tz, x2_neg(dh)))));
+  const f32x2 q = x2_mul(d.hi, d.hi);
+  const f32x2 ql = x2_fma(x2_mul(x2_splat(2.0f), d.hi), d.lo, x2_fma(d.hi, d.hi, x2_neg(q)));
+  const f32x2 poly =
+      x2_fma(d.hi, x2_fma(d.hi, x2_fma(d.hi, x2_splat(-0.166666667f), x2_splat(0.2f)), x2_splat(-0.25f)),
+             x2_splat(0.333333333f));
+  const f32x2 tail = x2_mul(x2_mul(q, d.hi), poly);
+  const f32x2 m05 = x2_splat(-0.5f);
+  const f32x2 rs = x2_fma(m05, q, d.hi);  // |d| > |d^2 / 2|: Fast2Sum
+  const f32x2 re = x2_fma(m05, q, x2_neg(x2_sub(rs, d.hi)));
+  const f32x2 rl = x2_add(x2_add(re, d.lo), x2_fma(m05, ql, tail));
+  const f2x2 s1 = two_sum_x2(tx, rs);
+  const f32x2 l1 = x2_add(s1.lo, x2_add(rl, ty));
+  const f32x2 E = x2_pack(ef[0], ef[1]);
+  const f32x2 Eh = x2_mul(E, x2_splat(0.693147182464599609375f));
+  const f32x2 El = x2_fma(E, x2_splat(-1.904654323148236e-09f), x2_fma(E, x2_splat(0.693147182464599609375f), x2_neg(Eh)));
+  const f2x2 s2 = two_sum_x2(Eh, s1.hi);
+  return fast_two_sum_x2(s2.hi, x2_add(s2.lo, x2_add(l1, El)));
+}
+
+template <int MODE>
+__device__ __forceinline__ f2x2 green_f2_x2(f2x2 d2, const float4* __restrict__ tab) {
+  float a0, a1;
+  x2_unpack(d2.hi, a0, a1);
+  const f32x2 y = x2_pack(rsqrt_mufu(a0), rsqrt_mufu(a1));
+  const f2x2 yy = two_prod_x2(y, y);
+  f2x2 m = two_prod_x2(d2.hi, yy.hi);
+  m.lo = x2_fma(d2.hi, yy.lo, x2_fma(d2.lo, yy.hi, m.lo));
+  const f32x2 r = x2_sub(x2_sub(x2_splat(1.0f), m.hi), m.lo);  // 1 - d^2 y^2, ~1e-7
+  // 1/d = y (1 + r/2 + 3 r^2 / 8): u = 2/d
+  const f2x2 u = fast_two_sum_x2(x2_mul(x2_splat(2.0f), y), x2_mul(y, x2_fma(x2_mul(x2_splat(0.75f), r), r, r)));
+  f2x2 v;
+  if (MODE == 0) {
+    v = two_sum_x2(u.hi, x2_splat(1.0f));
+    v = fast_two_sum_x2(v.hi, x2_add(v.lo, u.lo));
+  } else {
+    v = f2_add_sloppy_x2(f2_mul_x2(d2, u), d2);  // 2d = d^2 u
+  }
+  const f2x2 L = f2_log_pow2_x2(v, MODE == 0 ? 0 : 2, tab);
+  return f2_add_sloppy_x2(u, f2x2{x2_neg(L.hi), x2_neg(L.lo)});
+}
+
+// pair_f2_acc for two targets at once (lane h of every packed value is target h): the
+// packed target offsets A[0..2], one staged source (hi, lo) broadcast to both lanes.
+template <int MODE>
+__device__ __forceinline__ void pair_f2_acc_x2(const f2x2* A, float4 sh, float4 sl, const float4* __restrict__ tab,
+                                               f2x2& acc) {
+  f2x2 dx = two_sum_x2(A[0].hi, x2_splat(-sh.x)), dy = two_sum_x2(A[1].hi, x2_splat(-sh.y)),
+       dz = two_sum_x2(A[2].hi, x2_splat(-sh.z));
+  dx.lo = x2_add(dx.lo, x2_sub(A[0].lo, x2_splat(sl.x)));
+  dy.lo = x2_add(dy.lo, x2_sub(A[1].lo, x2_splat(sl.y)));
+  dz.lo = x2_add(dz.lo, x2_sub(A[2].lo, x2_splat(sl.z)));
+  const f32x2 px = x2_mul(dx.hi, dx.hi), py = x2_mul(dy.hi, dy.hi), pz = x2_mul(dz.hi, dz.hi);
+  const f2x2 s1 = two_sum_x2(px, py);
+  const f2x2 s2 = two_sum_x2(s1.hi, pz);
+  f32x2 lo = x2_add(x2_add(s1.lo, s2.lo),
+                    x2_add(x2_add(x2_fma(dx.hi, dx.hi, x2_neg(px)), x2_fma(dy.hi, dy.hi, x2_neg(py))),
+                           x2_fma(dz.hi, dz.hi, x2_neg(pz))));
+  const f32x2 two = x2_splat(2.0f);
+  lo = x2_fma(x2_fma(two, dx.hi, dx.lo), dx.lo, lo);
+  lo = x2_fma(x2_fma(two, dy.hi, dy.lo), dy.lo, lo);
+  lo = x2_fma(x2_fma(two, dz.hi, dz.lo), dz.lo, lo);
+  const f2x2 d2 = fast_two_sum_x2(s2.hi, lo);
+  const f2x2 g = f2_mul_x2(green_f2_x2<MODE>(d2, tab), f2x2{x2_splat(sh.w), x2_splat(sl.w)});
+  const f2x2 t = two_sum_x2(acc.hi, g.hi);
+  acc.hi = t.hi;
+  acc.lo = x2_add(acc.lo, x2_add(t.lo, g.lo));
+}
+
 }  // namespace ncs

@@ -288,10 +288,19 @@ __global__ void __launch_bounds__(DF_THREADS) direct_field_df_kernel(
     f2 part[DF_NT];
 #pragma unroll
     for (int t = 0; t < DF_NT; ++t) part[t] = f2{0.0f, 0.0f};
-    for (int s = 0; s < ns; ++s) {
-      const float4 h = Sh[s], l = Sl[s];
+    if constexpr (DF_NT == 2) {  // both targets in one packed float-float chain
+      f2x2 A[3], P{x2_splat(0.0f), x2_splat(0.0f)};
 #pragma unroll
-      for (int t = 0; t < DF_NT; ++t) pair_f2_acc<MODE>(a[t], h, l, tab, part[t]);
+      for (int c = 0; c < 3; ++c) A[c] = f2x2{x2_pack(a[0][c].hi, a[1][c].hi), x2_pack(a[0][c].lo, a[1][c].lo)};
+      for (int s = 0; s < ns; ++s) pair_f2_acc_x2<MODE>(A, Sh[s], Sl[s], tab, P);
+      x2_unpack(P.hi, part[0].hi, part[1].hi);
+      x2_unpack(P.lo, part[0].lo, part[1].lo);
+    } else {
+      for (int s = 0; s < ns; ++s) {
+        const float4 h = Sh[s], l = Sl[s];
+#pragma unroll
+        for (int t = 0; t < DF_NT; ++t) pair_f2_acc<MODE>(a[t], h, l, tab, part[t]);
+      }
     }
 #pragma unroll
     for (int t = 0; t < DF_NT; ++t) acc[t] += f2_to_double(part[t]);

@@ -736,11 +736,13 @@ __global__ void __launch_bounds__(P2L_THREADS) p2l_df_kernel(
       const int wbase = base + (threadIdx.x & ~31);
       const int nact = (wbase >= q) ? 0 : ((wbase + P2L_THREADS >= q) ? 1 : NT);
       if (nact == NT) {
-        for (int s = 0; s < ns; ++s) {
-          const float4 h = Sh[s], l = Sl[s];
+        // both targets in one packed float-float chain
+        f2x2 A[3], P{x2_splat(0.0f), x2_splat(0.0f)};
 #pragma unroll
-          for (int t = 0; t < NT; ++t) pair_f2_acc<MODE>(a[t], h, l, tab, part[t]);
-        }
+        for (int c = 0; c < 3; ++c) A[c] = f2x2{x2_pack(a[0][c].hi, a[1][c].hi), x2_pack(a[0][c].lo, a[1][c].lo)};
+        for (int s = 0; s < ns; ++s) pair_f2_acc_x2<MODE>(A, Sh[s], Sl[s], tab, P);
+        x2_unpack(P.hi, part[0].hi, part[1].hi);
+        x2_unpack(P.lo, part[0].lo, part[1].lo);
       } else if (nact == 1) {
         for (int s = 0; s < ns; ++s) pair_f2_acc<MODE>(a[0], Sh[s], Sl[s], tab, part[0]);
       }
@@ -814,10 +816,14 @@ __global__ void __launch_bounds__(DTD_THREADS) direct_list_df_kernel(
     f2 part[DTD_NT];
 #pragma unroll
     for (int t = 0; t < DTD_NT; ++t) part[t] = f2{0.0f, 0.0f};
-    for (int s = 0; s < ns; ++s) {
-      const float4 h = Sh[s], l = Sl[s];
+    static_assert(DTD_NT == 2, "the packed float-float chain serves two targets");
+    {
+      f2x2 A[3], P{x2_splat(0.0f), x2_splat(0.0f)};
 #pragma unroll
-      for (int t = 0; t < DTD_NT; ++t) pair_f2_acc<MODE>(a[t], h, l, tab, part[t]);
+      for (int c = 0; c < 3; ++c) A[c] = f2x2{x2_pack(a[0][c].hi, a[1][c].hi), x2_pack(a[0][c].lo, a[1][c].lo)};
+      for (int s = 0; s < ns; ++s) pair_f2_acc_x2<MODE>(A, Sh[s], Sl[s], tab, P);
+      x2_unpack(P.hi, part[0].hi, part[1].hi);
+      x2_unpack(P.lo, part[0].lo, part[1].lo);
     }
 #pragma unroll
     for (int t = 0; t < DTD_NT; ++t) acc[t] += f2_to_double(part[t]);

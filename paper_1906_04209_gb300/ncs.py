@@ -32,7 +32,7 @@ EXPORTS = ["ncs_default_params", "ncs_create", "ncs_create_from_operator", "ncs_
            "ncs_tree_pairs", "ncs_tree_stats", "ncs_profile_matvec", "ncs_create_from_operators", "ncs_get_reps",
            "ncs_tc_gemm_f32", "ncs_batch_solve", "ncs_block_dots", "ncs_block_dots_noalloc",
            "ncs_launch_count", "ncs_get_rep", "ncs_set_precision", "ncs_patch_residual", "ncs_solve_stats", "ncs_tune", "ncs_set_tuning",
-           "ncs_get_tuning"]
+           "ncs_get_tuning", "ncs_fma_peak"]
 
 
 class ncs_params(ctypes.Structure):
@@ -111,6 +111,7 @@ def load(path: str = LIB_PATH):
     lib.ncs_tune.argtypes = [VP, ctypes.c_int, ctypes.c_char_p, ctypes.POINTER(ncs_tuning), D, ctypes.c_int]
     lib.ncs_set_tuning.argtypes = [VP, ctypes.POINTER(ncs_tuning)]
     lib.ncs_get_tuning.argtypes = [VP, ctypes.POINTER(ncs_tuning)]
+    lib.ncs_fma_peak.argtypes = [ctypes.c_int, D]
     lib.ncs_launch_count.argtypes = []
     lib.ncs_launch_count.restype = ctypes.c_int64
     lib.ncs_destroy.argtypes = [VP]
@@ -165,6 +166,15 @@ def block_dots(n, k, V_ptr, ld, w_ptr, out_ptr, stream=0):
     rc = load().ncs_block_dots(n, k, VP(V_ptr), ld, VP(w_ptr), VP(out_ptr), VP(stream))
     if rc != NCS_OK:
         raise NcsError(rc, "ncs_block_dots failed")
+
+
+def fma_peak(precision=FP64):
+    """Measured FMA peak of the current device in TFLOP/s (see ncs_fma_peak)."""
+    out = ctypes.c_double()
+    rc = load().ncs_fma_peak(precision, ctypes.byref(out))
+    if rc != NCS_OK:
+        raise NcsError(rc, "ncs_fma_peak failed")
+    return out.value
 
 
 def launch_count():
