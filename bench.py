@@ -154,7 +154,8 @@ def run_ours(args):
     setup_s = time.time() - t0
     tuning = None
     if args.set_tuning:
-        ctx.set_tuning(**json.loads(args.set_tuning))
+        kv = dict(item.split("=") for item in args.set_tuning.split(","))
+        ctx.set_tuning(**{k: (float(v) if k == "l2p_weight" else int(v)) for k, v in kv.items()})
         tuning = {"config": ctx.get_tuning(), "set": True}
     elif args.tune:
         _progress("tune")
@@ -480,7 +481,7 @@ def main():
     ap.add_argument("--no-batch", dest="batch", action="store_false")
     ap.add_argument("--no-tune", dest="tune", action="store_false")
     # a fixed launch configuration instead of tuning (profiler captures of a chosen variant)
-    ap.add_argument("--set-tuning", default=None, help='JSON, e.g. {"p2l_poly": 2, "direct_poly": 2}')
+    ap.add_argument("--set-tuning", default=None, help="comma-separated key=value, e.g. p2l_poly=2,direct_poly=2")
     ap.add_argument("--batch-size", type=int, default=256)
     # a smaller layout of the same family (profiler captures only; the line names its N)
     ap.add_argument("--patches", type=int, default=None)

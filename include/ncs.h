@@ -130,6 +130,10 @@ typedef struct ncs_tuning {
   double l2p_weight;  /* cost of one L2P node-grid product in pair evaluations, weighed when
                          a group chooses its incoming grid or direct evaluation (Step 3):
                          0.01..1; changing it rebuilds the host tree */
+  int p2l_rsq;        /* of every 16 packed pair chains in the P2L kernel, how many take the
+                         reciprocal square root by Newton steps on the FMA pipe (Lomont's
+                         seed) instead of the MUFU unit: 0, 4, 8 (with p2l_poly <= 16) */
+  int direct_rsq;     /* the same for the direct lists: 0, 4, 8 */
 } ncs_tuning;
 
 /*
@@ -313,8 +317,8 @@ int ncs_solve(ncs_ctx* ctx, double tol, int precision, double* fhat, double* sca
 
 /*
  * Autotuner of the tree product. Times FP32 tree products of the context's layout under
- * candidate launch configurations (flags & 1: the pair-kernel variants, each stage timed
- * with CUDA events; flags & 2: the work-item size and the grid-or-direct weight, each
+ * candidate launch configurations (flags & 1: the pair-kernel variants (tile, polynomial
+ * logarithm and Newton reciprocal-square-root shares), each stage timed with CUDA events; flags & 2: the work-item size and the grid-or-direct weight, each
  * candidate on a rebuilt tree), keeps a candidate only if its product matches the
  * float-float product of the same input to 2e-5 of the largest entry, and applies the
  * fastest to ctx (products and solves that follow use it). With cache_path non-NULL the

@@ -297,6 +297,8 @@ void ensure_tree(ncs_ctx* c) {
   c->tdev.cfg.p2l_tile = c->tune.p2l_tile;
   c->tdev.cfg.p2l_poly = c->tune.p2l_poly;
   c->tdev.cfg.direct_poly = c->tune.direct_poly;
+  c->tdev.cfg.p2l_rsq = c->tune.p2l_rsq;
+  c->tdev.cfg.direct_rsq = c->tune.direct_rsq;
 }
 
 void outgoing(ncs_ctx* c, const double* x, int prec, cudaStream_t s) {
@@ -557,9 +559,10 @@ void validate_params(const ncs_params& p) {
 
 bool tuning_valid(const ncs_tuning& t) {
   const auto poly_ok = [](int p) { return p == 0 || p == 2 || p == 4 || p == 6; };
+  const auto rsq_ok = [](int r) { return r == 0 || r == 4 || r == 8; };
   return (t.p2l_tile == 8 || t.p2l_tile == 16) && poly_ok(t.p2l_poly) && poly_ok(t.direct_poly) &&
-         t.item_patches >= 8 && t.item_patches <= 64 && t.item_patches % t.p2l_tile == 0 &&
-         t.l2p_weight >= 0.01 && t.l2p_weight <= 1.0;
+         rsq_ok(t.p2l_rsq) && rsq_ok(t.direct_rsq) && t.item_patches >= 8 && t.item_patches <= 64 &&
+         t.item_patches % t.p2l_tile == 0 && t.l2p_weight >= 0.01 && t.l2p_weight <= 1.0;
 }
 
 // Applies a launch configuration; a change of the tree knobs drops the tree (rebuilt on
@@ -596,8 +599,8 @@ bool tune_cache_lookup(const char* path, const std::string& key, ncs_tuning* t) 
   bool hit = false;
   ncs_tuning v{};
   while (std::fgets(line, sizeof line, f)) {
-    if (std::sscanf(line, "ncs-tune-v1 %255s %d %d %d %d %lf", k, &v.p2l_tile, &v.p2l_poly, &v.direct_poly,
-                    &v.item_patches, &v.l2p_weight) == 6 &&
+    if (std::sscanf(line, "ncs-tune-v2 %255s %d %d %d %d %lf %d %d", k, &v.p2l_tile, &v.p2l_poly, &v.direct_poly,
+                    &v.item_patches, &v.l2p_weight, &v.p2l_rsq, &v.direct_rsq) == 8 &&
         key == k && tuning_valid(v)) {
       *t = v;
       hit = true;  // the last entry for a key wins
@@ -610,8 +613,8 @@ bool tune_cache_lookup(const char* path, const std::string& key, ncs_tuning* t) 
 void tune_cache_store(const char* path, const std::string& key, const ncs_tuning& t) {
   FILE* f = std::fopen(path, "a");
   if (!f) throw Fail{NCS_E_INPUT, std::string("tune cache: cannot append to ") + path};
-  std::fprintf(f, "ncs-tune-v1 %s %d %d %d %d %.17g\n", key.c_str(), t.p2l_tile, t.p2l_poly, t.direct_poly,
-               t.item_patches, t.l2p_weight);
+  std::fprintf(f, "ncs-tune-v2 %s %d %d %d %d %.17g %d %d\n", key.c_str(), t.p2l_tile, t.p2l_poly, t.direct_poly,
+               t.item_patches, t.l2p_weight, t.p2l_rsq, t.direct_rsq);
   std::fclose(f);
 }
 
@@ -1618,24 +1621,30 @@ int ncs_tune(ncs_ctx* c, int flags, const char* cache_path, ncs_tuning* out, dou
         double bp = m0.err <= kTol ? m0.p2l : 1e300;
         ncs_tuning bt = start;
         for (int jt : {8, 16})
-          for (int poly : {0, 2, 4, 6}) {
-            ncs_tuning t = start;
-            t.p2l_tile = jt;
-            t.p2l_poly = poly;
-            if (!tuning_valid(t) || (jt == start.p2l_tile && poly == start.p2l_poly)) continue;
+          for (int poly : {0, 2, 4, 6})
+            for (int rsq : {0, 4, 8}) {
+              ncs_tuning t = start;
+              t.p2l_tile = jt;
+              t.p2l_poly = poly;
+              t.p2l_rsq = rsq;
+              if (!tuning_valid(t) || (jt == start.p2l_tile && poly == start.p2l_poly && rsq == start.p2l_rsq))
+                continue;
+              apply_tuning(c, t);
+              const Meas m = measure(kReps);
+              if (m.err <= kTol && m.p2l < bp) bp = m.p2l, bt = t;
+            }
+        double bd = m0.err <= kTol ? m0.direct : 1e300;
+        const ncs_tuning bp2l = bt;
+        for (int poly : {0, 2, 4, 6})
+          for (int rsq : {0, 4, 8}) {
+            ncs_tuning t = bp2l;
+            t.direct_poly = poly;
+            t.direct_rsq = rsq;
+            if (poly == start.direct_poly && rsq == start.direct_rsq) continue;
             apply_tuning(c, t);
             const Meas m = measure(kReps);
-            if (m.err <= kTol && m.p2l < bp) bp = m.p2l, bt = t;
+            if (m.err <= kTol && m.direct < bd) bd = m.direct, bt.direct_poly = poly, bt.direct_rsq = rsq;
           }
-        double bd = m0.err <= kTol ? m0.direct : 1e300;
-        for (int poly : {0, 2, 4, 6}) {
-          ncs_tuning t = bt;
-          t.direct_poly = poly;
-          if (poly == start.direct_poly) continue;
-          apply_tuning(c, t);
-          const Meas m = measure(kReps);
-          if (m.err <= kTol && m.direct < bd) bd = m.direct, bt.direct_poly = poly;
-        }
         apply_tuning(c, bt);
         const Meas m = measure(kReps);
         best = bt;

@@ -188,9 +188,11 @@ __device__ __forceinline__ f32x2 x2_fma(f32x2 a, f32x2 b, f32x2 c) {
 
 // The packed constants of a pair loop, formed once per call.
 struct PairX2Consts {
-  f32x2 one, nln2, bias, c[9];
+  f32x2 one, nln2, bias, mhalf, three_halves, c[9];
   __device__ __forceinline__ PairX2Consts() {
     one = x2_pack(1.0f, 1.0f);
+    mhalf = x2_pack(-0.5f, -0.5f);
+    three_halves = x2_pack(1.5f, 1.5f);
     nln2 = x2_pack(-kLn2f, -kLn2f);
     bias = x2_pack(12582912.0f, 12582912.0f);
     const float cf[9] = {1.224903390e-01f,  -2.088673115e-01f, 2.178854942e-01f,
@@ -215,16 +217,40 @@ __device__ __forceinline__ f32x2 lg2_poly_x2(f32x2 x, const PairX2Consts& k) {
   return x2_fma(f, p, ef);
 }
 
+// 1/sqrt(x) for normal x > 0 on the FMA and integer pipes instead of the MUFU unit, both
+// halves: the seed of Lomont's "Fast Inverse Square Root" (2003), the bits 0x5f375a86 minus
+// half the bits of x (relative error ~3.4e-2), then two Newton steps
+// y <- y (3/2 - (x/2) y^2), each squaring the relative error (1.75e-3, then 4.7e-6): 7 FP32
+// operations and two integer ones per value. Used for a tuned share of the FP32 pairs only,
+// whose products the tuner checks against the float-float product.
+__device__ __forceinline__ f32x2 rsqrt_newton_x2(f32x2 x, const PairX2Consts& k) {
+  float x0, x1;
+  x2_unpack(x, x0, x1);
+  f32x2 y = x2_pack(__int_as_float(0x5f375a86 - (__float_as_int(x0) >> 1)),
+                    __int_as_float(0x5f375a86 - (__float_as_int(x1) >> 1)));
+  const f32x2 nhx = x2_mul(k.mhalf, x);
+  y = x2_mul(y, x2_fma(x2_mul(nhx, y), y, k.three_halves));
+  y = x2_mul(y, x2_fma(x2_mul(nhx, y), y, k.three_halves));
+  return y;
+}
+
 // Two pairs (one target, the two sources of a staged pair) into the packed accumulator.
-// (X, Y) = (x pair, y pair), (Z, W) = (z pair, strength pair) of the sources.
-template <int MODE, bool POLY>
+// (X, Y) = (x pair, y pair), (Z, W) = (z pair, strength pair) of the sources. POLY: the
+// logarithm by lg2_poly on the FMA pipe; RSQ: the reciprocal square root by
+// rsqrt_newton_x2 (else both on the MUFU unit).
+template <int MODE, bool POLY, bool RSQ = false>
 __device__ __forceinline__ f32x2 pair32_x2(f32x2 ax, f32x2 ay, f32x2 az, const ulonglong2& XY,
                                            const ulonglong2& ZW, f32x2 acc, const PairX2Consts& k) {
   const f32x2 dx = x2_sub(ax, XY.x), dy = x2_sub(ay, XY.y), dz = x2_sub(az, ZW.x);
   const f32x2 d2 = x2_fma(dx, dx, x2_fma(dy, dy, x2_mul(dz, dz)));
-  float d0, d1;
-  x2_unpack(d2, d0, d1);
-  const f32x2 rh = x2_pack(rsqrt_mufu(d0), rsqrt_mufu(d1));
+  f32x2 rh;
+  if constexpr (RSQ) {
+    rh = rsqrt_newton_x2(d2, k);
+  } else {
+    float d0, d1;
+    x2_unpack(d2, d0, d1);
+    rh = x2_pack(rsqrt_mufu(d0), rsqrt_mufu(d1));
+  }
   const f32x2 arg = (MODE == 0) ? x2_add(k.one, rh) : x2_fma(d2, rh, d2);
   f32x2 l;
   if constexpr (POLY) {
@@ -260,10 +286,10 @@ __device__ __forceinline__ void stage_pad_x2(float4* S, int ns) {
 
 // part[t] = sum over the ns staged sources (paired layout, padded to even) of G(a_t, s)
 // rho_s for the NT half-scaled targets: source pairs in groups of 8, the first POLY16
-// of every 16 two-pair chains (scaled to a group's 8 NT chains) on lg2_poly. POLY16 is
-// a run-time choice of the kernels' launch configuration (set by ncs_tune), with
-// NCS_PAIR_X2_POLY as the default.
-template <int MODE, int NT, int POLY16 = NCS_PAIR_X2_POLY>
+// of every 16 two-pair chains (scaled to a group's 8 NT chains) on lg2_poly and the last
+// RSQ16 with the Newton reciprocal square root. Both are run-time choices of the kernels'
+// launch configuration (set by ncs_tune), with NCS_PAIR_X2_POLY and 0 as the defaults.
+template <int MODE, int NT, int POLY16 = NCS_PAIR_X2_POLY, int RSQ16 = 0>
 __device__ __forceinline__ void pair_loop32x2(const float4* __restrict__ S, int ns, const float* ax, const float* ay,
                                               const float* az, float* part) {
   const PairX2Consts k;
@@ -277,6 +303,8 @@ __device__ __forceinline__ void pair_loop32x2(const float4* __restrict__ S, int 
     P[t] = x2_pack(0.0f, 0.0f);
   }
   constexpr int kPoly = POLY16 * NT / 2;  // poly chains per group of 8 * NT
+  constexpr int kRsq = RSQ16 * NT / 2;    // Newton rsqrt chains (the last ones of a group)
+  static_assert(kPoly + kRsq <= 8 * NT, "polynomial and Newton shares overlap");
   const int np = (ns + 1) >> 1;
   int s = 0;
   for (; s + 8 <= np; s += 8) {
@@ -287,6 +315,8 @@ __device__ __forceinline__ void pair_loop32x2(const float4* __restrict__ S, int 
       for (int t = 0; t < NT; ++t) {
         if (u * NT + t < kPoly)
           P[t] = pair32_x2<MODE, true>(AX[t], AY[t], AZ[t], XY, ZW, P[t], k);
+        else if (u * NT + t >= 8 * NT - kRsq)
+          P[t] = pair32_x2<MODE, false, true>(AX[t], AY[t], AZ[t], XY, ZW, P[t], k);
         else
           P[t] = pair32_x2<MODE, false>(AX[t], AY[t], AZ[t], XY, ZW, P[t], k);
       }

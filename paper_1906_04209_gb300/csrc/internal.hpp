@@ -184,7 +184,7 @@ struct ncs_ctx {
   // one captured Arnoldi step (product + orthogonalisation + state copy) per precision
   cudaGraphExec_t step_graph[4] = {nullptr, nullptr, nullptr, nullptr};
   long long step_graph_kernels[4] = {0, 0, 0, 0};
-  ncs_tuning tune{16, 4, 4, 16, 0.1};  // tree product launch configuration (ncs_tune)
+  ncs_tuning tune{16, 4, 4, 16, 0.1, 0, 0};  // tree product launch configuration (ncs_tune)
   // one-patch data of the near-patch quadrature (ncs_eval), uploaded on first use
   bool near_ready = false;
   double* near_d = nullptr;

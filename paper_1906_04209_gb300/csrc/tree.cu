@@ -62,7 +62,7 @@ constexpr int P2L_DF_JT = 8;
 // One block per work item (grid group g, a slice of its interaction-list patches). JT
 // source patches per shared-memory tile, POLY of every 16 packed pair chains with the
 // logarithm on the FMA pipe (FP32 only): both chosen at run time (KernelConfig).
-template <typename R, int MODE, int JT = P2L_JT, int POLY = NCS_PAIR_X2_POLY>
+template <typename R, int MODE, int JT = P2L_JT, int POLY = NCS_PAIR_X2_POLY, int RSQ = 0>
 __global__ void __launch_bounds__(P2L_THREADS) p2l_kernel(
     const int* __restrict__ witem_group, const int* __restrict__ witem_rep, const int* __restrict__ rep_p,
     const int* __restrict__ rep_off, int pt, const int64_t* __restrict__ witem_lo, const int64_t* __restrict__ witem_hi,
@@ -141,9 +141,9 @@ __global__ void __launch_bounds__(P2L_THREADS) p2l_kernel(
       if constexpr (sizeof(R) == 4) {
         if constexpr (NCS_PAIR_X2 != 0) {
           if (nact == P2L_NT)
-            pair_loop32x2<MODE, P2L_NT, POLY>(S, ns, ax, ay, az, part);
+            pair_loop32x2<MODE, P2L_NT, POLY, RSQ>(S, ns, ax, ay, az, part);
           else if (nact == 1)
-            pair_loop32x2<MODE, 1, POLY>(S, ns, ax, ay, az, part);
+            pair_loop32x2<MODE, 1, POLY, RSQ>(S, ns, ax, ay, az, part);
         } else {
           if (nact == P2L_NT)
             pair_loop32<MODE, P2L_NT>(S, ns, ax, ay, az, part);
@@ -247,7 +247,7 @@ constexpr int DT_JT = 8;
 // count within the tile's shared memory (an odd count only occurs in a partial tile)
 static_assert(P2L_JT % 2 == 0 && DT_JT % 2 == 0, "tile source counts must be even");
 
-template <typename R, int MODE, int POLY = NCS_PAIR_X2_POLY>
+template <typename R, int MODE, int POLY = NCS_PAIR_X2_POLY, int RSQ = 0>
 __global__ void __launch_bounds__(DT_THREADS) direct_list_kernel(
     int pt, int Kstar, int pmax, const int* __restrict__ rep_p, const int* __restrict__ rep_off,
     const int64_t* __restrict__ pd_off, const int* __restrict__ pd, const int* __restrict__ pdk,
@@ -323,7 +323,7 @@ __global__ void __launch_bounds__(DT_THREADS) direct_list_kernel(
     for (int t = 0; t < DT_NT; ++t) part[t] = 0;
     if constexpr (sizeof(R) == 4) {
       if constexpr (NCS_PAIR_X2 != 0)
-        pair_loop32x2<MODE, DT_NT, POLY>(S, ns, ax, ay, az, part);
+        pair_loop32x2<MODE, DT_NT, POLY, RSQ>(S, ns, ax, ay, az, part);
       else
         pair_loop32<MODE, DT_NT>(S, ns, ax, ay, az, part);
     } else {
@@ -1101,38 +1101,60 @@ static cudaError_t downward(const TreeDevice& t, cudaStream_t s) {
 // The FP32 pair kernels' run-time variants (KernelConfig): source patches per P2L tile
 // and the share of logarithms taken on the FMA pipe. Every variant has the same
 // parameters, so one pointer type serves them all.
+template <int MODE, int JT, int POLY>
+static auto p2l32_variant_rsq(int rsq) -> decltype(&p2l_kernel<float, MODE, JT, POLY, 0>) {
+  switch (rsq) {
+    case 0: return &p2l_kernel<float, MODE, JT, POLY, 0>;
+    case 4: return &p2l_kernel<float, MODE, JT, POLY, 4>;
+    case 8: return &p2l_kernel<float, MODE, JT, POLY, 8>;
+    default: return nullptr;
+  }
+}
+
 template <int MODE, int JT>
-static auto p2l32_variant(int poly) -> decltype(&p2l_kernel<float, MODE, JT, 0>) {
+static auto p2l32_variant(int poly, int rsq) -> decltype(&p2l_kernel<float, MODE, JT, 0, 0>) {
   switch (poly) {
-    case 0: return &p2l_kernel<float, MODE, JT, 0>;
-    case 2: return &p2l_kernel<float, MODE, JT, 2>;
-    case 4: return &p2l_kernel<float, MODE, JT, 4>;
-    case 6: return &p2l_kernel<float, MODE, JT, 6>;
+    case 0: return p2l32_variant_rsq<MODE, JT, 0>(rsq);
+    case 2: return p2l32_variant_rsq<MODE, JT, 2>(rsq);
+    case 4: return p2l32_variant_rsq<MODE, JT, 4>(rsq);
+    case 6: return p2l32_variant_rsq<MODE, JT, 6>(rsq);
     default: return nullptr;
   }
 }
 
 template <int MODE>
-static auto p2l32_variant(int jt, int poly) -> decltype(&p2l_kernel<float, MODE, 16, 0>) {
-  if (jt == 8) return p2l32_variant<MODE, 8>(poly);
-  if (jt == 16) return p2l32_variant<MODE, 16>(poly);
+static auto p2l32_variant(int jt, int poly, int rsq) -> decltype(&p2l_kernel<float, MODE, 16, 0, 0>) {
+  if (jt == 8) return p2l32_variant<MODE, 8>(poly, rsq);
+  if (jt == 16) return p2l32_variant<MODE, 16>(poly, rsq);
   return nullptr;
 }
 
+template <int MODE, int POLY>
+static auto direct32_variant_rsq(int rsq) -> decltype(&direct_list_kernel<float, MODE, POLY, 0>) {
+  switch (rsq) {
+    case 0: return &direct_list_kernel<float, MODE, POLY, 0>;
+    case 4: return &direct_list_kernel<float, MODE, POLY, 4>;
+    case 8: return &direct_list_kernel<float, MODE, POLY, 8>;
+    default: return nullptr;
+  }
+}
+
 template <int MODE>
-static auto direct32_variant(int poly) -> decltype(&direct_list_kernel<float, MODE, 0>) {
+static auto direct32_variant(int poly, int rsq) -> decltype(&direct_list_kernel<float, MODE, 0, 0>) {
   switch (poly) {
-    case 0: return &direct_list_kernel<float, MODE, 0>;
-    case 2: return &direct_list_kernel<float, MODE, 2>;
-    case 4: return &direct_list_kernel<float, MODE, 4>;
-    case 6: return &direct_list_kernel<float, MODE, 6>;
+    case 0: return direct32_variant_rsq<MODE, 0>(rsq);
+    case 2: return direct32_variant_rsq<MODE, 2>(rsq);
+    case 4: return direct32_variant_rsq<MODE, 4>(rsq);
+    case 6: return direct32_variant_rsq<MODE, 6>(rsq);
     default: return nullptr;
   }
 }
 
 bool kernel_config_valid(const KernelConfig& k) {
   const auto poly_ok = [](int p) { return p == 0 || p == 2 || p == 4 || p == 6; };
-  return (k.p2l_tile == 8 || k.p2l_tile == 16) && poly_ok(k.p2l_poly) && poly_ok(k.direct_poly);
+  const auto rsq_ok = [](int r) { return r == 0 || r == 4 || r == 8; };
+  return (k.p2l_tile == 8 || k.p2l_tile == 16) && poly_ok(k.p2l_poly) && poly_ok(k.direct_poly) &&
+         rsq_ok(k.p2l_rsq) && rsq_ok(k.direct_rsq);
 }
 
 template <typename R, int MODE>
@@ -1149,7 +1171,7 @@ static cudaError_t tree_field_impl(const DeviceData& dd, const TreeDevice& t, cu
     auto kern = &p2l_kernel<R, MODE>;
     int jt = P2L_JT;
     if constexpr (std::is_same<R, float>::value) {
-      kern = p2l32_variant<MODE>(t.cfg.p2l_tile, t.cfg.p2l_poly);
+      kern = p2l32_variant<MODE>(t.cfg.p2l_tile, t.cfg.p2l_poly, t.cfg.p2l_rsq);
       jt = t.cfg.p2l_tile;
       if (!kern) return cudaErrorInvalidValue;
     }
@@ -1169,7 +1191,7 @@ static cudaError_t tree_field_impl(const DeviceData& dd, const TreeDevice& t, cu
   {
     auto kern = &direct_list_kernel<R, MODE>;
     if constexpr (std::is_same<R, float>::value) {
-      kern = direct32_variant<MODE>(t.cfg.direct_poly);
+      kern = direct32_variant<MODE>(t.cfg.direct_poly, t.cfg.direct_rsq);
       if (!kern) return cudaErrorInvalidValue;
     }
     const size_t smem = (size_t)DT_JT * dd.pmax * sizeof(V4);

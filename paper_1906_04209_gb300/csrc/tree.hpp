@@ -30,6 +30,9 @@ struct KernelConfig {
   int p2l_poly = 4;     // of every 16 packed pair chains, how many take lg2 on the FMA pipe:
                         // 0, 2, 4 or 6 (the rest on the MUFU unit)
   int direct_poly = 4;  // the same for the direct lists
+  int p2l_rsq = 0;      // of every 16 chains, how many take the reciprocal square root by
+                        // Newton steps on the FMA pipe: 0, 4 or 8
+  int direct_rsq = 0;   // the same for the direct lists
 };
 bool kernel_config_valid(const KernelConfig& k);
 

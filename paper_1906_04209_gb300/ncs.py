@@ -46,7 +46,8 @@ class ncs_params(ctypes.Structure):
 
 class ncs_tuning(ctypes.Structure):
     _fields_ = [("p2l_tile", ctypes.c_int), ("p2l_poly", ctypes.c_int), ("direct_poly", ctypes.c_int),
-                ("item_patches", ctypes.c_int), ("l2p_weight", ctypes.c_double)]
+                ("item_patches", ctypes.c_int), ("l2p_weight", ctypes.c_double), ("p2l_rsq", ctypes.c_int),
+                ("direct_rsq", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

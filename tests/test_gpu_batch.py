@@ -68,3 +68,30 @@ def test_block_dots():
     ncs.block_dots(n, k, Vd.data_ptr(), n, wd.data_ptr(), out.data_ptr(), torch.cuda.current_stream().cuda_stream)
     ref = V @ w
     assert np.abs(out.cpu().numpy() - ref).max() <= 1e-12 * np.abs(V).max() * np.abs(w).max() * np.sqrt(n)
+
+
+def test_batch_workload_small_instances_vs_oracle():
+    """The 256-sphere batch workload (K = 128, uneven N and eps, both modes): every instance
+    with at most 60 patches (9 of them), solved by ncs_batch_solve with the library's own
+    precompute at reduced panels, against the oracle's GMRES on its own compressed
+    operator at the same settings (plain-C sums at every Zernike node)."""
+    from oracle import native
+    work = L.batch_workload(256)
+    sel = [(c, e, m) for c, e, m, _ in work if len(c) <= 60]
+    assert len(sel) == 9
+    K, kw = 128, dict(npan=8, nord=12, ntheta_fine=40, method=ncs.METHOD_DIRECT)
+    out = ncs.batch_solve(sel, K, tol=1e-10, precision=ncs.MIXED, workers=4, **kw)
+    assert out["rc"] == 0 and (out["status"] == 0).all()
+    for b, (c, eps, mode) in enumerate(sel):
+        pre = O.make_precompute(eps, mode, K, npan=8, nord=12, ntheta=40, tau=1e-11)
+        N = len(c)
+        pt, nd = np.repeat(np.arange(N), pre.Kstar), np.tile(np.arange(pre.Kstar), N)
+
+        def matvec(x):
+            return x + (native.rows(pre, c, x, pt, nd).reshape(N, pre.Kstar) @ pre.P.T).ravel()
+
+        x, _, _, true = S.gmres(matvec, O.rhs(pre, N), 1e-12)
+        Is, val = S.outputs(pre.op.I, x, N, mode)
+        print(f"instance N={N} eps={eps:.4f} mode {mode}: library {out['scalar'][b]:.12f}, oracle {val:.12f}")
+        assert abs(out["scalar"][b] - val) <= 1e-8 * abs(val)
+        assert out["relres"][b] <= 1e-10

@@ -182,11 +182,13 @@ def test_tuning_validation(libncs):
     """ncs_set_tuning accepts the documented ranges only; ncs_tune needs patches first."""
     c = ncs.Context(0.05, INTERIOR, 10, npan=6, nord=10, ntheta_fine=24)
     t0 = c.get_tuning()
-    assert t0 == dict(p2l_tile=16, p2l_poly=4, direct_poly=4, item_patches=16, l2p_weight=0.1)
-    c.set_tuning(p2l_tile=8, p2l_poly=2, direct_poly=6, item_patches=32, l2p_weight=0.2)
-    assert c.get_tuning() == dict(p2l_tile=8, p2l_poly=2, direct_poly=6, item_patches=32, l2p_weight=0.2)
+    assert t0 == dict(p2l_tile=16, p2l_poly=4, direct_poly=4, item_patches=16, l2p_weight=0.1, p2l_rsq=0,
+                      direct_rsq=0)
+    c.set_tuning(p2l_tile=8, p2l_poly=2, direct_poly=6, item_patches=32, l2p_weight=0.2, p2l_rsq=4, direct_rsq=8)
+    assert c.get_tuning() == dict(p2l_tile=8, p2l_poly=2, direct_poly=6, item_patches=32, l2p_weight=0.2,
+                                  p2l_rsq=4, direct_rsq=8)
     for bad in (dict(p2l_tile=12), dict(p2l_poly=3), dict(direct_poly=8), dict(item_patches=4),
-                dict(p2l_tile=16, item_patches=24), dict(l2p_weight=0.0)):
+                dict(p2l_tile=16, item_patches=24), dict(l2p_weight=0.0), dict(p2l_rsq=2), dict(direct_rsq=6)):
         with pytest.raises(ncs.NcsError) as e:
             c.set_tuning(**bad)
         assert e.value.code == ncs.NCS_E_INPUT
