@@ -9,7 +9,8 @@ the second-kind system (outgoing map, P2L onto incoming grids, direct sums, L2P,
 Zernike transform) in the FP32 kernels that the mixed-precision solve iterates with.
 The line also reports the FP64 and float-float product rates, the metric's solves to a
 1e-8 relative residual (mixed, float-float and plain FP64, each with its recomputed true
-residual and the density error against the FP64 solution) and the 256-sphere batch.
+residual and the density error against the FP64 solution), the 256-sphere batch, and the
+mixed solves of the other N = 1e5 workloads (exterior, and 20 von Mises-Fisher clusters).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
     torchrun --nproc-per-node N bench.py --gpus N ...   (independent replicas)
@@ -39,10 +40,11 @@ FLOPS_PER_PAIR = 20
 
 
 # DRAM bytes per pair of the FP32 P2L kernel: dram__bytes_read.sum + dram__bytes_write.sum
-# of one launch (170.2 + 15.5 MB) over its 1.5108e10 pairs, ncu capture of the packed pair
-# loop at N = 2e4 of the same layout family; the reads scale with the work items. Valid for
-# the launch configuration that was captured (reported as null for any other).
-P2L_CAPTURE = {"p2l_tile": 16, "p2l_poly": 4, "bytes_per_pair": 185.7e6 / 1.5108e10}
+# of one launch (169.9 + 15.5 MB) over its 1.4535e10 pairs, ncu capture of the packed pair
+# loop at N = 2e4 of the same layout family (profiles/p2l_kernel_fp32_N2e4.md); the reads scale
+# with the work items. Valid for the launch configuration that was captured (reported as null
+# for any other).
+P2L_CAPTURE = {"p2l_tile": 16, "p2l_poly": 2, "p2l_rsq": 0, "bytes_per_pair": 185.4e6 / 1.4535e10}
 
 
 _T0 = time.time()
@@ -51,6 +53,15 @@ _T0 = time.time()
 def _progress(msg):
     """One line per leg on stderr (the JSON line stays alone on stdout)."""
     print(f"[bench +{time.time() - _T0:.1f}s] {msg}", file=sys.stderr, flush=True)
+
+
+def _workload_name(args, N):
+    """The workload line: the metric's configuration, or the variant the flags select."""
+    if args.mode == "interior" and args.layout == "fibonacci" and N == 100000:
+        return WORKLOAD
+    lay = "jittered Fibonacci layout" if args.layout == "fibonacci" else "20 von Mises-Fisher clusters (kappa=50)"
+    kind = "interior narrow escape" if args.mode == "interior" else "exterior narrow capture"
+    return f"{kind}, N={N} patches, eps=0.001, K=136, {lay}, cube-sphere tree"
 
 
 def _dist():
@@ -147,6 +158,8 @@ def run_ours(args):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     centres, eps, mode, K = L.workload(3, layout=args.layout, N=args.patches)
+    if args.mode == "exterior":
+        mode = ncs.EXTERIOR
     N = len(centres)
     t0 = time.time()
     ctx = ncs.Context(eps, mode, K, method=ncs.METHOD_TREE, grid_tol=args.grid_tol, tensor_cores=args.tensor_cores)
@@ -255,6 +268,7 @@ def run_ours(args):
         solve = solve_legs(args, ctx, N, K, sp)
 
     batch = batch_leg(args) if (args.batch and rank == 0) else None
+    others = other_workloads_leg(args) if (args.other_workloads and rank == 0 and args.patches is None) else None
 
     peaks, src = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
@@ -282,7 +296,7 @@ def run_ours(args):
         # same family measured 156.0 MB for 1.5108e10 pairs; the P2L reads scale with its
         # work items, so it is scaled by the pair ratio (null for other precisions)
         "traffic": (round(P2L_CAPTURE["bytes_per_pair"] * p2l_pairs)
-                    if prec == ncs.FP32 and all(tuned_cfg[k] == P2L_CAPTURE[k] for k in ("p2l_tile", "p2l_poly"))
+                    if prec == ncs.FP32 and all(tuned_cfg[k] == P2L_CAPTURE[k] for k in ("p2l_tile", "p2l_poly", "p2l_rsq"))
                     else None),
         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum at N=2e4, scaled by pairs",
         "pairs_per_launch": p2l_pairs,
@@ -300,7 +314,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == ncs.FP32 else "f64",
         "data": "synthetic (seeded layout, random Gaussian input vector)",
-        "config": {"workload": WORKLOAD, "N": N, "eps": eps, "K": K, "mode": "interior",
+        "config": {"workload": _workload_name(args, N), "N": N, "eps": eps, "K": K, "mode": args.mode,
                    "layout": args.layout, "p": info["p"], "Kstar": info["Kstar"], "levels": tstats["levels"],
                    "grid_tol": args.grid_tol, "tensor_cores": args.tensor_cores, "parallelism": "replicas" if ws > 1 else "single",
                    "l2": "working set > L2 (skeleton offsets 200 MB, z 397 MB, grids per step)",
@@ -320,6 +334,7 @@ def run_ours(args):
         "tuning": tuning,
         "solve": solve,
         "batch": batch,
+        "other_workloads": others,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -393,6 +408,55 @@ def solve_legs(args, ctx, N, K, sp):
     t0 = time.time()
     l2 = ctx.patch_residual(ip, fh["mixed"])
     out["mixed"]["patch_residual"] = {"patch": ip, "l2": l2, "seconds": round(time.time() - t0, 3)}
+    return out
+
+
+def other_workloads_leg(args):
+    """The other N = 1e5 workloads of the metric's family (eps = 0.001, K = 136): exterior on
+    the jittered Fibonacci layout, interior and exterior on 20 von Mises-Fisher clusters. Each
+    gets its own context, tree and tuned launch configuration; reported: FP32 product time
+    (CUDA events, 5 products after 2 warm-up) and the mixed solve to args.solve_tol with its
+    true residual recomputed by a float-float product outside the timed region."""
+    import torch
+
+    from paper_1906_04209_gb300 import layouts as L, ncs
+    out = {}
+    for layout, mode in (("fibonacci", ncs.EXTERIOR), ("vmf", ncs.INTERIOR), ("vmf", ncs.EXTERIOR)):
+        name = f"{'exterior' if mode == ncs.EXTERIOR else 'interior'}_{layout}"
+        _progress(f"workload {name}")
+        c, eps, _, K = L.workload(3, layout=layout)
+        N = len(c)
+        ctx = ncs.Context(eps, mode, K, method=ncs.METHOD_TREE)
+        ctx.set_patches(c)
+        cfg, rep = ctx.tune(flags=1)  # the pair-kernel variants (no tree rebuilds)
+        x = torch.randn(N * K, dtype=torch.float64, device="cuda")
+        y = torch.empty_like(x)
+        sp = torch.cuda.current_stream().cuda_stream
+        for _ in range(2):
+            ctx.matvec_dev(x.data_ptr(), y.data_ptr(), ncs.FP32, sp)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(5):
+            ctx.matvec_dev(x.data_ptr(), y.data_ptr(), ncs.FP32, sp)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 5
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = ctx.solve(tol=args.solve_tol, precision=ncs.MIXED, want_fhat=True, allow_noconv=True)
+        sec = time.perf_counter() - t0
+        P = ctx.operator()["P"]
+        b = torch.tensor(np.tile(P.sum(axis=1), N), dtype=torch.float64, device="cuda")
+        xd = torch.from_numpy(r["fhat"]).to("cuda")
+        ctx.matvec_dev(xd.data_ptr(), y.data_ptr(), ncs.DF64, sp)
+        torch.cuda.synchronize()
+        true = float(torch.linalg.norm(b - y) / torch.linalg.norm(b))
+        st = ctx.tree_stats()
+        out[name] = {"N": N, "levels": st["levels"], "pairs_per_product": st["p2l_pairs"] + st["direct_pairs"],
+                     "tuning": cfg, "ms_per_product": round(ms, 3), "mixed_solve_s": round(sec, 3),
+                     "iterations": r["iterations"], "scalar": r["scalar"], "relres_true": true, "rc": r["rc"]}
+        del x, y, xd, b
+        ctx.close()
     return out
 
 
@@ -472,6 +536,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--layout", default="fibonacci", choices=["fibonacci", "vmf"])
+    ap.add_argument("--mode", default="interior", choices=["interior", "exterior"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--grid-tol", type=float, default=1e-8)
     ap.add_argument("--fp64-steps", type=int, default=1)
@@ -480,6 +545,7 @@ def main():
     ap.add_argument("--solve-tol", type=float, default=1e-8)
     ap.add_argument("--no-batch", dest="batch", action="store_false")
     ap.add_argument("--no-tune", dest="tune", action="store_false")
+    ap.add_argument("--no-other-workloads", dest="other_workloads", action="store_false")
     # a fixed launch configuration instead of tuning (profiler captures of a chosen variant)
     ap.add_argument("--set-tuning", default=None, help="comma-separated key=value, e.g. p2l_poly=2,direct_poly=2")
     ap.add_argument("--batch-size", type=int, default=256)

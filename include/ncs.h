@@ -75,7 +75,9 @@ typedef struct ncs_params {
   int threads;         /* host threads for the precompute and the tree set-up; 0 = all */
   double grid_tol;     /* incoming-grid tolerance (Section 7.3), default 1e-8 */
   int method;          /* NCS_METHOD_*, default AUTO */
-  int tree_min_patches;/* AUTO switches to the tree at this N, default 2000 */
+  int tree_min_patches;/* AUTO switches to the tree at this N, default 128 (on GB300 the tree
+                          product is faster from N ~ 200: 0.36 vs 0.49 ms at N = 200, 1.6 vs
+                          17.9 ms at N = 2000, K = 128) */
   int gmres_maxit;     /* GMRES iteration cap, default 200 */
   int verbose;         /* 0 silent .. 3 chatty (stderr) */
   int mixed_residual;  /* precision of the refinement residual of NCS_MIXED:
@@ -108,6 +110,10 @@ typedef struct ncs_params {
                           capture runs, no other host thread may synchronise the whole
                           device (cudaDeviceSynchronize, or calls that imply it): with
                           contexts driven from several threads set 0 (ncs_batch_solve does) */
+  int batch_ladder_by_n; /* ncs_batch_solve only. 1 (default): each sphere's ID ladder extent is
+                          min(id_ladder_max, 0 below 1000 patches, 0.1 rad below 3000, else
+                          1.0 rad), the measured balance between the precompute (one more
+                          representation per rung) and its products; 0: id_ladder_max for all */
 } ncs_params;
 
 /* Fills *p with the defaults listed above. */

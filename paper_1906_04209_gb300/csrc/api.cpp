@@ -618,6 +618,18 @@ void tune_cache_store(const char* path, const std::string& key, const ncs_tuning
   std::fclose(f);
 }
 
+// Far-field extent of the ID ladder for one sphere of a batch, from its patch count: every
+// extra representation costs one sketch CPQR and T assembly in the precompute (~10 ms of FP64
+// device work each at K = 128) and saves pair evaluations in every product. Measured on GB300
+// (K = 128, mixed solve to 1e-8, precompute + solve seconds for ladder extents 0 / 0.1 / 1.0):
+// N = 200: 0.16 / 0.24 / 0.30; N = 700: 0.24 / 0.27 / 0.32; N = 2000: 0.46 / 0.35 / 0.37;
+// N = 5000: 1.14 / 0.53 / 0.52. Hence no ladder below 1000 patches, a short one below 3000.
+double batch_ladder_extent(int64_t N) {
+  if (N < 1000) return 0.0;
+  if (N < 3000) return 0.1;
+  return 1.0;
+}
+
 }  // namespace
 
 extern "C" {
@@ -631,7 +643,7 @@ void ncs_default_params(ncs_params* p) {
   p->threads = 0;
   p->grid_tol = 1e-8;
   p->method = NCS_METHOD_AUTO;
-  p->tree_min_patches = 2000;
+  p->tree_min_patches = 128;
   p->gmres_maxit = 200;
   p->verbose = 0;
   p->mixed_residual = NCS_DF64;
@@ -640,6 +652,7 @@ void ncs_default_params(ncs_params* p) {
   p->id_ladder_max = 1.0;
   p->device_precompute = 1;
   p->cuda_graphs = 1;
+  p->batch_ladder_by_n = 1;
 }
 
 int ncs_create(double eps, int mode, int K, const ncs_params* params, ncs_ctx** out) {
@@ -1488,7 +1501,9 @@ int ncs_batch_solve(int B, const double* eps, const int* mode, const int64_t* N,
       if (b >= B) break;
       const auto a0 = std::chrono::steady_clock::now();
       ncs_ctx* c = nullptr;
-      int rc = ncs_create(eps[b], mode[b], K, &prm, &c);
+      ncs_params pb = prm;
+      if (prm.batch_ladder_by_n) pb.id_ladder_max = std::min(prm.id_ladder_max, batch_ladder_extent(N[b]));
+      int rc = ncs_create(eps[b], mode[b], K, &pb, &c);
       if (rc == NCS_OK) rc = ncs_set_patches(c, N[b], centres[b]);
       const auto a1 = std::chrono::steady_clock::now();
       double sc = 0.0, is = 0.0, rr = 0.0;
