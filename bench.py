@@ -44,7 +44,7 @@ FLOPS_PER_PAIR = 20
 # loop at N = 2e4 of the same layout family (profiles/p2l_kernel_fp32_N2e4.md); the reads scale
 # with the work items. Valid for the launch configuration that was captured (reported as null
 # for any other).
-P2L_CAPTURE = {"p2l_tile": 16, "p2l_poly": 2, "p2l_rsq": 0, "bytes_per_pair": 185.4e6 / 1.4535e10}
+P2L_CAPTURE = {"p2l_tile": 16, "item_patches": 16, "bytes_per_pair": 185.4e6 / 1.4535e10}
 
 
 _T0 = time.time()
@@ -273,15 +273,17 @@ def run_ours(args):
     peaks, src = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     # ALU roofline of the pair kernel: per pair the FP32 path issues mufu_per_pair MUFU
-    # ops (rsqrt, and log2 for the pairs whose logarithm is not taken on the FMA pipe);
-    # 152 SMs x 16 MUFU/clk cap it at 16 / mufu_per_pair pairs/clk/SM. Two fixed bounds are
-    # reported beside it: the joint MUFU + FMA-pipe bound over every share s of polynomial
-    # logarithms (9 FP32 operations per pair plus 11 per polynomial log2 on 128 FMA lanes:
-    # 16 / (2 - s) = 128 / (9 + 11 s) at s = 112/304, 9.80 pairs/clk/SM), and the FP32 pipe
-    # at the nominal 20 flops per pair (128 lanes x 2 flops per clock).
+    # ops (an rsqrt unless the pair takes the Newton reciprocal square root on the FMA pipe,
+    # a lg2 unless it takes the polynomial logarithm there); 152 SMs x 16 MUFU/clk cap it at
+    # 16 / mufu_per_pair pairs/clk/SM. Two fixed bounds are reported beside it: the joint
+    # MUFU + FMA-pipe bound over every share of the two offloads (9 FP32 operations per pair,
+    # plus 7 per Newton rsqrt and 11 per polynomial log2, on 128 FMA lanes; the cheaper
+    # rsqrt share b balances the pipes first: 16 / (2 - b) = 128 / (9 + 7 b) at b = 112/240,
+    # 10.43 pairs/clk/SM), and the FP32 pipe at the nominal 20 flops per pair (128 lanes x 2
+    # flops per clock).
     tuned_cfg = ctx.get_tuning()
-    poly = tuned_cfg["p2l_poly"]
-    mufu_per_pair = 2.0 - poly / 16.0
+    poly, rsq = tuned_cfg["p2l_poly"], tuned_cfg["p2l_rsq"]
+    mufu_per_pair = 2.0 - (poly + rsq) / 16.0
     pair_peak = 152 * (16.0 / mufu_per_pair) * sm_max * 1e6 if prec == ncs.FP32 else None
     p2l_pairs = tstats["p2l_pairs"]
     achieved_pairs = p2l_pairs / (p2l_avg / 1000.0)
@@ -293,17 +295,19 @@ def run_ours(args):
         "unit": "TFLOP/s",
         "frac": round(achieved_pairs / pair_peak, 4) if pair_peak else None,
         # DRAM bytes per launch: an ncu capture of this kernel on the N = 2e4 layout of the
-        # same family measured 156.0 MB for 1.5108e10 pairs; the P2L reads scale with its
-        # work items, so it is scaled by the pair ratio (null for other precisions)
+        # same family (P2L_CAPTURE), scaled by the pair ratio; the arithmetic variants
+        # (polynomial log, Newton rsqrt shares) move no data, so only the staging (patches per
+        # tile and per work item) must match the capture (null otherwise and for other
+        # precisions)
         "traffic": (round(P2L_CAPTURE["bytes_per_pair"] * p2l_pairs)
-                    if prec == ncs.FP32 and all(tuned_cfg[k] == P2L_CAPTURE[k] for k in ("p2l_tile", "p2l_poly", "p2l_rsq"))
+                    if prec == ncs.FP32 and all(tuned_cfg[k] == P2L_CAPTURE[k] for k in ("p2l_tile", "item_patches"))
                     else None),
         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum at N=2e4, scaled by pairs",
         "pairs_per_launch": p2l_pairs,
         "ms_per_launch": round(p2l_avg, 3),
         "peak_source": "derived: 152 SMs x 16 MUFU/clk / %g MUFU per pair x %g MHz (%s clocks)" % (
             mufu_per_pair, sm_max, src),
-        "frac_joint_mufu_fma": (round(achieved_pairs / (152 * (16.0 / (2.0 - 112.0 / 304.0)) * sm_max * 1e6), 4)
+        "frac_joint_mufu_fma": (round(achieved_pairs / (152 * (16.0 / (2.0 - 112.0 / 240.0)) * sm_max * 1e6), 4)
                                 if prec == ncs.FP32 else None),
         "frac_fp32_pipe": (round(achieved_pairs * FLOPS_PER_PAIR / (152 * 256 * sm_max * 1e6), 4)
                            if prec == ncs.FP32 else None),
