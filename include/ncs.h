@@ -114,6 +114,11 @@ typedef struct ncs_params {
                           min(id_ladder_max, 0 below 1000 patches, 0.1 rad below 3000, else
                           1.0 rad), the measured balance between the precompute (one more
                           representation per rung) and its products; 0: id_ladder_max for all */
+  int batch_grouped;     /* ncs_batch_solve with NCS_MIXED only. 1 (default): spheres with fewer
+                          than tree_min_patches patches (and method not NCS_METHOD_TREE) are
+                          solved together, one concatenated system per mode with one launch per
+                          product stage and Krylov step for all of them (each keeps its own
+                          eps, operator and GMRES state); 0: each on its own context */
 } ncs_params;
 
 /* Fills *p with the defaults listed above. */
@@ -436,6 +441,10 @@ int ncs_tc_gemm_f32(int64_t rows, int cols, int kdim, const float* A, const floa
  * run the precompute and tree set-up for it on one host core, solve it on the GPU on
  * its own stream, and release it, so set-up, transfers and GPU work of different
  * instances overlap and at most `workers` instances hold device memory at once.
+ * With params->batch_ladder_by_n each sphere's ID ladder extent follows its patch count;
+ * with params->batch_grouped (NCS_MIXED only) the spheres below tree_min_patches are set
+ * up by the workers and then solved together on the calling thread, one grouped system per
+ * mode (direct products, the mixed refinement of ncs_solve per instance in lock step).
  * centres[b] points to N[b] x 3 host doubles. Per-instance outputs (each may be NULL):
  * scalar (mu or C), I_sigma, iterations, relres, status (NCS_OK or the instance's error
  * code). seconds (may be NULL): [set-up summed over instances, solve summed over

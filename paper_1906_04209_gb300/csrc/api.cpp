@@ -9,6 +9,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <exception>
+#include <memory>
+#include <mutex>
 #include <new>
 #include <string>
 #include <atomic>
@@ -630,6 +632,307 @@ double batch_ladder_extent(int64_t N) {
   return 1.0;
 }
 
+// ---- grouped solve of small spheres (ncs_batch_solve). Spheres with few patches keep
+// only a few hundred blocks busy per product and spend most of a solve in launch latency;
+// a group of them (common K and mode) is solved as one concatenated system whose products,
+// Krylov steps and refinement sweeps each take one launch per stage for all instances.
+
+struct GroupResult {
+  double scalar = 0.0, Is = 0.0, rel = 1.0;
+  int iters = 0;
+  int status = NCS_OK;
+};
+
+// Device buffers of one group, freed together.
+struct GroupStore {
+  std::vector<void*> ptrs;
+  template <typename T>
+  T* up(const std::vector<T>& h) {
+    T* p = dev_upload(h);
+    ptrs.push_back(p);
+    return p;
+  }
+  template <typename T>
+  T* alloc(size_t n) {
+    T* p = dev_alloc<T>(n);
+    ptrs.push_back(p);
+    return p;
+  }
+  ~GroupStore() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+};
+
+// Patch frame of unit centre c on the host (the frame of the device kernels).
+void host_frame(const double* c, double* e1, double* e2) {
+  e1[0] = -c[1];
+  e1[1] = c[0];
+  e1[2] = 0.0;
+  const double na2 = e1[0] * e1[0] + e1[1] * e1[1];
+  if (na2 >= 1e-24) {
+    const double inv = 1.0 / std::sqrt(na2);
+    e1[0] *= inv;
+    e1[1] *= inv;
+  } else {
+    e1[0] = 1.0;
+    e1[1] = 0.0;
+  }
+  e2[0] = c[1] * e1[2] - c[2] * e1[1];
+  e2[1] = c[2] * e1[0] - c[0] * e1[2];
+  e2[2] = c[0] * e1[1] - c[1] * e1[0];
+}
+
+// Solves the instances cs (same K and mode, direct products) by the mixed scheme of
+// ncs_solve: FP32 inner GMRES for every instance still refining, in lock step, then the
+// residual b - A x recomputed at prm.mixed_residual precision; an instance leaves the
+// sweep once its residual meets tol or stops decreasing. Per-instance results in res.
+void group_solve(const std::vector<ncs_ctx*>& cs, double tol, cudaStream_t s, std::vector<GroupResult>& res) {
+  const int B = (int)cs.size();
+  const ncs::Precomputed& pc0 = cs[0]->pc;
+  const int K = pc0.K, Kstar = pc0.Kstar, mode = pc0.mode;
+  const ncs_params& prm = cs[0]->prm;
+  const int maxit = prm.gmres_maxit;
+  res.assign(B, GroupResult{});
+  // host tables
+  std::vector<int64_t> pbase(B + 1, 0), tt_off(B), roff;
+  std::vector<int> pinst, ptot(B), nrep(B), repbase(B), rep_p, rep_off;
+  std::vector<double> rep_rho, ieps(B), zloc, I, centres;
+  std::vector<double> TT;
+  int pmax = 1;
+  int64_t maxseg = 1;
+  for (int b = 0; b < B; ++b) {
+    const ncs_ctx* c = cs[b];
+    const ncs::Precomputed& pc = c->pc;
+    if (pc.K != K || pc.Kstar != Kstar || pc.mode != mode) throw Fail{NCS_E_INPUT, "group: mixed K or mode"};
+    const int64_t N = (int64_t)(c->centres.size() / 3);
+    pbase[b + 1] = pbase[b] + N;
+    maxseg = std::max<int64_t>(maxseg, N * K);
+    ieps[b] = pc.eps;
+    nrep[b] = (int)pc.reps.size();
+    repbase[b] = (int)rep_p.size();
+    int pt = 0;
+    for (const auto& r : pc.reps) {
+      rep_p.push_back(r.p);
+      rep_off.push_back(pt);
+      rep_rho.push_back(r.rho_min);
+      pt += r.p;
+      pmax = std::max(pmax, r.p);
+    }
+    ptot[b] = pt;
+    tt_off[b] = (int64_t)TT.size();
+    TT.resize(TT.size() + (size_t)K * pt);
+    double* Tb = TT.data() + tt_off[b];
+    for (const auto& r : pc.reps) {
+      const int o = rep_off[repbase[b] + (int)(&r - pc.reps.data())];
+      for (int m = 0; m < r.p; ++m)
+        for (int k = 0; k < K; ++k) Tb[(size_t)k * pt + o + m] = r.T[(size_t)m * K + k];
+    }
+    zloc.insert(zloc.end(), pc.zloc.begin(), pc.zloc.end());
+    I.insert(I.end(), pc.I.begin(), pc.I.end());
+    centres.insert(centres.end(), c->centres.begin(), c->centres.end());
+    for (int64_t i = 0; i < N; ++i) pinst.push_back(b);
+  }
+  const int64_t P = pbase[B];
+  const int64_t n = P * K;
+  // coefficient offsets and skeleton offsets (global frame) of every patch
+  roff.resize(P);
+  int64_t R = 0;
+  for (int64_t i = 0; i < P; ++i) {
+    roff[i] = R;
+    R += ptot[pinst[i]];
+  }
+  std::vector<double> soff(3 * (size_t)R);
+  for (int64_t i = 0; i < P; ++i) {
+    const ncs::Precomputed& pc = cs[pinst[i]]->pc;
+    const double* c = &centres[3 * i];
+    double e1[3], e2[3];
+    host_frame(c, e1, e2);
+    int64_t q = roff[i];
+    for (const auto& r : pc.reps)
+      for (int m = 0; m < r.p; ++m, ++q) {
+        const double* o = &r.sloc[3 * (size_t)m];
+        for (int a = 0; a < 3; ++a) soff[3 * q + a] = o[0] * e1[a] + o[1] * e2[a] + o[2] * c[a];
+      }
+  }
+  std::vector<double> PT((size_t)Kstar * K);
+  for (int j = 0; j < K; ++j)
+    for (int q = 0; q < Kstar; ++q) PT[(size_t)q * K + j] = pc0.P[(size_t)j * Kstar + q];
+  std::vector<float> lt(4 * 64);
+  for (int i = 0; i < 64; ++i) {
+    const double ci = 1.0 + (i + 0.5) / 64.0;
+    const double L = std::log(ci), inv = 1.0 / ci;
+    lt[4 * i + 0] = (float)L;
+    lt[4 * i + 1] = (float)(L - (double)(float)L);
+    lt[4 * i + 2] = (float)inv;
+    lt[4 * i + 3] = (float)(inv - (double)(float)inv);
+  }
+  GroupStore st;
+  ncs::GroupDev g;
+  g.B = B;
+  g.K = K;
+  g.Kstar = Kstar;
+  g.mode = mode;
+  g.maxit = maxit;
+  g.pmax = pmax;
+  g.seg_blocks = ncs::group_seg_blocks(maxseg);
+  g.P = P;
+  g.pinst = st.up(pinst);
+  g.pbase = st.up(pbase);
+  g.roff = st.up(roff);
+  g.inst_ptot = st.up(ptot);
+  g.tt_off = st.up(tt_off);
+  g.inst_eps = st.up(ieps);
+  g.inst_nrep = st.up(nrep);
+  g.inst_repbase = st.up(repbase);
+  g.rep_p = st.up(rep_p);
+  g.rep_off = st.up(rep_off);
+  g.rep_rho = st.up(rep_rho);
+  g.zloc = st.up(zloc);
+  g.centres = st.up(centres);
+  g.soff64 = st.up(soff);
+  g.soff32 = st.up(std::vector<float>(soff.begin(), soff.end()));
+  g.rho64 = st.alloc<double>(R);
+  g.rho32 = st.alloc<float>(R);
+  g.TT64 = st.up(TT);
+  g.TT32 = st.up(std::vector<float>(TT.begin(), TT.end()));
+  g.z = st.alloc<double>((size_t)P * Kstar);
+  g.I = st.up(I);
+  g.logtab = reinterpret_cast<const float4*>(st.up(lt));
+  const size_t m1 = (size_t)maxit + 1;
+  g.st = reinterpret_cast<ncs::GmresState*>(st.alloc<double>(B * ((sizeof(ncs::GmresState) + 7) / 8)));
+  g.H = st.alloc<double>(B * m1 * maxit);
+  g.cs = st.alloc<double>((size_t)B * maxit);
+  g.sn = st.alloc<double>((size_t)B * maxit);
+  g.g = st.alloc<double>(B * m1);
+  g.y = st.alloc<double>((size_t)B * maxit);
+  g.h1 = st.alloc<double>(B * m1);
+  g.h2 = st.alloc<double>(B * m1);
+  g.pnorm = st.alloc<double>((size_t)B * g.seg_blocks);
+  g.vk = st.alloc<double>(n);
+  // the Zernike transform y = x + P z of ncs_solve's product (P is common to the group)
+  DeviceData dd;
+  dd.N = P;
+  dd.K = K;
+  dd.Kstar = Kstar;
+  dd.z = g.z;
+  dd.PT64 = st.up(PT);
+  dd.PT32 = st.up(std::vector<float>(PT.begin(), PT.end()));
+  double* V = st.alloc<double>(m1 * n);
+  double* work = st.alloc<double>(5 * (size_t)n);
+  double *bv = work, *x = work + n, *r = work + 2 * n, *corr = work + 3 * n, *w = work + 4 * n;
+  double* dsc = st.alloc<double>(B);  // per-instance scalars (dots, scale factors)
+  ncs::GmresState* sth = nullptr;
+  CU(cudaHostAlloc((void**)&sth, B * sizeof(ncs::GmresState), cudaHostAllocDefault));
+  std::unique_ptr<ncs::GmresState, decltype(&cudaFreeHost)> sth_guard(sth, &cudaFreeHost);
+  std::vector<double> hb(B);
+  auto seg_dots = [&](const double* a, const double* c2) {
+    CU(ncs::launch_group_dots(g, a, c2, dsc, s));
+    CU(cudaMemcpyAsync(hb.data(), dsc, B * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    return hb;
+  };
+  auto product = [&](const double* in, double* out, int prec) {
+    CU(ncs::launch_group_field(g, in, prec, s));
+    CU(ncs::launch_apply_P(dd, in, out, prec, s));
+  };
+  // right-hand side b_i = P 1 (eq. opinteqnsdisc)
+  {
+    std::vector<double> P1(K, 0.0);
+    for (int j = 0; j < K; ++j)
+      for (int q = 0; q < Kstar; ++q) P1[j] += pc0.P[(size_t)j * Kstar + q];
+    std::vector<double> bh((size_t)n);
+    for (int64_t i = 0; i < P; ++i) std::memcpy(&bh[(size_t)i * K], P1.data(), K * sizeof(double));
+    CU(cudaMemcpyAsync(bv, bh.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
+  }
+  std::vector<double> bnorm = seg_dots(bv, bv);
+  for (double& v : bnorm) v = std::sqrt(v);
+  CU(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+  CU(cudaMemcpyAsync(r, bv, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  std::vector<char> active(B, 1);
+  // inner FP32 GMRES (x0 = 0, no restart) of every active instance for A corr = r
+  auto inner = [&]() {
+    std::vector<double> beta = seg_dots(r, r);
+    std::vector<double> scale(B, 0.0);
+    for (int b = 0; b < B; ++b) {
+      beta[b] = std::sqrt(beta[b]);
+      const bool run = active[b] && std::isfinite(beta[b]) && beta[b] > 0.0;
+      const double itol = std::min(std::max(0.3 * tol / res[b].rel, 3e-6), 0.5);
+      sth[b] = ncs::GmresState{0, run ? 0 : 1, run ? ncs::kGmresRunning : ncs::kGmresConverged, maxit,
+                               run ? beta[b] : 1.0, itol, run ? 1.0 : 0.0, 0.0};
+      scale[b] = run ? 1.0 / beta[b] : 0.0;
+      if (active[b] && !std::isfinite(beta[b])) {
+        res[b].status = NCS_E_NUMERIC;
+        active[b] = 0;
+      }
+    }
+    CU(cudaMemcpyAsync(g.st, sth, B * sizeof(ncs::GmresState), cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(dsc, scale.data(), B * sizeof(double), cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(V, r, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CU(ncs::launch_group_scale(g, dsc, V, s));
+    CU(cudaMemcpyAsync(g.vk, V, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CU(cudaStreamSynchronize(s));
+    for (int step = 0; step < maxit; ++step) {
+      std::vector<char> running(B);
+      bool any = false;
+      for (int b = 0; b < B; ++b) any |= (running[b] = !sth[b].done);
+      if (!any) break;
+      product(g.vk, w, NCS_FP32);
+      CU(ncs::launch_group_arnoldi(g, V, w, s));
+      CU(cudaMemcpyAsync(sth, g.st, B * sizeof(ncs::GmresState), cudaMemcpyDeviceToHost, s));
+      CU(cudaStreamSynchronize(s));
+      for (int b = 0; b < B; ++b) res[b].iters += running[b];
+    }
+    for (int b = 0; b < B; ++b)
+      if (active[b] && (sth[b].flag == ncs::kGmresNonFinite || (sth[b].flag == ncs::kGmresBreakdown && sth[b].m == 0))) {
+        res[b].status = NCS_E_NUMERIC;
+        active[b] = 0;
+      }
+    CU(ncs::launch_group_solution(g, V, corr, s));
+  };
+  for (int outer = 0; outer < 20; ++outer) {
+    bool any = false;
+    for (int b = 0; b < B; ++b) {
+      if (active[b] && res[b].rel <= tol) active[b] = 0;
+      any |= (bool)active[b];
+    }
+    if (!any) break;
+    inner();
+    // instances that ran no step (inactive) have corr = 0 on their segment
+    CU(ncs::launch_axpby(n, 1.0, corr, 1.0, x, s));
+    product(x, r, prm.mixed_residual);
+    CU(ncs::launch_axpby(n, 1.0, bv, -1.0, r, s));
+    const std::vector<double> rr = seg_dots(r, r);
+    for (int b = 0; b < B; ++b) {
+      if (!active[b]) continue;
+      ++res[b].iters;
+      const double newrel = std::sqrt(rr[b]) / bnorm[b];
+      if (!std::isfinite(newrel)) {
+        res[b].status = NCS_E_NUMERIC;
+        active[b] = 0;
+        continue;
+      }
+      const bool stalled = newrel > 0.9 * res[b].rel && outer > 0;
+      res[b].rel = newrel;
+      if (stalled) active[b] = 0;
+    }
+    if (log_level() > 0) {
+      int left = 0;
+      for (int b = 0; b < B; ++b) left += active[b];
+      std::fprintf(stderr, "ncs: group refinement %d: %d of %d instances still refining\n", outer, left, B);
+    }
+  }
+  // I_sigma = I . sum_i f_i (eq. getI), then mu or C
+  CU(ncs::launch_group_isigma(g, x, dsc, s));
+  CU(cudaMemcpyAsync(hb.data(), dsc, B * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  for (int b = 0; b < B; ++b) {
+    GroupResult& o = res[b];
+    o.Is = hb[b];
+    o.scalar = mode == NCS_INTERIOR ? 1.0 / (3.0 * o.Is) - 0.6 : 4.0 * M_PI * o.Is;
+    if (o.status == NCS_OK && !(o.rel <= tol)) o.status = NCS_E_NOCONV;
+  }
+}
+
 }  // namespace
 
 extern "C" {
@@ -653,6 +956,7 @@ void ncs_default_params(ncs_params* p) {
   p->device_precompute = 1;
   p->cuda_graphs = 1;
   p->batch_ladder_by_n = 1;
+  p->batch_grouped = 1;
 }
 
 int ncs_create(double eps, int mode, int K, const ncs_params* params, ncs_ctx** out) {
@@ -1493,6 +1797,16 @@ int ncs_batch_solve(int B, const double* eps, const int* mode, const int64_t* N,
   W = std::min(W, B);
   std::atomic<int> next(0);
   std::atomic<double> t_pre(0.0), t_solve(0.0);
+  // spheres below the tree threshold are set up by the workers and solved together
+  // afterwards (one grouped system per mode), when the solve is mixed
+  std::mutex small_mu;
+  std::vector<ncs_ctx*> small_ctx;
+  std::vector<int> small_idx;
+  auto add_time = [](std::atomic<double>& a, double v) {
+    double cur = a.load();
+    while (!a.compare_exchange_weak(cur, cur + v)) {
+    }
+  };
   const auto t0 = std::chrono::steady_clock::now();
   auto work = [&]() {
     cudaSetDevice(dev);
@@ -1503,9 +1817,19 @@ int ncs_batch_solve(int B, const double* eps, const int* mode, const int64_t* N,
       ncs_ctx* c = nullptr;
       ncs_params pb = prm;
       if (prm.batch_ladder_by_n) pb.id_ladder_max = std::min(prm.id_ladder_max, batch_ladder_extent(N[b]));
+      const bool grouped = prm.batch_grouped && precision == NCS_MIXED && prm.method != NCS_METHOD_TREE &&
+                           N[b] < prm.tree_min_patches;
+      if (grouped) pb.method = NCS_METHOD_DIRECT;
       int rc = ncs_create(eps[b], mode[b], K, &pb, &c);
       if (rc == NCS_OK) rc = ncs_set_patches(c, N[b], centres[b]);
       const auto a1 = std::chrono::steady_clock::now();
+      if (grouped && rc == NCS_OK) {
+        add_time(t_pre, std::chrono::duration<double>(a1 - a0).count());
+        std::lock_guard<std::mutex> lk(small_mu);
+        small_ctx.push_back(c);
+        small_idx.push_back(b);
+        continue;
+      }
       double sc = 0.0, is = 0.0, rr = 0.0;
       int it = 0;
       if (rc == NCS_OK) rc = ncs_solve(c, tol, precision, nullptr, &sc, &is, &it, &rr);
@@ -1516,17 +1840,53 @@ int ncs_batch_solve(int B, const double* eps, const int* mode, const int64_t* N,
       if (relres) relres[b] = rr;
       if (status) status[b] = rc;
       ncs_destroy(c);
-      double cur = t_pre.load();
-      while (!t_pre.compare_exchange_weak(cur, cur + std::chrono::duration<double>(a1 - a0).count())) {
-      }
-      cur = t_solve.load();
-      while (!t_solve.compare_exchange_weak(cur, cur + std::chrono::duration<double>(a2 - a1).count())) {
-      }
+      add_time(t_pre, std::chrono::duration<double>(a1 - a0).count());
+      add_time(t_solve, std::chrono::duration<double>(a2 - a1).count());
     }
   };
   std::vector<std::thread> th;
   for (int w = 0; w < W; ++w) th.emplace_back(work);
   for (auto& t : th) t.join();
+  if (!small_ctx.empty()) {
+    const auto g0 = std::chrono::steady_clock::now();
+    cudaStream_t gs = nullptr;
+    int grc = cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking) == cudaSuccess ? NCS_OK : NCS_E_CUDA;
+    for (int m = 0; m < 2; ++m) {
+      std::vector<ncs_ctx*> cs;
+      std::vector<int> idx;
+      for (size_t q = 0; q < small_ctx.size(); ++q)
+        if (mode[small_idx[q]] == m) {
+          cs.push_back(small_ctx[q]);
+          idx.push_back(small_idx[q]);
+        }
+      if (cs.empty()) continue;
+      std::vector<GroupResult> gr;
+      int rc = grc;
+      if (rc == NCS_OK) {
+        try {
+          group_solve(cs, tol, gs, gr);
+        } catch (const Fail& f) {
+          rc = f.code;
+          if (log_level() > 0) std::fprintf(stderr, "ncs: grouped solve: %s\n", f.msg.c_str());
+        } catch (const std::exception& e) {
+          rc = NCS_E_INPUT;
+          if (log_level() > 0) std::fprintf(stderr, "ncs: grouped solve: %s\n", e.what());
+        }
+      }
+      for (size_t q = 0; q < idx.size(); ++q) {
+        const int b = idx[q];
+        const GroupResult o = rc == NCS_OK ? gr[q] : GroupResult{0.0, 0.0, 1.0, 0, rc};
+        if (scalar) scalar[b] = o.scalar;
+        if (Isigma) Isigma[b] = o.Is;
+        if (iterations) iterations[b] = o.iters;
+        if (relres) relres[b] = o.rel;
+        if (status) status[b] = o.status;
+      }
+    }
+    if (gs) cudaStreamDestroy(gs);
+    for (ncs_ctx* c : small_ctx) ncs_destroy(c);
+    add_time(t_solve, std::chrono::duration<double>(std::chrono::steady_clock::now() - g0).count());
+  }
   const double total = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (seconds) {
     seconds[0] = t_pre.load();    // summed over instances (set-up: precompute + tree)

@@ -152,6 +152,56 @@ cudaError_t launch_arnoldi_orthogonalize(int64_t n, const double* V, double* w, 
 // y = R^-1 g (m from the device state).
 cudaError_t launch_gmres_backsolve(const GmresDev& gd, cudaStream_t s);
 
+// ---- grouped solve of small spheres (group.cu): B instances sharing K, Kstar and the
+// mode, their patches concatenated (patch i of the group belongs to instance pinst[i];
+// instance b owns patches [pbase[b], pbase[b + 1]) and entries [pbase[b] K, pbase[b + 1] K)
+// of every vector). Each instance keeps its eps, outgoing operator and GMRES state.
+struct GroupDev {
+  int B = 0, K = 0, Kstar = 0, mode = 0, maxit = 0, pmax = 0;
+  int seg_blocks = 1;              // blocks per instance of the segmented vector kernels
+  int64_t P = 0;                   // patches over all instances
+  const int* pinst = nullptr;      // P: instance of each patch
+  const int64_t* pbase = nullptr;  // B + 1: first patch of each instance
+  const int64_t* roff = nullptr;   // P: first outgoing coefficient of each patch
+  const int* inst_ptot = nullptr;  // B: skeleton points over all representations
+  const int64_t* tt_off = nullptr; // B: offset of the instance's T^T (K x ptot) in TT64/TT32
+  const double* inst_eps = nullptr;
+  const int* inst_nrep = nullptr;     // B: outgoing representations
+  const int* inst_repbase = nullptr;  // B: first entry of the instance in rep_p/rep_off/rep_rho
+  const int* rep_p = nullptr;
+  const int* rep_off = nullptr;
+  const double* rep_rho = nullptr;
+  const double* zloc = nullptr;    // B x Kstar x 3 local Zernike-node offsets
+  const double* centres = nullptr; // P x 3
+  const double* soff64 = nullptr;  // skeleton offsets, laid out like the coefficients (x 3)
+  const float* soff32 = nullptr;
+  double* rho64 = nullptr;         // outgoing coefficients
+  float* rho32 = nullptr;
+  const double* TT64 = nullptr;
+  const float* TT32 = nullptr;
+  double* z = nullptr;             // P x Kstar
+  const double* I = nullptr;       // B x K
+  const float4* logtab = nullptr;
+  GmresState* st = nullptr;        // B
+  double *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr;  // per instance blocks
+  double *h1 = nullptr, *h2 = nullptr;  // B x (maxit + 1)
+  double* pnorm = nullptr;         // B x seg_blocks
+  double* vk = nullptr;            // P x K: the newest basis vector of every instance
+};
+int group_seg_blocks(int64_t maxseg);
+// z = compressed far field of x (outgoing products, then the direct sums per instance)
+cudaError_t launch_group_field(const GroupDev& g, const double* x, int prec, cudaStream_t s);
+// One Arnoldi step of every running instance (two Gram-Schmidt passes, Givens, normalise).
+cudaError_t launch_group_arnoldi(const GroupDev& g, const double* V, double* w, cudaStream_t s);
+// e = V y with y = R^-1 g per instance
+cudaError_t launch_group_solution(const GroupDev& g, const double* V, double* e, cudaStream_t s);
+// out[b] = a . c over instance b's segment
+cudaError_t launch_group_dots(const GroupDev& g, const double* a, const double* c, double* out, cudaStream_t s);
+// out[b] = I_b . sum of instance b's densities
+cudaError_t launch_group_isigma(const GroupDev& g, const double* x, double* out, cudaStream_t s);
+// x[seg_b] *= a[b]
+cudaError_t launch_group_scale(const GroupDev& g, const double* a, double* x, cudaStream_t s);
+
 }  // namespace ncs
 
 // The opaque context of the C ABI.

@@ -42,7 +42,7 @@ class ncs_params(ctypes.Structure):
                 ("verbose", ctypes.c_int), ("mixed_residual", ctypes.c_int), ("tensor_cores", ctypes.c_int),
                 ("residual_update", ctypes.c_int), ("id_ladder_max", ctypes.c_double),
                 ("device_precompute", ctypes.c_int), ("cuda_graphs", ctypes.c_int),
-                ("batch_ladder_by_n", ctypes.c_int)]
+                ("batch_ladder_by_n", ctypes.c_int), ("batch_grouped", ctypes.c_int)]
 
 
 class ncs_tuning(ctypes.Structure):

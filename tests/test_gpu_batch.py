@@ -95,3 +95,28 @@ def test_batch_workload_small_instances_vs_oracle():
         print(f"instance N={N} eps={eps:.4f} mode {mode}: library {out['scalar'][b]:.12f}, oracle {val:.12f}")
         assert abs(out["scalar"][b] - val) <= 1e-8 * abs(val)
         assert out["relres"][b] <= 1e-10
+
+
+def test_grouped_small_spheres_match_separate_contexts():
+    """Spheres below the tree threshold solved as one grouped system (batch_grouped = 1:
+    concatenated patches, per-instance operators and GMRES states) against the same batch
+    solved on one context per sphere (batch_grouped = 0): the same mean first passage times
+    and capacitances, both to the requested residual, and fewer kernel launches grouped."""
+    g = L.rng(79)
+    inst = []
+    for b in range(10):
+        N = int(g.integers(20, 120))
+        eps = float(g.uniform(0.02, 0.04))
+        inst.append((L.uniform(N, eps, L.rng(79, b + 1)), eps, b % 2))
+    kw = dict(npan=6, nord=10, ntheta_fine=24)
+    out, launches = {}, {}
+    for grouped in (1, 0):
+        n0 = ncs.launch_count()
+        out[grouped] = ncs.batch_solve(inst, 21, tol=1e-10, precision=ncs.MIXED, workers=4, batch_grouped=grouped, **kw)
+        launches[grouped] = ncs.launch_count() - n0
+        assert out[grouped]["rc"] == 0 and (out[grouped]["status"] == 0).all()
+        assert (out[grouped]["relres"] <= 1e-10).all()
+    d = np.abs(out[1]["scalar"] - out[0]["scalar"]) / np.abs(out[0]["scalar"])
+    print(f"grouped vs separate: max relative difference {d.max():.2e}; launches {launches[1]} vs {launches[0]}")
+    assert d.max() <= 1e-9
+    assert launches[1] < launches[0]
