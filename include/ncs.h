@@ -444,7 +444,9 @@ int ncs_tc_gemm_f32(int64_t rows, int cols, int kdim, const float* A, const floa
  * With params->batch_ladder_by_n each sphere's ID ladder extent follows its patch count;
  * with params->batch_grouped (NCS_MIXED only) the spheres below tree_min_patches are set
  * up by the workers and then solved together on the calling thread, one grouped system per
- * mode (direct products, the mixed refinement of ncs_solve per instance in lock step).
+ * mode (direct products, the mixed refinement of ncs_solve per instance in lock step, the
+ * Krylov step of all of them captured once as a CUDA graph and replayed when
+ * params->cuda_graphs is set).
  * centres[b] points to N[b] x 3 host doubles. Per-instance outputs (each may be NULL):
  * scalar (mu or C), I_sigma, iterations, relres, status (NCS_OK or the instance's error
  * code). seconds (may be NULL): [set-up summed over instances, solve summed over

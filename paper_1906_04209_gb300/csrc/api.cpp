@@ -685,8 +685,11 @@ void host_frame(const double* c, double* e1, double* e2) {
 // Solves the instances cs (same K and mode, direct products) by the mixed scheme of
 // ncs_solve: FP32 inner GMRES for every instance still refining, in lock step, then the
 // residual b - A x recomputed at prm.mixed_residual precision; an instance leaves the
-// sweep once its residual meets tol or stops decreasing. Per-instance results in res.
-void group_solve(const std::vector<ncs_ctx*>& cs, double tol, cudaStream_t s, std::vector<GroupResult>& res) {
+// sweep once its residual meets tol or stops decreasing. With `graphs` the Krylov step
+// (product, Arnoldi kernels, copy of the states) is captured once as a CUDA graph and
+// replayed; the caller guarantees that no other host thread uses the device meanwhile.
+// Per-instance results in res.
+void group_solve(const std::vector<ncs_ctx*>& cs, double tol, bool graphs, cudaStream_t s, std::vector<GroupResult>& res) {
   const int B = (int)cs.size();
   const ncs::Precomputed& pc0 = cs[0]->pc;
   const int K = pc0.K, Kstar = pc0.Kstar, mode = pc0.mode;
@@ -849,6 +852,42 @@ void group_solve(const std::vector<ncs_ctx*>& cs, double tol, cudaStream_t s, st
   CU(cudaMemsetAsync(x, 0, n * sizeof(double), s));
   CU(cudaMemcpyAsync(r, bv, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   std::vector<char> active(B, 1);
+  // one Krylov step of every running instance: w = A vk, orthogonalisation, Givens, the
+  // next basis vector, and the states copied into pinned host memory
+  auto krylov_step = [&]() {
+    product(g.vk, w, NCS_FP32);
+    CU(ncs::launch_group_arnoldi(g, V, w, s));
+    CU(cudaMemcpyAsync(sth, g.st, B * sizeof(ncs::GmresState), cudaMemcpyDeviceToHost, s));
+  };
+  std::unique_ptr<std::remove_pointer<cudaGraphExec_t>::type, decltype(&cudaGraphExecDestroy)> graph(
+      nullptr, &cudaGraphExecDestroy);
+  long long graph_kernels = 0;
+  auto capture = [&]() {
+    graphs = false;  // one attempt; on failure the step keeps launching directly
+    cudaGraph_t gr = nullptr;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    const long long n0 = ncs::g_launches.load();
+    bool ok = true;
+    try {
+      krylov_step();
+    } catch (const Fail&) {
+      ok = false;
+    }
+    const long long n1 = ncs::g_launches.load();
+    ncs::g_launches.fetch_sub(n1 - n0);  // captured, not launched
+    const cudaError_t e = cudaStreamEndCapture(s, &gr);
+    cudaGraphExec_t ge = nullptr;
+    if (ok && e == cudaSuccess && gr && cudaGraphInstantiate(&ge, gr, 0) == cudaSuccess) {
+      graph.reset(ge);
+      graph_kernels = n1 - n0;
+    } else {
+      cudaGetLastError();
+    }
+    if (gr) cudaGraphDestroy(gr);
+  };
   // inner FP32 GMRES (x0 = 0, no restart) of every active instance for A corr = r
   auto inner = [&]() {
     std::vector<double> beta = seg_dots(r, r);
@@ -876,9 +915,13 @@ void group_solve(const std::vector<ncs_ctx*>& cs, double tol, cudaStream_t s, st
       bool any = false;
       for (int b = 0; b < B; ++b) any |= (running[b] = !sth[b].done);
       if (!any) break;
-      product(g.vk, w, NCS_FP32);
-      CU(ncs::launch_group_arnoldi(g, V, w, s));
-      CU(cudaMemcpyAsync(sth, g.st, B * sizeof(ncs::GmresState), cudaMemcpyDeviceToHost, s));
+      if (step > 0 && graphs && !graph) capture();
+      if (step > 0 && graph) {
+        CU(cudaGraphLaunch(graph.get(), s));
+        ncs::g_launches.fetch_add(graph_kernels);
+      } else {
+        krylov_step();
+      }
       CU(cudaStreamSynchronize(s));
       for (int b = 0; b < B; ++b) res[b].iters += running[b];
     }
@@ -1785,6 +1828,7 @@ int ncs_batch_solve(int B, const double* eps, const int* mode, const int64_t* N,
     prm = *params;
   else
     ncs_default_params(&prm);
+  const bool user_graphs = prm.cuda_graphs != 0;  // the grouped solve runs alone: it may capture
   prm.threads = 1;  // one host thread per instance; instances run concurrently
   // no CUDA-graph capture: a capture on one worker's stream makes device-wide
   // synchronisation (which allocation, freeing and the precompute of the other workers may
@@ -1864,7 +1908,7 @@ int ncs_batch_solve(int B, const double* eps, const int* mode, const int64_t* N,
       int rc = grc;
       if (rc == NCS_OK) {
         try {
-          group_solve(cs, tol, gs, gr);
+          group_solve(cs, tol, user_graphs, gs, gr);
         } catch (const Fail& f) {
           rc = f.code;
           if (log_level() > 0) std::fprintf(stderr, "ncs: grouped solve: %s\n", f.msg.c_str());
