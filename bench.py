@@ -44,7 +44,7 @@ FLOPS_PER_PAIR = 20
 # loop at N = 2e4 of the same layout family (profiles/p2l_kernel_fp32_N2e4.md); the reads scale
 # with the work items. Valid for the launch configuration that was captured (reported as null
 # for any other).
-P2L_CAPTURE = {"p2l_tile": 16, "item_patches": 16, "bytes_per_pair": 185.4e6 / 1.4535e10}
+P2L_CAPTURE = {"p2l_tile": 16, "item_patches": 16, "bytes_per_pair": 185.5e6 / 1.4535e10}
 
 
 _T0 = time.time()
