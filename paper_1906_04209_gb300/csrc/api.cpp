@@ -2059,7 +2059,7 @@ int ncs_tune(ncs_ctx* c, int flags, const char* cache_path, ncs_tuning* out, dou
             ncs_tuning t = bp2l;
             t.direct_poly = poly;
             t.direct_rsq = rsq;
-            if (poly == start.direct_poly && rsq == start.direct_rsq) continue;
+            if (!tuning_valid(t) || (poly == start.direct_poly && rsq == start.direct_rsq)) continue;
             apply_tuning(c, t);
             const Meas m = measure(kReps);
             if (m.err <= kTol && m.direct < bd) bd = m.direct, bt.direct_poly = poly, bt.direct_rsq = rsq;

@@ -39,6 +39,41 @@ __device__ __forceinline__ f2 f2_from_double(double v) {
 
 __device__ __forceinline__ double f2_to_double(f2 a) { return (double)a.hi + (double)a.lo; }
 
+// Split on a power-of-two grid: hi = the multiple of q nearest v, lo = v - hi rounded to
+// FP32. With |v| <= 2^23 q (q = 2^e, qinv = 2^-e) hi is exact in FP32, and so is the
+// difference of two such highs on the same grid (an integer multiple of q below 2^24 q):
+// the pair kernels then form an offset's high word with one subtraction, no TwoSum.
+// The representation error is |lo| 2^-24 <= q 2^-25.
+__device__ __forceinline__ f2 f2_split_grid(double v, double q, double qinv) {
+  const double h = rint(v * qinv) * q;
+  return {(float)h, (float)(v - h)};
+}
+
+// Grid spacing for the offsets of one block: every thread passes the largest |offset| it
+// will split (per coordinate, m[3]); the block's maximum B_c gives q_c = 2^(e_c - 23) with
+// 2^e_c >= B_c, so |v| <= 2^23 q_c for every offset of the block. All threads must call it;
+// `scratch` is 3 words of shared memory, `qs` 6 shared doubles that receive q_c and 1/q_c.
+// Non-negative doubles order as their bit patterns.
+__device__ __forceinline__ void block_grid(const double* m, unsigned long long* scratch, double* qs) {
+  __syncthreads();
+  if (threadIdx.x < 3) scratch[threadIdx.x] = 0ull;
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    double v = m[c];
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(&scratch[c], (unsigned long long)__double_as_longlong(v));
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    int e = 0;
+    frexp(__longlong_as_double((long long)scratch[threadIdx.x]), &e);  // B = f 2^e, f in [1/2, 1); e = 0 for B = 0
+    qs[threadIdx.x] = ldexp(1.0, e - 23);
+    qs[3 + threadIdx.x] = ldexp(1.0, 23 - e);
+  }
+  __syncthreads();
+}
+
 __device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
   const f2 s = two_sum(a.hi, b.hi);
   const f2 t = two_sum(a.lo, b.lo);
@@ -270,14 +305,25 @@ __device__ __forceinline__ f2x2 green_f2_x2(f2x2 d2, const float4* __restrict__ 
 
 // pair_f2_acc for two targets at once (lane h of every packed value is target h): the
 // packed target offsets A[0..2], one staged source (hi, lo) broadcast to both lanes.
-template <int MODE>
+// GRID: targets and sources were split by f2_split_grid on the same grid, so the high
+// words subtract exactly and each offset is (hi difference, lo difference), unnormalised
+// but with |lo| <= q far below |hi| for the separated pairs these kernels sum.
+template <int MODE, bool GRID = false>
 __device__ __forceinline__ void pair_f2_acc_x2(const f2x2* A, float4 sh, float4 sl, const float4* __restrict__ tab,
                                                f2x2& acc) {
-  f2x2 dx = two_sum_x2(A[0].hi, x2_splat(-sh.x)), dy = two_sum_x2(A[1].hi, x2_splat(-sh.y)),
-       dz = two_sum_x2(A[2].hi, x2_splat(-sh.z));
-  dx.lo = x2_add(dx.lo, x2_sub(A[0].lo, x2_splat(sl.x)));
-  dy.lo = x2_add(dy.lo, x2_sub(A[1].lo, x2_splat(sl.y)));
-  dz.lo = x2_add(dz.lo, x2_sub(A[2].lo, x2_splat(sl.z)));
+  f2x2 dx, dy, dz;
+  if constexpr (GRID) {
+    dx = f2x2{x2_sub(A[0].hi, x2_splat(sh.x)), x2_sub(A[0].lo, x2_splat(sl.x))};
+    dy = f2x2{x2_sub(A[1].hi, x2_splat(sh.y)), x2_sub(A[1].lo, x2_splat(sl.y))};
+    dz = f2x2{x2_sub(A[2].hi, x2_splat(sh.z)), x2_sub(A[2].lo, x2_splat(sl.z))};
+  } else {
+    dx = two_sum_x2(A[0].hi, x2_splat(-sh.x));
+    dy = two_sum_x2(A[1].hi, x2_splat(-sh.y));
+    dz = two_sum_x2(A[2].hi, x2_splat(-sh.z));
+    dx.lo = x2_add(dx.lo, x2_sub(A[0].lo, x2_splat(sl.x)));
+    dy.lo = x2_add(dy.lo, x2_sub(A[1].lo, x2_splat(sl.y)));
+    dz.lo = x2_add(dz.lo, x2_sub(A[2].lo, x2_splat(sl.z)));
+  }
   const f32x2 px = x2_mul(dx.hi, dx.hi), py = x2_mul(dy.hi, dy.hi), pz = x2_mul(dz.hi, dz.hi);
   const f2x2 s1 = two_sum_x2(px, py);
   const f2x2 s2 = two_sum_x2(s1.hi, pz);

@@ -702,6 +702,24 @@ __global__ void __launch_bounds__(P2L_THREADS) p2l_df_kernel(
   const int q = shape_nr[sh] * shape_nth[sh];
   const int64_t off = goff[g];
   const double gx = gcen[3 * g], gy = gcen[3 * g + 1], gz = gcen[3 * g + 2];
+  // one grid for the high words of every offset of the item (targets and sources), so
+  // that the pair loop subtracts them exactly (f2_split_grid)
+  __shared__ unsigned long long gbits[3];
+  __shared__ double qs[6];  // grid spacing per coordinate, then its inverse
+  {
+    const double gc[3] = {gx, gy, gz};
+    double m[3] = {0.0, 0.0, 0.0};
+    for (int ap = threadIdx.x; ap < q; ap += P2L_THREADS)
+      for (int c = 0; c < 3; ++c) m[c] = fmax(m[c], fabs(gpos[3 * (off + ap) + c]));
+    const int64_t npts = (hi - lo) * p;
+    for (int64_t idx = threadIdx.x; idx < npts; idx += P2L_THREADS) {
+      const int64_t jj = idx / p;
+      const int j = isrc[lo + jj];
+      const int64_t gs = (int64_t)j * pt + col + (idx - jj * p);
+      for (int c = 0; c < 3; ++c) m[c] = fmax(m[c], fabs((centres[3 * j + c] - gc[c]) + soff[3 * gs + c]));
+    }
+    block_grid(m, gbits, qs);
+  }
   constexpr int NT = 2;
   for (int base = 0; base < q; base += P2L_THREADS * NT) {
     f2 a[NT][3];
@@ -709,7 +727,7 @@ __global__ void __launch_bounds__(P2L_THREADS) p2l_df_kernel(
 #pragma unroll
     for (int t = 0; t < NT; ++t) {
       const int ap = base + t * P2L_THREADS + threadIdx.x;
-      for (int c = 0; c < 3; ++c) a[t][c] = f2_from_double(ap < q ? gpos[3 * (off + ap) + c] : 0.0);
+      for (int c = 0; c < 3; ++c) a[t][c] = f2_split_grid(ap < q ? gpos[3 * (off + ap) + c] : 0.0, qs[c], qs[3 + c]);
       acc[t] = 0.0;
     }
     for (int64_t s0 = lo; s0 < hi; s0 += P2L_DF_JT) {
@@ -723,8 +741,9 @@ __global__ void __launch_bounds__(P2L_THREADS) p2l_df_kernel(
       for (int idx = threadIdx.x; idx < nj * p; idx += P2L_THREADS) {
         const int jj = idx / p;
         const int64_t gs = (int64_t)isrc[s0 + jj] * pt + col + (idx - jj * p);
-        const f2 x = f2_from_double(D[jj][0] + soff[3 * gs]), y = f2_from_double(D[jj][1] + soff[3 * gs + 1]),
-                 z = f2_from_double(D[jj][2] + soff[3 * gs + 2]), r = f2_from_double(rho[gs]);
+        const f2 x = f2_split_grid(D[jj][0] + soff[3 * gs], qs[0], qs[3]),
+                 y = f2_split_grid(D[jj][1] + soff[3 * gs + 1], qs[1], qs[4]),
+                 z = f2_split_grid(D[jj][2] + soff[3 * gs + 2], qs[2], qs[5]), r = f2_from_double(rho[gs]);
         Sh[idx] = make_float4(x.hi, y.hi, z.hi, r.hi);
         Sl[idx] = make_float4(x.lo, y.lo, z.lo, r.lo);
       }
@@ -740,7 +759,7 @@ __global__ void __launch_bounds__(P2L_THREADS) p2l_df_kernel(
         f2x2 A[3], P{x2_splat(0.0f), x2_splat(0.0f)};
 #pragma unroll
         for (int c = 0; c < 3; ++c) A[c] = f2x2{x2_pack(a[0][c].hi, a[1][c].hi), x2_pack(a[0][c].lo, a[1][c].lo)};
-        for (int s = 0; s < ns; ++s) pair_f2_acc_x2<MODE>(A, Sh[s], Sl[s], tab, P);
+        for (int s = 0; s < ns; ++s) pair_f2_acc_x2<MODE, true>(A, Sh[s], Sl[s], tab, P);
         x2_unpack(P.hi, part[0].hi, part[1].hi);
         x2_unpack(P.lo, part[0].lo, part[1].lo);
       } else if (nact == 1) {
@@ -777,15 +796,37 @@ __global__ void __launch_bounds__(DTD_THREADS) direct_list_df_kernel(
   f2 a[DTD_NT][3];
   double acc[DTD_NT];
   int kk[DTD_NT];
+  double gq[DTD_NT][3];
+  double m[3] = {0.0, 0.0, 0.0};
 #pragma unroll
   for (int t = 0; t < DTD_NT; ++t) {
     kk[t] = (blockIdx.y * DTD_NT + t) * DTD_THREADS + threadIdx.x;
-    double gq[3] = {0.0, 0.0, 0.0};
-    if (kk[t] < Kstar) frame_apply(e1, e2, cx, cy, cz, zloc[3 * kk[t]], zloc[3 * kk[t] + 1], zloc[3 * kk[t] + 2], gq);
-    for (int c = 0; c < 3; ++c) a[t][c] = f2_from_double(gq[c]);
+    for (int c = 0; c < 3; ++c) gq[t][c] = 0.0;
+    if (kk[t] < Kstar)
+      frame_apply(e1, e2, cx, cy, cz, zloc[3 * kk[t]], zloc[3 * kk[t] + 1], zloc[3 * kk[t] + 2], gq[t]);
+    for (int c = 0; c < 3; ++c) m[c] = fmax(m[c], fabs(gq[t][c]));
     acc[t] = 0.0;
   }
   const int64_t lo = pd_off[i], hi = pd_off[i + 1];
+  // one grid for the high words of the block's offsets (its nodes and every listed
+  // source), so that the pair loop subtracts them exactly (f2_split_grid)
+  __shared__ unsigned long long gbits[3];
+  __shared__ double qs[6];  // grid spacing per coordinate, then its inverse
+  {
+    for (int64_t s0 = lo; s0 < hi; ++s0) {
+      const int64_t j = pd[s0];
+      const int k = pdk[s0];
+      const int pk = rep_p[k];
+      for (int mm = threadIdx.x; mm < pk; mm += DTD_THREADS) {
+        const int64_t gs = j * pt + rep_off[k] + mm;
+        for (int c = 0; c < 3; ++c) m[c] = fmax(m[c], fabs((centres[3 * j + c] - centres[3 * i + c]) + soff[3 * gs + c]));
+      }
+    }
+    block_grid(m, gbits, qs);
+  }
+#pragma unroll
+  for (int t = 0; t < DTD_NT; ++t)
+    for (int c = 0; c < 3; ++c) a[t][c] = f2_split_grid(gq[t][c], qs[c], qs[3 + c]);
   for (int64_t s0 = lo; s0 < hi; s0 += DT_JT) {
     const int nj = (int)min((int64_t)DT_JT, hi - s0);
     __syncthreads();
@@ -807,8 +848,9 @@ __global__ void __launch_bounds__(DTD_THREADS) direct_list_df_kernel(
       int jj = 0;
       while (idx >= toff[jj + 1]) ++jj;
       const int64_t gs = (int64_t)pd[s0 + jj] * pt + tcol[jj] + (idx - toff[jj]);
-      const f2 x = f2_from_double(D[jj][0] + soff[3 * gs]), y = f2_from_double(D[jj][1] + soff[3 * gs + 1]),
-               zz = f2_from_double(D[jj][2] + soff[3 * gs + 2]), r = f2_from_double(rho[gs]);
+      const f2 x = f2_split_grid(D[jj][0] + soff[3 * gs], qs[0], qs[3]),
+               y = f2_split_grid(D[jj][1] + soff[3 * gs + 1], qs[1], qs[4]),
+               zz = f2_split_grid(D[jj][2] + soff[3 * gs + 2], qs[2], qs[5]), r = f2_from_double(rho[gs]);
       Sh[idx] = make_float4(x.hi, y.hi, zz.hi, r.hi);
       Sl[idx] = make_float4(x.lo, y.lo, zz.lo, r.lo);
     }
@@ -821,7 +863,7 @@ __global__ void __launch_bounds__(DTD_THREADS) direct_list_df_kernel(
       f2x2 A[3], P{x2_splat(0.0f), x2_splat(0.0f)};
 #pragma unroll
       for (int c = 0; c < 3; ++c) A[c] = f2x2{x2_pack(a[0][c].hi, a[1][c].hi), x2_pack(a[0][c].lo, a[1][c].lo)};
-      for (int s = 0; s < ns; ++s) pair_f2_acc_x2<MODE>(A, Sh[s], Sl[s], tab, P);
+      for (int s = 0; s < ns; ++s) pair_f2_acc_x2<MODE, true>(A, Sh[s], Sl[s], tab, P);
       x2_unpack(P.hi, part[0].hi, part[1].hi);
       x2_unpack(P.lo, part[0].lo, part[1].lo);
     }
