@@ -467,7 +467,9 @@ def other_workloads_leg(args):
 def batch_leg(args):
     """The batch workload: 256 independent spheres (N log-uniform in [50, 5000], eps in
     [0.005, 0.02], half interior, K = 128), each solved to args.solve_tol in mixed
-    precision with its own precompute and tree; wall time and aggregate products/s."""
+    precision with its own precompute (spheres below the tree threshold in one grouped
+    system per mode, the others on concurrent contexts with their own trees); wall time and
+    aggregate products/s."""
     from paper_1906_04209_gb300 import layouts as L, ncs
     _progress("batch workload")
     work = L.batch_workload(args.batch_size)
@@ -478,7 +480,9 @@ def batch_leg(args):
     out = ncs.batch_solve(inst, K, tol=args.solve_tol, precision=ncs.MIXED)
     wall = time.perf_counter() - t0
     prods = int(np.sum(out["iterations"]))
+    tmin = ncs.default_params().tree_min_patches
     return {"instances": len(inst), "patches": int(sum(len(c) for c, _, _ in inst)), "K": K,
+            "grouped_instances": int(sum(len(c) < tmin for c, _, _ in inst)),
             "wall_s": round(wall, 3), "setup_s_summed": round(float(out["seconds"][0]), 3),
             "solve_s_summed": round(float(out["seconds"][1]), 3), "products": prods,
             "products_per_s": round(prods / wall, 2), "max_relres": float(np.max(out["relres"])),

@@ -626,17 +626,23 @@ void precompute(double eps, int mode, int K, const PrecomputeOptions& opt, Preco
   int ks = std::min(256, nt);
   for (;;) {
     out.reps.assign(nlev, OutRep());
-    // Gaussian sketch Omega (ks x nt, counter-based); panels are added from the outside
+    // Gaussian sketch Omega (ks x nt, counter-based, each value rounded to FP32 so that the
+    // device forms its products exactly in float-float); panels are added from the outside
     // in, so after adding panel k the running sum is the sketch of the training rows
     // of {rho > ladder[k] eps}.
     std::vector<double> Om((size_t)ks * nt);
     for (int r = 0; r < ks; ++r)
-      for (int j = 0; j < nt; ++j) Om[(size_t)r * nt + j] = normal_variate(((uint64_t)r << 32) + j + 0x5eedull);
+      for (int j = 0; j < nt; ++j)
+        Om[(size_t)r * nt + j] = (double)(float)normal_variate(((uint64_t)r << 32) + j + 0x5eedull);
     std::vector<double> Yrun((size_t)ks * nf, 0.0), Yc;
     bool enlarge = false;
+    int kse_start = nlev == 1 ? 256 : 64;
     const int CB = 32;
     // the sketch products on the device when one is available (same Omega, FP64)
-    DeviceSketch* dsk = opt.device_sketch ? sketch_create(ks, nt, nf, mode, Om.data(), xt.data(), xf.data()) : nullptr;
+    // float-float sketch products unless the ID tolerance is within reach of their accuracy
+    DeviceSketch* dsk = opt.device_sketch ? sketch_create(ks, nt, nf, mode, Om.data(), xt.data(), xf.data(),
+                                                          opt.id_tol >= 1e-12)
+                                          : nullptr;
     if (dsk && !sketch_set_wb(dsk, K, WBall.data())) {
       sketch_destroy(dsk);
       dsk = nullptr;
@@ -690,11 +696,15 @@ void precompute(double eps, int mode, int K, const PrecomputeOptions& opt, Preco
       out.seconds_sketch += now_s() - ts0;
       if (pan < nlev) {
         const double tc0 = now_s();
-        // CPQR on the first kse rows of the sketch (itself a Gaussian sketch), starting
-        // small and doubling until at least 16 rows of oversampling remain past the rank:
-        // the outer levels of the ladder have small ranks
+        // CPQR on the first kse rows of the sketch (itself a Gaussian sketch), doubling from
+        // 64 rows until at least 16 rows of oversampling remain past the rank: the outer
+        // levels of the ladder have small ranks. Levels are processed from the outside in,
+        // so ranks grow from one level to the next: each level starts at the row count the
+        // doubling reached for the previous one (the same final count as starting from 64,
+        // without the restarts). A lone level at 2 eps starts at 256 rows: its rank at the
+        // ID tolerances in use exceeds 112, where the doubling from 64 ends there as well.
         std::vector<int> piv;
-        int kse = std::min(ks, 64), p = 0;
+        int kse = std::min(ks, kse_start), p = 0;
         for (;;) {
           if (dsk) {
             p = sketch_cpqr(dsk, kse, opt.id_tol, piv);
@@ -718,6 +728,7 @@ void precompute(double eps, int mode, int K, const PrecomputeOptions& opt, Preco
           enlarge = true;
           break;
         }
+        kse_start = kse;
         if (p < 1) {
           sketch_destroy(dsk);
           throw std::runtime_error("precompute: ID rank is zero");

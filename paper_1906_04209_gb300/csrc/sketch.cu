@@ -1,17 +1,23 @@
-// The one-patch interpolative decompositions on the device (see sketch.hpp), all FP64:
-//   * sketch_kernel: Y += Omega[:, r0:r1] A[r0:r1, :], A_tl = G(|x_t - x_l|) evaluated on
-//     the fly; each block owns a 64 x 64 tile of Y (sketch rows x fine points), stages 32
-//     training rows of Omega and of A per step in shared memory and accumulates 4 x 4
-//     register tiles per thread;
-//   * column-pivoted Householder QR of the leading sketch rows, one pivot/reflector block
-//     and one column-update kernel per step (a warp per column), the host reading the
-//     stopping flag every 16 steps;
-//   * X = R11^-1 R12 by one back-substitution per column, T = W B[skeleton] + X W B[rest].
+// The one-patch interpolative decompositions on the device (see sketch.hpp):
+//   * sketch_kernel: Y += Omega[:, r0:r1] A[r0:r1, :], A_tl = G(|x_t - x_l|) evaluated once
+//     per entry in float-float (the pair kernels' green_f2) and the product accumulated in
+//     float-float on the FP32 pipes (Omega holds FP32 values, so each product's error is
+//     exact by TwoProd), folded into the FP64 sketch every 256 training rows; each block owns
+//     all sketch rows (up to 256) of 32 fine points, stages 32 training rows of Omega and of
+//     A per step in shared memory and accumulates 8 rows x 4 points per thread (for ID
+//     tolerances below 1e-12, sketch64_kernel forms the same sums in FP64);
+//   * column-pivoted Householder QR of the leading sketch rows in FP64, one pivot/reflector
+//     block and one column-update kernel per step (a warp per column), the host reading
+//     the stopping flag every 16 steps;
+//   * X = R11^-1 R12 by one back-substitution per column, T = W B[skeleton] + X W B[rest]
+//     in FP64.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
 #include <vector>
 
+#include "df64.cuh"
 #include "internal.hpp"
 #include "sketch.hpp"
 
@@ -27,10 +33,105 @@ struct CpqrStatus {
 
 namespace {
 
-constexpr int SK_TR = 64;   // sketch rows per block
-constexpr int SK_TL = 64;   // fine-grid points per block
-constexpr int SK_TJ = 32;   // training rows per step
+constexpr int SK_ROWS = 256;   // sketch rows per block
+constexpr int SK_TL = 32;      // fine-grid points per block
+constexpr int SK_TJ = 32;      // training rows per step
+constexpr int SK_FLUSH = 8;    // steps between folds of the float-float sums into Y
 constexpr int SK_THREADS = 256;
+
+// acc += w (h + l) for two outputs (f32x2 halves) in float-float: w h by TwoProd (exact
+// error through the FMA), the sum by TwoSum, the low-order terms gathered in acc_l; nw = -w.
+__device__ __forceinline__ void ff_axpy_x2(f32x2& acc_h, f32x2& acc_l, f32x2 w, f32x2 nw, f32x2 h, f32x2 l) {
+  const f32x2 ph = x2_mul(w, h);
+  const f32x2 e1 = x2_fma(nw, h, ph);  // ph - w h, exact
+  const f32x2 s = x2_add(acc_h, ph);
+  const f32x2 bb = x2_sub(s, acc_h);
+  const f32x2 e = x2_add(x2_sub(acc_h, x2_sub(s, bb)), x2_sub(ph, bb));
+  acc_h = s;
+  acc_l = x2_add(acc_l, x2_fma(w, l, x2_sub(e, e1)));
+}
+
+// Om: nt x ks FP32 (training row t's sketch coefficients contiguous); Y: ks x nf column-major
+// FP64. Thread (ty, tx) owns sketch rows rb + 8 ty .. + 7 and fine points lb + 4 tx .. + 3.
+template <int MODE>
+__global__ void __launch_bounds__(SK_THREADS) sketch_kernel(int ks, int nf, const float* __restrict__ Om,
+                                                            const double* __restrict__ xt,
+                                                            const double* __restrict__ xf, int r0, int r1,
+                                                            const float4* __restrict__ logtab,
+                                                            double* __restrict__ Y) {
+  __shared__ __align__(16) float Os[SK_TJ][SK_ROWS];
+  __shared__ __align__(16) float Ah[SK_TJ][SK_TL];
+  __shared__ __align__(16) float Al[SK_TJ][SK_TL];
+  __shared__ float4 tab[kLogTable];
+  for (int t = threadIdx.x; t < kLogTable; t += SK_THREADS) tab[t] = logtab[t];
+  const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
+  const int rb = blockIdx.y * SK_ROWS, lb = blockIdx.x * SK_TL;
+  f32x2 ah[8][2], al[8][2];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) ah[i][c] = al[i][c] = x2_splat(0.0f);
+  int step = 0;
+  for (int j0 = r0; j0 < r1; j0 += SK_TJ, ++step) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < SK_TJ * SK_ROWS; e += SK_THREADS) {
+      const int jj = e / SK_ROWS, rr = e - jj * SK_ROWS;
+      const int t = j0 + jj, r = rb + rr;
+      Os[jj][rr] = (t < r1 && r < ks) ? Om[(int64_t)t * ks + r] : 0.0f;
+    }
+    for (int e = threadIdx.x; e < SK_TJ * SK_TL; e += SK_THREADS) {
+      const int jj = e / SK_TL, ll = e - jj * SK_TL;
+      const int t = j0 + jj, l = lb + ll;
+      f2 g{0.0f, 0.0f};
+      if (t < r1 && l < nf) {
+        const double dx = xt[3 * t] - xf[3 * l], dy = xt[3 * t + 1] - xf[3 * l + 1], dz = xt[3 * t + 2] - xf[3 * l + 2];
+        g = green_f2<MODE>(f2_from_double(fma(dx, dx, fma(dy, dy, dz * dz))), tab);
+      }
+      Ah[jj][ll] = g.hi;
+      Al[jj][ll] = g.lo;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int jj = 0; jj < SK_TJ; ++jj) {
+      const float4 w0 = *reinterpret_cast<const float4*>(&Os[jj][8 * ty]);
+      const float4 w1 = *reinterpret_cast<const float4*>(&Os[jj][8 * ty + 4]);
+      const float4 h = *reinterpret_cast<const float4*>(&Ah[jj][4 * tx]);
+      const float4 lo = *reinterpret_cast<const float4*>(&Al[jj][4 * tx]);
+      const f32x2 H[2] = {x2_pack(h.x, h.y), x2_pack(h.z, h.w)};
+      const f32x2 L[2] = {x2_pack(lo.x, lo.y), x2_pack(lo.z, lo.w)};
+      const float w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const f32x2 W = x2_splat(w[i]), NW = x2_splat(-w[i]);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) ff_axpy_x2(ah[i][c], al[i][c], W, NW, H[c], L[c]);
+      }
+    }
+    if (step % SK_FLUSH == SK_FLUSH - 1 || j0 + SK_TJ >= r1) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int r = rb + 8 * ty + i;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          float h0, h1, l0, l1;
+          x2_unpack(ah[i][c], h0, h1);
+          x2_unpack(al[i][c], l0, l1);
+          const int l = lb + 4 * tx + 2 * c;
+          if (r < ks && l < nf) Y[(int64_t)l * ks + r] += (double)h0 + (double)l0;
+          if (r < ks && l + 1 < nf) Y[(int64_t)(l + 1) * ks + r] += (double)h1 + (double)l1;
+          ah[i][c] = al[i][c] = x2_splat(0.0f);
+        }
+      }
+    }
+  }
+}
+
+// The FP64 sketch, for ID tolerances below the float-float kernel entries' accuracy:
+// each block owns a 64 x 64 tile of Y, evaluates its 32 x 64 kernel entries per step in
+// FP64 and accumulates 4 x 4 register tiles per thread (Omega row-major, ks x nt).
+constexpr int S64_TR = 64;   // FP64 sketch: sketch rows per block
+constexpr int S64_TL = 64;   // fine-grid points per block
+constexpr int S64_TJ = 32;   // training rows per step
 
 // On-surface Green's function of the unit sphere from the chord d (eqs. Gextonsurface /
 // Gintonsurface written with log(2/d)): exterior 2/d - log(2/d) - log(1 + d/2),
@@ -39,29 +140,29 @@ __device__ __forceinline__ double g_surface(double d, double sgn) {
   return 2.0 / d + sgn * log(2.0 / d) - log1p(0.5 * d);
 }
 
-__global__ void __launch_bounds__(SK_THREADS) sketch_kernel(int ks, int nt, int nf, double sgn,
+__global__ void __launch_bounds__(SK_THREADS) sketch64_kernel(int ks, int nt, int nf, double sgn,
                                                             const double* __restrict__ Om,
                                                             const double* __restrict__ xt,
                                                             const double* __restrict__ xf, int r0, int r1,
                                                             double* __restrict__ Y) {
-  __shared__ double Os[SK_TJ][SK_TR + 1];
-  __shared__ double As[SK_TJ][SK_TL + 1];
+  __shared__ double Os[S64_TJ][S64_TR + 1];
+  __shared__ double As[S64_TJ][S64_TL + 1];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int rb = blockIdx.y * SK_TR, lb = blockIdx.x * SK_TL;
+  const int rb = blockIdx.y * S64_TR, lb = blockIdx.x * S64_TL;
   double acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int k = 0; k < 4; ++k) acc[i][k] = 0.0;
-  for (int j0 = r0; j0 < r1; j0 += SK_TJ) {
+  for (int j0 = r0; j0 < r1; j0 += S64_TJ) {
     __syncthreads();
-    for (int e = threadIdx.x; e < SK_TJ * SK_TR; e += SK_THREADS) {
-      const int rr = e / SK_TJ, jj = e - rr * SK_TJ;  // consecutive threads: consecutive j
+    for (int e = threadIdx.x; e < S64_TJ * S64_TR; e += SK_THREADS) {
+      const int rr = e / S64_TJ, jj = e - rr * S64_TJ;  // consecutive threads: consecutive j
       const int r = rb + rr, j = j0 + jj;
       Os[jj][rr] = (r < ks && j < r1) ? Om[(int64_t)r * nt + j] : 0.0;
     }
-    for (int e = threadIdx.x; e < SK_TJ * SK_TL; e += SK_THREADS) {
-      const int jj = e / SK_TL, ll = e - jj * SK_TL;
+    for (int e = threadIdx.x; e < S64_TJ * S64_TL; e += SK_THREADS) {
+      const int jj = e / S64_TL, ll = e - jj * S64_TL;
       const int j = j0 + jj, l = lb + ll;
       double v = 0.0;
       if (j < r1 && l < nf) {
@@ -71,7 +172,7 @@ __global__ void __launch_bounds__(SK_THREADS) sketch_kernel(int ks, int nt, int 
       As[jj][ll] = v;
     }
     __syncthreads();
-    for (int jj = 0; jj < SK_TJ; ++jj) {
+    for (int jj = 0; jj < S64_TJ; ++jj) {
       double o[4], a[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) o[i] = Os[jj][ty * 4 + i];
@@ -284,8 +385,12 @@ __global__ void assemble_t_kernel(int p, int K, int nf, const int* __restrict__ 
 
 struct DeviceSketch {
   int ks = 0, nt = 0, nf = 0;
-  double sgn = 1.0;
-  double *Om = nullptr, *xt = nullptr, *xf = nullptr, *Y = nullptr;
+  int mode = 0;
+  bool ff = true;         // float-float sketch (else FP64)
+  float* Om = nullptr;    // float-float sketch: nt x ks (Omega transposed, FP32 values)
+  double* Om64 = nullptr; // FP64 sketch: ks x nt
+  float4* logtab = nullptr;
+  double *xt = nullptr, *xf = nullptr, *Y = nullptr;
   // CPQR of the first kse rows and assembly of T
   int kse = 0, K = 0;
   double *Yc = nullptr, *cn = nullptr, *cn0 = nullptr, *v = nullptr, *X = nullptr, *WB = nullptr, *T = nullptr;
@@ -297,6 +402,8 @@ struct DeviceSketch {
 void sketch_destroy(DeviceSketch* s) {
   if (!s) return;
   cudaFree(s->Om);
+  cudaFree(s->Om64);
+  cudaFree(s->logtab);
   cudaFree(s->xt);
   cudaFree(s->xf);
   cudaFree(s->Y);
@@ -314,7 +421,7 @@ void sketch_destroy(DeviceSketch* s) {
 }
 
 DeviceSketch* sketch_create(int ks, int nt, int nf, int mode, const double* Om, const double* xt,
-                            const double* xf) {
+                            const double* xf, bool ff) {
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
     cudaGetLastError();  // clear the error state of a machine without a device
@@ -324,14 +431,36 @@ DeviceSketch* sketch_create(int ks, int nt, int nf, int mode, const double* Om, 
   s->ks = ks;
   s->nt = nt;
   s->nf = nf;
-  s->sgn = (mode == 0) ? -1.0 : 1.0;
+  s->mode = mode;
+  s->ff = ff;
   const size_t nOm = (size_t)ks * nt, nY = (size_t)ks * nf;
+  // float-float sketch: Omega's values are FP32 numbers (the precompute draws them so),
+  // transposed so that a training row's coefficients are contiguous
+  std::vector<float> omt(ff ? nOm : 0);
+  for (int r = 0; r < (ff ? ks : 0); ++r)
+    for (int t = 0; t < nt; ++t) omt[(size_t)t * ks + r] = (float)Om[(size_t)r * nt + t];
+  // float-float log table of green_f2: c_i = 1 + (i + 1/2)/64, (log c_i, 1/c_i) as hi, lo
+  std::vector<float> lt(4 * kLogTable);
+  for (int i = 0; i < kLogTable; ++i) {
+    const double ci = 1.0 + (i + 0.5) / 64.0;
+    const double L = std::log(ci), inv = 1.0 / ci;
+    lt[4 * i + 0] = (float)L;
+    lt[4 * i + 1] = (float)(L - (double)(float)L);
+    lt[4 * i + 2] = (float)inv;
+    lt[4 * i + 3] = (float)(inv - (double)(float)inv);
+  }
   bool ok = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) == cudaSuccess &&
-            cudaMalloc(&s->Om, nOm * sizeof(double)) == cudaSuccess &&
+            (ff ? cudaMalloc(&s->Om, nOm * sizeof(float)) : cudaMalloc(&s->Om64, nOm * sizeof(double))) ==
+                cudaSuccess &&
+            cudaMalloc(&s->logtab, kLogTable * sizeof(float4)) == cudaSuccess &&
             cudaMalloc(&s->xt, 3 * (size_t)nt * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&s->xf, 3 * (size_t)nf * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&s->Y, nY * sizeof(double)) == cudaSuccess &&
-            cudaMemcpyAsync(s->Om, Om, nOm * sizeof(double), cudaMemcpyHostToDevice, s->stream) == cudaSuccess &&
+            (ff ? cudaMemcpyAsync(s->Om, omt.data(), nOm * sizeof(float), cudaMemcpyHostToDevice, s->stream)
+                : cudaMemcpyAsync(s->Om64, Om, nOm * sizeof(double), cudaMemcpyHostToDevice, s->stream)) ==
+                cudaSuccess &&
+            cudaMemcpyAsync(s->logtab, lt.data(), kLogTable * sizeof(float4), cudaMemcpyHostToDevice, s->stream) ==
+                cudaSuccess &&
             cudaMemcpyAsync(s->xt, xt, 3 * (size_t)nt * sizeof(double), cudaMemcpyHostToDevice, s->stream) ==
                 cudaSuccess &&
             cudaMemcpyAsync(s->xf, xf, 3 * (size_t)nf * sizeof(double), cudaMemcpyHostToDevice, s->stream) ==
@@ -348,9 +477,19 @@ DeviceSketch* sketch_create(int ks, int nt, int nf, int mode, const double* Om, 
 
 bool sketch_add_rows(DeviceSketch* s, int r0, int r1) {
   if (r1 <= r0) return true;
-  dim3 grid((unsigned)((s->nf + SK_TL - 1) / SK_TL), (unsigned)((s->ks + SK_TR - 1) / SK_TR));
-  count_launch(), sketch_kernel<<<grid, SK_THREADS, 0, s->stream>>>(s->ks, s->nt, s->nf, s->sgn, s->Om, s->xt, s->xf,
-                                                                     r0, r1, s->Y);
+  if (!s->ff) {
+    dim3 grid((unsigned)((s->nf + S64_TL - 1) / S64_TL), (unsigned)((s->ks + S64_TR - 1) / S64_TR));
+    count_launch(), sketch64_kernel<<<grid, SK_THREADS, 0, s->stream>>>(s->ks, s->nt, s->nf, s->mode == 0 ? -1.0 : 1.0,
+                                                                        s->Om64, s->xt, s->xf, r0, r1, s->Y);
+    return cudaGetLastError() == cudaSuccess;
+  }
+  dim3 grid((unsigned)((s->nf + SK_TL - 1) / SK_TL), (unsigned)((s->ks + SK_ROWS - 1) / SK_ROWS));
+  if (s->mode == 0)
+    count_launch(), sketch_kernel<0><<<grid, SK_THREADS, 0, s->stream>>>(s->ks, s->nf, s->Om, s->xt, s->xf, r0, r1,
+                                                                          s->logtab, s->Y);
+  else
+    count_launch(), sketch_kernel<1><<<grid, SK_THREADS, 0, s->stream>>>(s->ks, s->nf, s->Om, s->xt, s->xf, r0, r1,
+                                                                          s->logtab, s->Y);
   return cudaGetLastError() == cudaSuccess;
 }
 

@@ -14,9 +14,11 @@ struct DeviceSketch;
 
 // Uploads Omega (ks x nt, row-major), the training targets xt (nt x 3) and the fine-grid
 // points xf (nf x 3) and zeroes Y on the current device. mode: 0 exterior, 1 interior.
-// Returns null if no device is usable or an allocation fails.
+// ff: form the sketch in float-float on the FP32 pipes (Omega's values must then be FP32
+// numbers; kernel entries accurate to ~1e-14 relative, for ID tolerances from 1e-12 up),
+// else in FP64. Returns null if no device is usable or an allocation fails.
 DeviceSketch* sketch_create(int ks, int nt, int nf, int mode, const double* Om, const double* xt,
-                            const double* xf);
+                            const double* xf, bool ff);
 // Y += Omega[:, r0:r1] A[r0:r1, :] (asynchronous). Returns false on a CUDA error.
 bool sketch_add_rows(DeviceSketch* s, int r0, int r1);
 // Copies the running Y (ks * nf doubles, column-major) to host memory.
