@@ -348,7 +348,8 @@ def run_ours(args):
 
 def solve_legs(args, ctx, N, K, sp):
     """The metric's solves of the same workload to a relative residual of args.solve_tol:
-    mixed (FP32 inner GMRES + float-float refinement residuals), float-float (every
+    mixed (FP32 inner GMRES on the inner tree, whose incoming grids are sized to the FP32
+    products' accuracy + float-float refinement residuals on the product's tree), float-float (every
     product FP64-accurate on the FP32 pipes) and plain FP64 (every product on the FP64
     pipe). Each is timed around the ncs_solve call (densities copied back included); its
     true residual b - A x is then recomputed with one float-float product, outside the
@@ -376,10 +377,17 @@ def solve_legs(args, ctx, N, K, sp):
         ctx.matvec_dev(xd.data_ptr(), yd.data_ptr(), ncs.DF64, sp)
         torch.cuda.synchronize()
         true = float(torch.linalg.norm(b - yd)) / bn
+        if name == "mixed":
+            inf = ctx.info()
+            inner = {"grid_tol": ncs.default_params().inner_grid_tol, "grid_points": inf["inner_grid_points"],
+                     "pairs_per_product": inf["inner_tree_pairs"], "product_tree_grid_points": inf["grid_points"],
+                     "product_tree_pairs": inf["tree_pairs"]}
         out[name] = {"seconds": round(sec, 3), "iterations": r["iterations"],
                      "gmres_steps": int(st["gmres_steps"]), "residual_products": int(st["residual_products"]),
                      "residual_updates": int(st["residual_updates"]), "graph_replays": int(st["graph_replays"]),
                      "mu": r["scalar"], "relres_reported": r["relres"], "relres_true": true, "rc": r["rc"]}
+        if name == "mixed":
+            out[name]["inner_tree"] = inner
         fh[name] = r["fhat"]
         del xd, yd
     ref = "fp64" if "fp64" in fh else "df64"

@@ -119,6 +119,14 @@ typedef struct ncs_params {
                           solved together, one concatenated system per mode with one launch per
                           product stage and Krylov step for all of them (each keeps its own
                           eps, operator and GMRES state); 0: each on its own context */
+  double inner_grid_tol; /* NCS_MIXED with the tree on >= 10000 patches: incoming-grid tolerance of
+                          the tree that the inner FP32 solves (and the FP32 residual update) use,
+                          default 1e-5:
+                          their products need only the accuracy of FP32 pair sums, so coarser
+                          grids (fewer grid points and pair evaluations) serve them, while the
+                          refinement residuals keep grid_tol. Built with the product's tree when
+                          the context's precision is NCS_MIXED (else at the first mixed solve).
+                          Values <= grid_tol (e.g. 0) use the product's tree throughout */
 } ncs_params;
 
 /* Fills *p with the defaults listed above. */
@@ -208,8 +216,9 @@ int ncs_get_rep(const ncs_ctx* ctx, int r, double* T, double* skel_t, double* sk
  * Writes context sizes into out[0..n): K, Kstar, p, M, nf (fine-grid points),
  * N (patches set, 0 if none), nrad (radial nodes), tree levels (0 if no tree),
  * grid points over all tree groups, pair evaluations per tree matvec (FP counts
- * of far-field kernel evaluations), direct pairs per matvec. out: n caller int64s.
- * Errors: NCS_E_INPUT (NULL).
+ * of far-field kernel evaluations), direct pairs per matvec, and the grid points and
+ * pair evaluations of the mixed solve's inner tree (0 if not built; see inner_grid_tol);
+ * at most 13 values. out: n caller int64s. Errors: NCS_E_INPUT (NULL).
  */
 int ncs_info(const ncs_ctx* ctx, int64_t* out, int n);
 

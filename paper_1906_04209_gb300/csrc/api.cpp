@@ -80,7 +80,7 @@ T* dev_alloc(size_t n) {
 // The captured Arnoldi steps hold the layout's, the workspace's and the product path's
 // pointers: dropped whenever one of them changes.
 void invalidate_graphs(ncs_ctx* c) {
-  for (int p = 0; p < 4; ++p)
+  for (int p = 0; p < ncs_ctx::kGraphSlots; ++p)
     if (c->step_graph[p]) {
       cudaGraphExecDestroy(c->step_graph[p]);
       c->step_graph[p] = nullptr;
@@ -101,6 +101,16 @@ void free_krylov(ncs_ctx* c) {
   c->Vcap = 0;
 }
 
+// Both trees (the product's and the mixed solve's inner one), host and device.
+void drop_trees(ncs_ctx* c) {
+  ncs::tree_free(c->tdev);
+  ncs::tree_free(c->tdev_in);
+  c->tree_built = c->tree_uploaded = false;
+  c->tree_in_built = c->tree_in_uploaded = false;
+  c->tree = ncs::TreeHost();
+  c->tree_in = ncs::TreeHost();
+}
+
 void free_layout(ncs_ctx* c) {
   DeviceData& d = c->d;
   dev_free(d.centres);
@@ -111,10 +121,7 @@ void free_layout(ncs_ctx* c) {
   dev_free(d.z);
   dev_free(d.Apack);
   free_krylov(c);
-  ncs::tree_free(c->tdev);
-  c->tree_built = false;
-  c->tree_uploaded = false;
-  c->tree = ncs::TreeHost();
+  drop_trees(c);
   d.N = 0;
 }
 
@@ -270,9 +277,9 @@ bool use_tree(const ncs_ctx* c) {
   return (int64_t)(c->centres.size() / 3) >= c->prm.tree_min_patches;
 }
 
-ncs::TreeOptions tree_options(const ncs_ctx* c) {
+ncs::TreeOptions tree_options(const ncs_ctx* c, double grid_tol) {
   ncs::TreeOptions to;
-  to.grid_tol = c->prm.grid_tol;
+  to.grid_tol = grid_tol;
   to.eps = c->pc.eps;
   to.item_patches = c->tune.item_patches;
   to.l2p_weight = c->tune.l2p_weight;
@@ -286,21 +293,54 @@ void ensure_tree_host(ncs_ctx* c) {
   // the thread count is an ICV of the calling host thread: the context's, on every build
   omp_set_num_threads(c->prm.threads > 0 ? c->prm.threads : omp_get_num_procs());
 #endif
-  ncs::tree_build(c->centres, c->pc, tree_options(c), c->tree);
+  ncs::tree_build(c->centres, c->pc, tree_options(c, c->prm.grid_tol), c->tree);
   c->tree_built = true;
 }
 
+void set_kernel_config(const ncs_ctx* c, ncs::TreeDevice& t) {
+  t.cfg.p2l_tile = c->tune.p2l_tile;
+  t.cfg.p2l_poly = c->tune.p2l_poly;
+  t.cfg.direct_poly = c->tune.direct_poly;
+  t.cfg.p2l_rsq = c->tune.p2l_rsq;
+  t.cfg.direct_rsq = c->tune.direct_rsq;
+}
+
+// The mixed solve's inner FP32 products need only the accuracy of FP32 pair sums (~1e-6), so
+// they may use incoming grids to a looser tolerance than the product's (fewer grid points
+// and P2L pairs); the refinement residuals keep the product's tree. Below ~1e4 patches a
+// tree product is bound by launch latency rather than by its pair sums, and a second tree
+// would cost more set-up than it saves.
+constexpr int64_t kInnerTreeMinPatches = 10000;
+bool inner_tree_enabled(const ncs_ctx* c) {
+  return c->prm.inner_grid_tol > c->prm.grid_tol && (int64_t)(c->centres.size() / 3) >= kInnerTreeMinPatches;
+}
+
+void ensure_inner_tree(ncs_ctx* c) {
+  if (!inner_tree_enabled(c)) return;
+  if (!c->tree_in_built) {
+#ifdef _OPENMP
+    omp_set_num_threads(c->prm.threads > 0 ? c->prm.threads : omp_get_num_procs());
+#endif
+    ncs::tree_build(c->centres, c->pc, tree_options(c, c->prm.inner_grid_tol), c->tree_in);
+    c->tree_in_built = true;
+  }
+  if (!c->tree_in_uploaded) {
+    ncs::tree_upload(c->tree_in, c->pc, c->tdev_in);
+    c->tree_in_uploaded = true;
+  }
+  set_kernel_config(c, c->tdev_in);
+}
+
+// The product's tree; with the context's precision mixed, the inner tree as well (built
+// with the product's, so that a solve finds both ready).
 void ensure_tree(ncs_ctx* c) {
   ensure_tree_host(c);
   if (!c->tree_uploaded) {
     ncs::tree_upload(c->tree, c->pc, c->tdev);
     c->tree_uploaded = true;
   }
-  c->tdev.cfg.p2l_tile = c->tune.p2l_tile;
-  c->tdev.cfg.p2l_poly = c->tune.p2l_poly;
-  c->tdev.cfg.direct_poly = c->tune.direct_poly;
-  c->tdev.cfg.p2l_rsq = c->tune.p2l_rsq;
-  c->tdev.cfg.direct_rsq = c->tune.direct_rsq;
+  set_kernel_config(c, c->tdev);
+  if (c->precision == NCS_MIXED) ensure_inner_tree(c);
 }
 
 void outgoing(ncs_ctx* c, const double* x, int prec, cudaStream_t s) {
@@ -334,7 +374,8 @@ void field(ncs_ctx* c, const double* x, int prec, cudaStream_t s) {
   outgoing(c, x, prec, s);
   if (use_tree(c)) {
     ensure_tree(c);
-    CU(ncs::launch_tree_field(c->d, c->tdev, c->pc.mode, prec, s));
+    const bool inner = c->inner_active && prec == NCS_FP32 && c->tree_in_uploaded;
+    CU(ncs::launch_tree_field(c->d, inner ? c->tdev_in : c->tdev, c->pc.mode, prec, s));
   } else {
     CU(ncs::launch_direct_field(c->d, c->pc.mode, prec, c->pc.eps, s));
   }
@@ -405,7 +446,7 @@ void arnoldi_step(ncs_ctx* c, int prec, cudaStream_t s) {
 
 // Captures arnoldi_step as a CUDA graph (once per precision and workspace). On any failure
 // the context keeps launching the step directly (the same kernels) and says why.
-void capture_step(ncs_ctx* c, int prec, cudaStream_t s) {
+void capture_step(ncs_ctx* c, int prec, int slot, cudaStream_t s) {
   cudaGraph_t g = nullptr;
   if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
     cudaGetLastError();
@@ -425,8 +466,8 @@ void capture_step(ncs_ctx* c, int prec, cudaStream_t s) {
   const cudaError_t e = cudaStreamEndCapture(s, &g);
   cudaGraphExec_t ge = nullptr;
   if (ok && e == cudaSuccess && g && cudaGraphInstantiate(&ge, g, 0) == cudaSuccess) {
-    c->step_graph[prec] = ge;
-    c->step_graph_kernels[prec] = n1 - n0;
+    c->step_graph[slot] = ge;
+    c->step_graph_kernels[slot] = n1 - n0;
   } else {
     cudaGetLastError();
     if (ok) c->graph_note = std::string("graph capture: ") + cudaGetErrorString(e);
@@ -452,16 +493,18 @@ int gmres(ncs_ctx* c, const double* r, double* e, double tol, int prec, int maxi
   }
   ncs::GmresDev& gd = c->gd;
   maxit = std::min(maxit, gd.maxit);
+  // the inner solves of a mixed solve run on their own tree: their own captured step
+  const int slot = (c->inner_active && prec == NCS_FP32) ? 4 : prec;
   *c->st_host = ncs::GmresState{0, 0, ncs::kGmresRunning, maxit, beta, tol, 1.0, 0.0};
   CU(cudaMemcpyAsync(gd.st, c->st_host, sizeof(ncs::GmresState), cudaMemcpyHostToDevice, s));
   CU(ncs::launch_scale_copy(n, r, 1.0 / beta, c->V, s));
   CU(cudaMemcpyAsync(gd.vk, c->V, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   int steps = 0;
   while (steps < maxit) {
-    if (steps > 0 && c->prm.cuda_graphs && !c->graphs_off && !c->step_graph[prec]) capture_step(c, prec, s);
-    if (steps > 0 && c->step_graph[prec]) {
-      CU(cudaGraphLaunch(c->step_graph[prec], s));
-      ncs::g_launches.fetch_add(c->step_graph_kernels[prec]);
+    if (steps > 0 && c->prm.cuda_graphs && !c->graphs_off && !c->step_graph[slot]) capture_step(c, prec, slot, s);
+    if (steps > 0 && c->step_graph[slot]) {
+      CU(cudaGraphLaunch(c->step_graph[slot], s));
+      ncs::g_launches.fetch_add(c->step_graph_kernels[slot]);
       c->solve_stats[5] += 1.0;
     } else {
       arnoldi_step(c, prec, s);
@@ -553,6 +596,7 @@ void validate_params(const ncs_params& p) {
   if (!(p.id_tol > 0.0 && p.id_tol < 1e-2)) throw Fail{NCS_E_INPUT, "id_tol out of range"};
   if (!(p.id_ladder_max >= 0.0 && p.id_ladder_max <= 4.0)) throw Fail{NCS_E_INPUT, "id_ladder_max out of range"};
   if (!(p.grid_tol > 0.0 && p.grid_tol < 1e-1)) throw Fail{NCS_E_INPUT, "grid_tol out of range"};
+  if (!(p.inner_grid_tol >= 0.0 && p.inner_grid_tol < 1e-1)) throw Fail{NCS_E_INPUT, "inner_grid_tol out of range"};
   if (p.gmres_maxit < 1 || p.gmres_maxit > 2000) throw Fail{NCS_E_INPUT, "gmres_maxit out of range"};
   if (p.method < 0 || p.method > 2) throw Fail{NCS_E_INPUT, "bad method"};
   if (p.mixed_residual != NCS_FP64 && p.mixed_residual != NCS_DF64)
@@ -573,12 +617,7 @@ void apply_tuning(ncs_ctx* c, const ncs_tuning& t) {
   const bool rebuild = t.item_patches != c->tune.item_patches || t.l2p_weight != c->tune.l2p_weight;
   c->tune = t;
   invalidate_graphs(c);
-  if (rebuild && c->tree_built) {
-    ncs::tree_free(c->tdev);
-    c->tree_built = false;
-    c->tree_uploaded = false;
-    c->tree = ncs::TreeHost();
-  }
+  if (rebuild && (c->tree_built || c->tree_in_built)) drop_trees(c);
 }
 
 // Cache key of a workload: mode, K, eps, N (in half-octaves) and the shape of its tree
@@ -1000,6 +1039,7 @@ void ncs_default_params(ncs_params* p) {
   p->cuda_graphs = 1;
   p->batch_ladder_by_n = 1;
   p->batch_grouped = 1;
+  p->inner_grid_tol = 1e-5;
 }
 
 int ncs_create(double eps, int mode, int K, const ncs_params* params, ncs_ctx** out) {
@@ -1148,7 +1188,7 @@ int ncs_get_rep(const ncs_ctx* c, int r, double* T, double* skel_t, double* skel
 
 int ncs_info(const ncs_ctx* c, int64_t* out, int n) {
   if (!c || !out) return NCS_E_INPUT;
-  const int64_t v[11] = {c->pc.K,
+  const int64_t v[13] = {c->pc.K,
                          c->pc.Kstar,
                          c->pc.p,
                          c->pc.M,
@@ -1159,8 +1199,10 @@ int ncs_info(const ncs_ctx* c, int64_t* out, int n) {
                          c->tree_built ? c->tree.total_grid_points : 0,
                          c->tree_built ? c->tree.pairs_per_matvec : 0,
                          (int64_t)(c->centres.size() / 3) * ((int64_t)(c->centres.size() / 3) - 1) *
-                             (int64_t)c->pc.p * c->pc.Kstar};
-  for (int i = 0; i < n && i < 11; ++i) out[i] = v[i];
+                             (int64_t)c->pc.p * c->pc.Kstar,
+                         c->tree_in_built ? c->tree_in.total_grid_points : 0,
+                         c->tree_in_built ? c->tree_in.pairs_per_matvec : 0};
+  for (int i = 0; i < n && i < 13; ++i) out[i] = v[i];
   return NCS_OK;
 }
 
@@ -1224,7 +1266,7 @@ int ncs_tree_pairs(ncs_ctx* c, int64_t* count, int* target, int* source, int* le
   try {
     if (c->centres.empty()) throw Fail{NCS_E_STATE, "no patches: call ncs_set_patches first"};
     std::vector<int> t, s, l, k;
-    ncs::tree_pairs(c->centres, c->pc, tree_options(c), t, s, l, k);
+    ncs::tree_pairs(c->centres, c->pc, tree_options(c, c->prm.grid_tol), t, s, l, k);
     if (target && source && level && kind) {
       if (*count < (int64_t)t.size()) throw Fail{NCS_E_INPUT, "pair buffers too small"};
       std::memcpy(target, t.data(), t.size() * sizeof(int));
@@ -1430,6 +1472,14 @@ int ncs_solve(ncs_ctx* c, double tol, int precision, double* fhat, double* scala
       // the residual precision before the solve reports convergence.
       constexpr double kUpdateRel = 1e-4;
       double* corr = c->work + 4 * n;
+      // the inner solves and the FP32 residual update run on the inner tree (if any); the
+      // flag is cleared again on every exit
+      if (use_tree(c)) ensure_inner_tree(c);
+      struct InnerScope {
+        ncs_ctx* c;
+        explicit InnerScope(ncs_ctx* cc) : c(cc) { c->inner_active = true; }
+        ~InnerScope() { c->inner_active = false; }
+      };
       CU(cudaMemsetAsync(x, 0, n * sizeof(double), s));
       CU(cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
       rel = 1.0;
@@ -1449,12 +1499,18 @@ int ncs_solve(ncs_ctx* c, double tol, int precision, double* fhat, double* scala
         }
         const double inner_tol = std::max(0.3 * tol / rel, 3e-6);
         double inner_est = 1.0;
-        total += gmres(c, r, corr, std::min(inner_tol, 0.5), NCS_FP32, maxit, &inner_est, s);
+        {
+          InnerScope in(c);
+          total += gmres(c, r, corr, std::min(inner_tol, 0.5), NCS_FP32, maxit, &inner_est, s);
+        }
         c->solve_stats[3] += 1.0;
         CU(ncs::launch_axpby(n, 1.0, corr, 1.0, x, s));
         if (rel <= kUpdateRel && c->prm.residual_update) {
           double* Ac = c->work + 3 * n;
-          matvec(c, corr, Ac, NCS_FP32, s);
+          {
+            InnerScope in(c);
+            matvec(c, corr, Ac, NCS_FP32, s);
+          }
           CU(ncs::launch_axpby(n, -1.0, Ac, 1.0, r, s));
           c->solve_stats[2] += 1.0;
           updated = true;

@@ -220,6 +220,12 @@ struct ncs_ctx {
   ncs::TreeDevice tdev;
   bool tree_built = false;      // host tree ready
   bool tree_uploaded = false;   // device copy ready
+  // the tree of the mixed solve's inner FP32 products: incoming grids to prm.inner_grid_tol
+  ncs::TreeHost tree_in;
+  ncs::TreeDevice tdev_in;
+  bool tree_in_built = false;
+  bool tree_in_uploaded = false;
+  bool inner_active = false;    // inside ncs_solve's inner solves: FP32 tree products use tdev_in
   bool device_ready = false;    // operator uploaded, stream created
   bool layout_dirty = false;    // centres changed since the last upload
   // GMRES workspace
@@ -231,9 +237,11 @@ struct ncs_ctx {
   double* gmem = nullptr;      // backing store of gd
   ncs::GmresDev gd;
   ncs::GmresState* st_host = nullptr;  // pinned copy of *gd.st, read after each step
-  // one captured Arnoldi step (product + orthogonalisation + state copy) per precision
-  cudaGraphExec_t step_graph[4] = {nullptr, nullptr, nullptr, nullptr};
-  long long step_graph_kernels[4] = {0, 0, 0, 0};
+  // one captured Arnoldi step (product + orthogonalisation + state copy) per precision, and
+  // (slot 4) for the inner FP32 products of the mixed solve
+  static constexpr int kGraphSlots = 5;
+  cudaGraphExec_t step_graph[kGraphSlots] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  long long step_graph_kernels[kGraphSlots] = {0, 0, 0, 0, 0};
   ncs_tuning tune{16, 4, 4, 16, 0.1, 0, 0};  // tree product launch configuration (ncs_tune)
   // one-patch data of the near-patch quadrature (ncs_eval), uploaded on first use
   bool near_ready = false;

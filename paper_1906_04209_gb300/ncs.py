@@ -42,7 +42,8 @@ class ncs_params(ctypes.Structure):
                 ("verbose", ctypes.c_int), ("mixed_residual", ctypes.c_int), ("tensor_cores", ctypes.c_int),
                 ("residual_update", ctypes.c_int), ("id_ladder_max", ctypes.c_double),
                 ("device_precompute", ctypes.c_int), ("cuda_graphs", ctypes.c_int),
-                ("batch_ladder_by_n", ctypes.c_int), ("batch_grouped", ctypes.c_int)]
+                ("batch_ladder_by_n", ctypes.c_int), ("batch_grouped", ctypes.c_int),
+                ("inner_grid_tol", ctypes.c_double)]
 
 
 class ncs_tuning(ctypes.Structure):
@@ -247,9 +248,10 @@ class Context:
             pass
 
     def info(self) -> dict:
-        out = (ctypes.c_int64 * 11)()
-        load().ncs_info(self.h, out, 11)
-        keys = ["K", "Kstar", "p", "M", "nf", "N", "nrad", "levels", "grid_points", "tree_pairs", "direct_pairs"]
+        out = (ctypes.c_int64 * 13)()
+        load().ncs_info(self.h, out, 13)
+        keys = ["K", "Kstar", "p", "M", "nf", "N", "nrad", "levels", "grid_points", "tree_pairs", "direct_pairs",
+                "inner_grid_points", "inner_tree_pairs"]
         return dict(zip(keys, [int(v) for v in out]))
 
     def timings(self):
