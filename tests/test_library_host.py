@@ -105,6 +105,20 @@ def test_create_validation(libncs):
         assert e.value.code == ncs.NCS_E_INPUT
 
 
+def test_inner_grid_tol_validation(libncs):
+    """inner_grid_tol (the mixed solve's inner tree) accepts 0 (off) up to below 0.1; the
+    context reports no inner tree before one is built."""
+    assert ncs.default_params().inner_grid_tol == 1e-5
+    for bad in (-1e-6, 0.1, 0.5):
+        with pytest.raises(ncs.NcsError) as e:
+            ncs.Context(0.1, 1, 3, npan=4, nord=6, inner_grid_tol=bad)
+        assert e.value.code == ncs.NCS_E_INPUT
+    for ok in (0.0, 1e-9, 1e-3):
+        c = ncs.Context(0.1, 1, 3, npan=4, nord=6, ntheta_fine=8, inner_grid_tol=ok)
+        info = c.info()
+        assert info["inner_grid_points"] == 0 and info["inner_tree_pairs"] == 0
+
+
 def test_set_patches_validation(libncs):
     c = ncs.Context(0.1, 1, 3, npan=4, nord=6, ntheta_fine=8)
     with pytest.raises(ncs.NcsError) as e:  # geodesic distance 0.25 < 3 eps
