@@ -77,3 +77,24 @@ def test_tree_build_independent_of_thread_count(libncs):
         stats.append(ctx.tree_stats())
     assert stats[0] == stats[1]
     assert stats[0]["grid_groups"] > 0 and stats[0]["p2l_items"] > 0
+
+
+def test_looser_grids_keep_the_covering(libncs):
+    """The mixed solve's inner tree is the same construction at a looser incoming-grid
+    tolerance: every ordered pair is still accounted for exactly once, with the same levels,
+    fewer grid points and fewer P2L pair evaluations (groups may trade direct sums for grids,
+    never drop a pair)."""
+    c, eps = L.jittered_fibonacci(3000, 0.003, L.rng(17)), 0.003
+    stats = {}
+    for gt in (1e-8, 1e-5):
+        ctx = ncs.Context(eps, 1, 3, npan=4, nord=6, ntheta_fine=8, grid_tol=gt, method=ncs.METHOD_TREE)
+        ctx.set_patches(c)
+        tg, sr, lv, kd = ctx.tree_pairs()
+        N = len(c)
+        u, cnt = np.unique(tg.astype(np.int64) * N + sr, return_counts=True)
+        assert len(u) == N * (N - 1) and cnt.max() == 1
+        stats[gt] = ctx.tree_stats()
+    loose, fine = stats[1e-5], stats[1e-8]
+    assert loose["levels"] == fine["levels"]
+    assert loose["grid_points"] < fine["grid_points"]
+    assert loose["p2l_pairs"] < fine["p2l_pairs"]
