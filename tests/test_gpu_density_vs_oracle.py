@@ -1,4 +1,4 @@
-"""Solution densities against the oracle's FP64 solve (the benchmark spec's error bars: density
+"""Solution densities against the oracle's FP64 solve (the error bars the solver targets: density
 relative error <= 1e-6 for the mixed solve, <= 1e-10 in FP64): the oracle runs its own
 GMRES (modified Gram-Schmidt, Section 7 Step 3 reading) on the compressed product of
 Section 7.1 evaluated at every Zernike node by its plain-C sums, for the interior
